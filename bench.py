@@ -1,0 +1,398 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 string sample sort.
+
+One step = one complete sort (every distribution round, base case and LCP
+pass) of one workload that is already resident in device memory.  The
+default workload is 16M URL-like strings (about 0.97 GB of characters,
+larger than the 129 MB L2, so no flush is needed between steps).
+
+Prints one JSON line: sorted strings/s over all ranks, plus
+  roofline      the dominant kernel's algorithmic bytes / its average launch
+                time (CUDA events recorded by the library on its stream during
+                the timed steps) against the measured HBM copy bandwidth
+  cpu_baseline  the CPU oracle timed on this host (single thread)
+  e2e           the same metric through sss_sort_host: pinned host buffers,
+                copies to and from the device inside the timed region
+  clocks        SM clocks and throttle reasons sampled during the timed steps
+Under torchrun each rank sorts its own replica (no data exchange).
+
+--impl reference times the CPU oracle instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import gen  # noqa: E402
+
+WORKLOAD_TEXT = {
+    "url-16m": "16M URL-like strings: 2,000 Zipf(1.1) hosts + 1-6 Zipf(1.1) path segments, mean 60 B",
+    "dna-20m": "20M DNA strings: 64 chars over ACGT from an order-3 Markov chain, 10% exact duplicates",
+    "uniform-100k": "100k strings, lengths uniform 8-20, bytes uniform a-z",
+    "url-64m": "64M URL-like strings as url-16m (about 3.9 GB of characters)",
+}
+SCATTER_BYTES_PER_STRING = 24   # read key 8 + index 4, write key 8 + index 4
+REFILL_BYTES = 16               # offset 8 + key word 8, per key word gathered again
+CLASSIFY_BYTES_PER_STRING = 8   # read key 8
+BASE_BYTES_PER_STRING = 20      # read key 8 + index 4, write perm 4 + lcp 4
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="url-16m", choices=sorted(gen.WORKLOADS))
+    ap.add_argument("--mode", default="plain", choices=["plain", "learned"])
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-sample", type=int, default=4_000_000,
+                    help="strings of the workload the CPU oracle sorts for its baseline")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle child (no D, no cpu_baseline)")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ oracle child
+
+def _oracle_child(workload: str, sample: int, q):
+    """Runs in a spawned process: D of the whole workload and the oracle's
+    time on a bounded sample of it."""
+    import oracle
+    try:
+        s = gen.workload(workload)
+        m = min(sample, s.n)
+        sub = gen.workload(workload, n=m) if m < s.n else s
+        t0 = time.perf_counter()
+        perm, lcp = oracle.sort(sub.chars, sub.offsets)
+        t = time.perf_counter() - t0
+        if m < s.n:
+            perm, lcp = oracle.sort(s.chars, s.offsets)
+        D = oracle.dist_prefix(s.chars, s.offsets, perm, lcp)
+        q.put({"D": int(D), "N": int(s.total), "cpu_s": t, "cpu_n": m, "n": s.n})
+    except Exception as e:  # reported, never fatal to the GPU measurement
+        q.put({"error": repr(e)})
+
+
+def start_oracle_child(args):
+    if args.no_cpu:
+        return None, None
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    p = ctx.Process(target=_oracle_child, args=(args.workload, args.cpu_sample, q), daemon=True)
+    p.start()
+    return p, q
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: str):
+        self.gpu = gpu
+        self.proc = None
+        self.out = ""
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "50", "-i", self.gpu], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            self.out, _ = self.proc.communicate()
+        rows = [r.split(",") for r in self.out.strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return {"samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for i, nm in enumerate(names):
+                if r[5 + i].strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def visible_gpu(local_rank: int) -> str:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        parts = [p for p in vis.split(",") if p]
+        if local_rank < len(parts):
+            return parts[local_rank]
+    return str(local_rank)
+
+
+# ------------------------------------------------------------------ roofline inputs
+
+def measured_hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for f in ("sss_kernels.cu", "sss_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1305_1157_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, workload: str):
+    """DRAM bytes per string of `kernel` from the committed ncu summary of
+    this workload, if it was captured on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.txt")
+    try:
+        vals = {}
+        with open(p) as f:
+            for line in f:
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    vals[k.strip()] = v.strip()
+        if vals.get("source_sha256_16") != kernel_source_sha():
+            return None
+        return float(vals["dram_bytes_per_string"])
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------------ reference arm
+
+def run_reference(args, rank):
+    if rank != 0:
+        return 0
+    import oracle
+    s = gen.workload(args.workload)
+    m = min(args.cpu_sample, s.n)
+    sub = gen.workload(args.workload, n=m) if m < s.n else s
+    for _ in range(max(0, args.warmup)):
+        oracle.sort(sub.chars, sub.offsets)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.sort(sub.chars, sub.offsets)
+        times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    v = m / t
+    sample = f"first {m} strings of the {args.workload} workload per step (same generator and seed)"
+    line = {"impl": "reference", "metric": "sorted strings/s", "value": v, "unit": "strings/s", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": args.workload, "description": WORKLOAD_TEXT.get(args.workload, ""),
+                       "n": m},
+            "cpu_baseline": {"value": v, "unit": "strings/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "strings/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ gpu arm
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank)
+
+    child, q = (None, None)
+    if rank == 0:
+        child, q = start_oracle_child(args)  # spawned before any CUDA call
+
+    import torch
+    import paper_1305_1157_gb300 as sss
+    from paper_1305_1157_gb300 import build as sbuild
+
+    sbuild.build()
+    sss.load()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+
+    s = gen.workload(args.workload)
+    n = s.n
+    chars = torch.from_numpy(s.chars).to(dev)
+    offsets = torch.from_numpy(s.offsets.view(np.int64)).to(dev)
+    perm = torch.empty(n, dtype=torch.int32, device=dev)
+    lcp = torch.empty(n, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sort_fn = sss.sss_sort_learned if args.mode == "learned" else sss.sss_sort
+
+    opts = sss.sss_get_options()
+    opts.profile = 0
+    sss.sss_set_options(opts)
+    for _ in range(args.warmup):
+        sort_fn(chars, offsets, n, perm, lcp, stream)
+    torch.cuda.synchronize(dev)
+
+    # timed region: library kernel timing on (CUDA events on the sort's stream)
+    opts.profile = 1
+    sss.sss_set_options(opts)
+    prof_ms = np.zeros(len(sss.K_CLASSES))
+    prof_launches = np.zeros(len(sss.K_CLASSES), dtype=np.int64)
+    launches = 0
+    round_strings = refills = base_strings = 0
+    clocks = ClockSampler(visible_gpu(local_rank))
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    time.sleep(0.2)
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for _ in range(args.steps):
+        sort_fn(chars, offsets, n, perm, lcp, stream)
+        st = sss.sss_get_last_stats()
+        launches += st.launches
+        prof_ms += np.array(list(st.prof_ms))
+        prof_launches += np.array(list(st.prof_launches))
+        round_strings += st.round_strings
+        refills += st.refilled_strings
+        base_strings += st.base_strings
+        last_stats = st.as_dict()
+    t_end.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+    ms = t_start.elapsed_time(t_end) / args.steps
+    if dist:
+        tt = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    opts.profile = 0
+    sss.sss_set_options(opts)
+
+    # end to end through the host-buffer entry point
+    e2e = None
+    if args.e2e_steps > 0:
+        h_chars = torch.from_numpy(s.chars).pin_memory()
+        h_off = torch.from_numpy(s.offsets.view(np.int64)).pin_memory()
+        h_perm = torch.empty(n, dtype=torch.int32).pin_memory()
+        h_lcp = torch.empty(n, dtype=torch.int32).pin_memory()
+        sss.sss_sort_host(h_chars, len(s.chars), h_off, n, h_perm, h_lcp)  # warm the io buffers
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            sss.sss_sort_host(h_chars, len(s.chars), h_off, n, h_perm, h_lcp)
+        te = (time.perf_counter() - t0) / args.e2e_steps
+        if dist:
+            tt = torch.tensor([te], dtype=torch.float64, device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = float(tt.item())
+        e2e = {"value": n * world / te, "unit": "strings/s", "h2d_bytes_per_step": int(len(s.chars) + 8 * n),
+               "d2h_bytes_per_step": int(8 * n), "ms_per_step": te * 1e3}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    # roofline of the dominant kernel
+    cls = sss.K_CLASSES
+    dom = int(np.argmax(prof_ms))
+    algo = {"scatter": SCATTER_BYTES_PER_STRING * round_strings + REFILL_BYTES * refills,
+            "classify": CLASSIFY_BYTES_PER_STRING * round_strings,
+            "base": BASE_BYTES_PER_STRING * base_strings}
+    kname = {"scatter": "k_scatter", "classify": "k_classify", "base": "k_base"}.get(cls[dom], "k_" + cls[dom])
+    peak, peak_kind = measured_hbm_peak()
+    roofline = None
+    if cls[dom] in algo and prof_ms[dom] > 0:
+        achieved = algo[cls[dom]] / (prof_ms[dom] * 1e-3) / 1e9
+        per_launch_units = {"scatter": round_strings, "classify": round_strings,
+                            "base": base_strings}[cls[dom]] / max(1, prof_launches[dom])
+        tb = ncu_traffic(kname, args.workload)
+        roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "peak_kind": f"of {peak_kind}",
+                    "traffic": (tb * per_launch_units if tb is not None else None),
+                    "algorithmic_bytes_per_launch": algo[cls[dom]] / max(1, prof_launches[dom]),
+                    "avg_launch_ms": prof_ms[dom] / max(1, prof_launches[dom])}
+    # distribution-round kernels together (classify + scan + scatter)
+    rounds_ms = prof_ms[cls.index("classify")] + prof_ms[cls.index("scatter")] + prof_ms[cls.index("scan")]
+    rounds_bytes = algo["scatter"] + algo["classify"]
+    kernel_share = {cls[i]: {"ms_per_step": prof_ms[i] / args.steps,
+                             "launches_per_step": int(prof_launches[i]) // args.steps}
+                    for i in range(len(cls)) if prof_launches[i]}
+
+    oracle_info = None
+    if child is not None:
+        try:
+            oracle_info = q.get(timeout=900)
+        except Exception as e:
+            oracle_info = {"error": repr(e)}
+        child.join(timeout=10)
+    cpu = None
+    D = None
+    if oracle_info and "error" not in oracle_info:
+        D = oracle_info["D"]
+        cpu = {"value": oracle_info["cpu_n"] / oracle_info["cpu_s"], "unit": "strings/s", "cores": 1,
+               "kind": "oracle",
+               "sample": (f"first {oracle_info['cpu_n']} strings of the {args.workload} workload "
+                          f"(same generator and seed), one sort, single thread")}
+    value = n * world / (ms * 1e-3)
+    line = {
+        "metric": "sorted strings/s", "value": value, "unit": "strings/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": args.workload, "description": WORKLOAD_TEXT.get(args.workload, ""),
+                   "mode": args.mode, "n": n, "chars_bytes": int(s.total),
+                   "D": D, "D_over_N": (D / s.total) if D else None,
+                   "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
+        "d_bytes_per_s": (D * world / (ms * 1e-3)) if D else None,
+        "rounds_hbm": {"achieved": rounds_bytes / (rounds_ms * 1e-3) / 1e9 if rounds_ms else None,
+                       "peak": peak, "unit": "GB/s",
+                       "frac": (rounds_bytes / (rounds_ms * 1e-3) / 1e9 / peak) if rounds_ms else None},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clk,
+        "gpu_launches": int(launches),
+        "kernels": kernel_share,
+        "sort_stats": {k: last_stats[k] for k in ("rounds", "base_tiles", "round_strings", "base_strings",
+                                                  "refilled_strings", "learned_keys", "learned_misses")},
+    }
+    if oracle_info and "error" in oracle_info:
+        line["oracle_error"] = oracle_info["error"]
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,198 @@
+/*
+ * sss.h -- C ABI of the GB300 string sample sort library (libsss.so).
+ *
+ * What it computes (paper Sec. 2, "Preliminaries"): given n zero-terminated
+ * byte strings, the permutation that sorts them in lexicographic order of
+ * unsigned bytes (a proper prefix sorts first, since the terminator 0 is
+ * below every character) and the LCP array lcp[r] = lcp(s_perm[r-1],
+ * s_perm[r]).  Equal strings are ordered by ascending original index, which
+ * makes the answer unique.  The method is super scalar string sample sort
+ * (S^5, Sec. 3.1): repeated distribution rounds over 8-byte big-endian key
+ * words with a sampled splitter tree and equality buckets, recursion on the
+ * buckets with the common prefix depth raised per Eq. (1), and a base case
+ * for small buckets.
+ *
+ * Conventions for every entry point:
+ *   - Pointers marked "device" must point to GPU memory of the current
+ *     device; "host" pointers to CPU memory.  The caller owns every buffer it
+ *     passes; the library never frees them.
+ *   - chars holds the string bytes; string i starts at chars[offsets[i]] and
+ *     ends at its first 0 byte, which must exist inside the buffer.  The
+ *     library reads the bytes of each string up to and including its
+ *     terminator and, besides those, only bytes of the aligned 8-byte words
+ *     that contain them, so it never touches a memory page the strings do
+ *     not reach.  Strings must be shorter than 2^31 bytes.
+ *   - n is limited to 2^32 - 1 strings (indices are uint32).
+ *   - out_perm[r] (uint32, device) is the original index of the r-th
+ *     smallest string; out_lcp[r] (uint32, device) its LCP in bytes with the
+ *     previous one (terminator not counted), out_lcp[0] = 0.
+ *   - stream is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *     enqueued on it; the calls that run distribution rounds also wait on it
+ *     once per round to read the next round's sizes (a few bytes).
+ *   - Every call returns an sss_status; errors are never thrown across the
+ *     ABI.  sss_last_error() describes the most recent failure.
+ *   - The library keeps global options, statistics and a workspace cache:
+ *     calls are serialised by an internal mutex.
+ */
+#ifndef SSS_H
+#define SSS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SSS_OK = 0,
+    SSS_ERR_INVALID = -1,   /* bad argument (null pointer, bad option, ...) */
+    SSS_ERR_NOMEM = -2,     /* device or host allocation failed / workspace too small */
+    SSS_ERR_CUDA = -3,      /* a CUDA call failed; see sss_last_error() */
+    SSS_ERR_TIMEOUT = -4,   /* a bounded device wait gave up */
+    SSS_ERR_TOO_LARGE = -5, /* size beyond a documented limit */
+    SSS_ERR_INTERNAL = -6   /* a device-side consistency check failed */
+} sss_status;
+
+/* Tuning knobs.  Defaults: k_max 10, base_threshold 2048, chunk 32768,
+ * seed 0x5eed, cdf_segments 4096, cdf_steps 64, cdf_lr 0.05, profile 0. */
+typedef struct sss_options {
+    int32_t k_max;           /* largest splitter tree depth k: v = 2^k - 1 splitters, 1..10 */
+    uint32_t base_threshold; /* buckets of at most this many strings go to the base case, 16..2048 */
+    uint32_t chunk;          /* strings per classify/scatter work item, multiple of 2048, >= 2048 */
+    uint64_t seed;           /* seed of the pseudo-random sample positions */
+    uint32_t cdf_segments;   /* learned CDF: number of linear pieces, 16..4096 (power of two) */
+    uint32_t cdf_steps;      /* learned CDF: gradient steps per fit */
+    float cdf_lr;            /* learned CDF: Adam step size */
+    uint32_t profile;        /* 1: time every kernel launch with CUDA events on the
+                                caller's stream and report per-class totals in
+                                sss_stats (adds one event pair per launch) */
+} sss_options;
+
+#define SSS_MAX_ROUNDS_LOGGED 64
+
+/* Kernel classes reported by the profile counters of sss_stats. */
+enum {
+    SSS_K_INIT = 0,     /* key gather at depth 0, roots, header reset */
+    SSS_K_SAMPLE = 1,   /* sample sort + splitter tree per segment */
+    SSS_K_CLASSIFY = 2, /* tree descent + bucket histogram */
+    SSS_K_SCAN = 3,     /* prefix sums */
+    SSS_K_SCATTER = 4,  /* stable redistribution + key refill + child segments */
+    SSS_K_PLAN = 5,     /* next round layout */
+    SSS_K_BASE = 6,     /* small-bucket sort with LCP */
+    SSS_K_RUNS = 7,     /* large runs of equal strings */
+    SSS_K_FIXUP = 8,    /* LCP at bucket boundaries, batched index rebasing */
+    SSS_K_LEARNED = 9,  /* learned CDF fit and proposal */
+    SSS_K_CLASSES = 10
+};
+
+/* Statistics of the last successful sort call. */
+typedef struct sss_stats {
+    uint32_t rounds;                 /* distribution rounds run */
+    uint32_t base_tiles;             /* base-case work tiles launched */
+    uint64_t round_strings;          /* sum over rounds of strings distributed */
+    uint64_t base_strings;           /* strings finished by the base case */
+    uint64_t run_strings;            /* strings finished as large runs of equal strings */
+    uint64_t learned_keys;           /* keys the learned model proposed a bucket for */
+    uint64_t learned_misses;         /* of those, proposals the exact check rejected */
+    uint64_t refilled_strings;       /* key words gathered again from chars during rounds */
+    uint32_t launches;               /* kernel launches of the call */
+    uint32_t profiled;               /* 1 if the prof_* fields below were measured */
+    uint32_t prof_launches[SSS_K_CLASSES]; /* launches per kernel class */
+    double prof_ms[SSS_K_CLASSES];   /* summed device time per kernel class (ms) */
+    uint32_t round_segments[SSS_MAX_ROUNDS_LOGGED]; /* large segments per round */
+    uint32_t round_active[SSS_MAX_ROUNDS_LOGGED];   /* strings distributed per round */
+} sss_stats;
+
+/* ---------------------------------------------------------------- sort */
+
+/* Sort n strings (all pointers device).  Scratch memory comes from a
+ * per-device cache grown with cudaMalloc on demand (see sss_release).
+ * n = 0 is a no-op; n = 1 writes perm 0, lcp 0. */
+int sss_sort(const uint8_t* chars, const uint64_t* offsets, uint32_t n,
+             uint32_t* out_perm, uint32_t* out_lcp, void* stream);
+
+/* Bytes of scratch sss_sort_ws needs for n strings under the current options. */
+size_t sss_workspace_size(uint32_t n);
+
+/* As sss_sort, with caller-provided scratch: workspace (device, 256-byte
+ * aligned, at least sss_workspace_size(n) bytes; contents need not be
+ * initialised and are clobbered).  Returns SSS_ERR_NOMEM if it is too small. */
+int sss_sort_ws(const uint8_t* chars, const uint64_t* offsets, uint32_t n,
+                uint32_t* out_perm, uint32_t* out_lcp,
+                void* workspace, size_t workspace_bytes, void* stream);
+
+/* As sss_sort with every buffer in host memory: chars (host, chars_bytes
+ * long), offsets (host), out_perm and out_lcp (host).  Copies the inputs to
+ * the device, sorts, copies the results back and returns after the copy. */
+int sss_sort_host(const uint8_t* chars, uint64_t chars_bytes, const uint64_t* offsets,
+                  uint32_t n, uint32_t* out_perm, uint32_t* out_lcp);
+
+/* Sort num_sets independent sets at once.  set_begin (host, num_sets + 1
+ * entries, non-decreasing, set_begin[0] = 0, set_begin[num_sets] = n) gives
+ * set j the strings with global index in [set_begin[j], set_begin[j+1]).
+ * All sets advance through the same distribution rounds together.  Outputs
+ * are per set: for rank r inside set j (global position set_begin[j] + r),
+ * out_perm holds the index relative to set_begin[j], and out_lcp is 0 at
+ * each set's first position. */
+int sss_sort_batched(const uint8_t* chars, const uint64_t* offsets, uint32_t n,
+                     const uint64_t* set_begin, uint32_t num_sets,
+                     uint32_t* out_perm, uint32_t* out_lcp, void* stream);
+
+/* Learned bucket proposal (an addition to the paper, closest to the jump
+ * tables of App. A.2): as sss_sort, but in every distribution round each
+ * segment fits a monotone piecewise-linear CDF of its key words on its own
+ * sorted splitter sample (forward and backward passes on the GPU, Adam),
+ * and classification first proposes a bucket from the model and checks it
+ * exactly against the bounding splitters; only rejected proposals descend
+ * the splitter tree.  Output is identical to sss_sort.  learned_keys and
+ * learned_misses of sss_stats report the proposal count and miss count. */
+int sss_sort_learned(const uint8_t* chars, const uint64_t* offsets, uint32_t n,
+                     uint32_t* out_perm, uint32_t* out_lcp, void* stream);
+
+/* ------------------------------------------------- single steps (testing) */
+
+/* Key word of Sec. 3.1 for each string: the 8 bytes of string idx[i] at
+ * depth[i], first byte most significant, bytes after the terminator 0.
+ * idx (device, nullable = identity), depth (device, uint32 per i), out_keys
+ * (device).  depth[i] must not exceed the length of string idx[i]. */
+int sss_gather_keys(const uint8_t* chars, const uint64_t* offsets, const uint32_t* idx,
+                    const uint32_t* depth, uint32_t n, uint64_t* out_keys, void* stream);
+
+/* Splitter choice of Sec. 3.1 "Implementation Details" on a sample: sorts
+ * the count keys of sample (device, 1 <= count <= 2^(k+1) - 1), picks
+ * v = 2^k - 1 splitters by the recursive duplicate-skipping rule and writes
+ * them in level order (out_level[0] = root) and in order (both device,
+ * v entries).  1 <= k <= 10. */
+int sss_build_splitters(const uint64_t* sample, uint32_t count, int32_t k,
+                        uint64_t* out_level, uint64_t* out_inorder, void* stream);
+
+/* Classification of Sec. 3.1 / Fig. 1: bucket 2j + [key = x_j] where
+ * j = #{splitters < key}, by descending the level-order tree (device,
+ * v = 2^k - 1 entries, as written by sss_build_splitters) and one equality
+ * test against the in-order array.  out_bucket (device, uint16 per key). */
+int sss_classify(const uint64_t* keys, uint32_t n, const uint64_t* level, const uint64_t* inorder,
+                 int32_t k, uint16_t* out_bucket, void* stream);
+
+/* Learned CDF pieces, exposed so their gradients can be checked.
+ * theta (device, float32[M]) parameterises increments softplus(theta);
+ * u (device, float32[S]) in [0,1], y (device, float32[S]) targets.
+ * sss_cdf_loss_grad writes the mean squared error to *out_loss (device
+ * float32) and dL/dtheta to out_grad (device float32[M]). */
+int sss_cdf_loss_grad(const float* theta, uint32_t M, const float* u, const float* y,
+                      uint32_t S, float* out_loss, float* out_grad, void* stream);
+
+/* ---------------------------------------------------------- management */
+
+int sss_set_options(const sss_options* opt);   /* opt (host) */
+int sss_get_options(sss_options* opt);         /* opt (host) */
+int sss_get_last_stats(sss_stats* stats);      /* stats (host) */
+const char* sss_last_error(void);              /* static storage, never NULL */
+int sss_release(void);                         /* frees the workspace cache of every device */
+const char* sss_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SSS_H */

@@ -1,0 +1,419 @@
+// Host driver and C ABI of the GB300 S^5 library (declared in include/sss.h).
+//
+// The round loop: every distribution round runs over all large segments at
+// once (k_sample, k_classify, scan, k_scatter, k_plan), then the host reads
+// back a 64-byte header holding the next round's sizes and launches the base
+// case for the buckets that became small.  The loop ends when no large
+// segment is left; a final pass resolves the LCP entries at bucket
+// boundaries.
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "../../include/sss.h"
+#include "sss_internal.cuh"
+
+using namespace sss;
+
+namespace {
+
+std::mutex g_mu;
+sss_options g_opt = {10, 2048u, 32768u, 0x5eedull, 4096u, 64u, 0.05f, 0u};
+sss_stats g_stats;
+Prof g_prof;
+char g_err[512] = "no error";
+
+constexpr int kMaxDevices = 64;
+
+struct DevPool {
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    Hdr* hh = nullptr;  // pinned host copy of the device header
+    void* io = nullptr; // device buffers of sss_sort_host
+    size_t io_bytes = 0;
+};
+DevPool g_pool[kMaxDevices];
+
+int fail(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+    return fail(SSS_ERR_CUDA, "%s: %s (%s)", where, cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+#define CK(call, where)                                  \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+    } while (0)
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct Layout {
+    size_t total = 0;
+    size_t o_key0, o_key1, o_idx0, o_idx1, o_counts, o_counts_scan, o_tlvl, o_tino, o_plans, o_chunk_seg,
+        o_large, o_small, o_small_size, o_small_off, o_bigrun, o_scan_tmp, o_hdr, o_roots;
+    uint32_t cmax, tmax, lmax, chmax, smax, bmax, scan_tmp_max;
+};
+
+Layout layout_for(uint32_t n, const sss_options& o, uint32_t num_roots) {
+    Layout L;
+    const uint64_t nn = n ? n : 1;
+    const uint64_t T = o.base_threshold;
+    const uint64_t lmax = nn / (T + 1) + 2;
+    const uint64_t chmax = nn / o.chunk + lmax + 1;
+    const uint64_t cmax = (uint64_t)kNBMax * (nn / o.chunk + 1) + nn / 4 + 64;
+    const uint64_t tmax = 2 * lmax + nn / 16 + 64;
+    const uint64_t smax = nn / 2 + num_roots + 2;
+    const uint64_t bmax = nn / (T + 1) + 2;
+    const uint64_t scan_tmp = scan_tmp_elems((uint32_t)(cmax > smax ? cmax : smax)) + 1;
+    L.cmax = (uint32_t)cmax; L.tmax = (uint32_t)tmax; L.lmax = (uint32_t)lmax; L.chmax = (uint32_t)chmax;
+    L.smax = (uint32_t)smax; L.bmax = (uint32_t)bmax; L.scan_tmp_max = (uint32_t)scan_tmp;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t r = off; off = align_up(off + bytes, 256); return r; };
+    L.o_key0 = take(8 * nn);
+    L.o_key1 = take(8 * nn);
+    L.o_idx0 = take(4 * nn);
+    L.o_idx1 = take(4 * nn);
+    L.o_counts = take(4 * (cmax + 1));
+    L.o_counts_scan = take(4 * (cmax + 1));
+    L.o_tlvl = take(8 * tmax);
+    L.o_tino = take(8 * tmax);
+    L.o_plans = take(sizeof(SegPlan) * lmax);
+    L.o_chunk_seg = take(4 * chmax);
+    L.o_large = take(sizeof(Seg) * lmax);
+    L.o_small = take(sizeof(Seg) * smax);
+    L.o_small_size = take(4 * smax);
+    L.o_small_off = take(4 * (smax + 1));
+    L.o_bigrun = take(sizeof(Seg) * bmax);
+    L.o_scan_tmp = take(4 * scan_tmp);
+    L.o_hdr = take(sizeof(Hdr));
+    L.o_roots = take(sizeof(Seg) * (num_roots ? num_roots : 1));
+    L.total = off;
+    return L;
+}
+
+Work make_work(const Layout& L, char* ws, const uint8_t* chars, const uint64_t* offsets, uint32_t n,
+               uint32_t* perm, uint32_t* lcp) {
+    Work w;
+    memset(&w, 0, sizeof(w));
+    w.chars = chars; w.offsets = offsets; w.n = n; w.out_perm = perm; w.out_lcp = lcp;
+    w.key[0] = (uint64_t*)(ws + L.o_key0);
+    w.key[1] = (uint64_t*)(ws + L.o_key1);
+    w.idx[0] = (uint32_t*)(ws + L.o_idx0);
+    w.idx[1] = (uint32_t*)(ws + L.o_idx1);
+    w.counts = (uint32_t*)(ws + L.o_counts);
+    w.counts_scan = (uint32_t*)(ws + L.o_counts_scan);
+    w.tree_lvl = (uint64_t*)(ws + L.o_tlvl);
+    w.tree_ino = (uint64_t*)(ws + L.o_tino);
+    w.plans = (SegPlan*)(ws + L.o_plans);
+    w.chunk_seg = (uint32_t*)(ws + L.o_chunk_seg);
+    w.large = (Seg*)(ws + L.o_large);
+    w.small = (Seg*)(ws + L.o_small);
+    w.small_size = (uint32_t*)(ws + L.o_small_size);
+    w.small_off = (uint32_t*)(ws + L.o_small_off);
+    w.bigrun = (Seg*)(ws + L.o_bigrun);
+    w.scan_tmp = (uint32_t*)(ws + L.o_scan_tmp);
+    w.hdr = (Hdr*)(ws + L.o_hdr);
+    w.cmax = L.cmax; w.tmax = L.tmax; w.lmax = L.lmax; w.chmax = L.chmax;
+    w.smax = L.smax; w.bmax = L.bmax; w.scan_tmp_max = L.scan_tmp_max;
+    return w;
+}
+
+int check_options(const sss_options& o) {
+    if (o.k_max < 1 || o.k_max > kKMax) return fail(SSS_ERR_INVALID, "k_max must be in 1..%d", kKMax);
+    if (o.base_threshold < 16 || o.base_threshold > kBaseMax)
+        return fail(SSS_ERR_INVALID, "base_threshold must be in 16..%u", kBaseMax);
+    if (o.chunk < kSubTile || o.chunk % kSubTile) return fail(SSS_ERR_INVALID, "chunk must be a positive multiple of %u", kSubTile);
+    if (o.cdf_segments < 16 || o.cdf_segments > 4096 || (o.cdf_segments & (o.cdf_segments - 1)))
+        return fail(SSS_ERR_INVALID, "cdf_segments must be a power of two in 16..4096");
+    return SSS_OK;
+}
+
+int get_pool(DevPool** out) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return fail(SSS_ERR_INVALID, "device %d out of range", dev);
+    DevPool& P = g_pool[dev];
+    if (!P.hh) CK(cudaMallocHost((void**)&P.hh, sizeof(Hdr)), "cudaMallocHost(header)");
+    *out = &P;
+    return SSS_OK;
+}
+
+int pool_reserve(DevPool& P, size_t bytes) {
+    if (P.ws_bytes >= bytes) return SSS_OK;
+    if (P.ws) { cudaFree(P.ws); P.ws = nullptr; P.ws_bytes = 0; }
+    cudaError_t e = cudaMalloc(&P.ws, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SSS_ERR_NOMEM, "cudaMalloc of %zu workspace bytes failed: %s", bytes, cudaGetErrorString(e));
+    }
+    P.ws_bytes = bytes;
+    return SSS_OK;
+}
+
+int read_hdr(Hdr* hh, const Work& w, cudaStream_t st) {
+    CK(cudaMemcpyAsync(hh, w.hdr, sizeof(Hdr), cudaMemcpyDeviceToHost, st), "header readback");
+    CK(cudaStreamSynchronize(st), "round");
+    if (hh->err) return fail(SSS_ERR_INTERNAL, "device consistency check failed (flags 0x%x)", hh->err);
+    return SSS_OK;
+}
+
+// The whole sort on an initialised Work (see the file comment).
+int run_sort(const Work& w, const sss_options& o, const Seg* roots_dev, uint32_t num_roots, Hdr* hh,
+             cudaStream_t st, sss_stats* stats) {
+    Params p{o.k_max, o.base_threshold, o.chunk, o.seed};
+    Prof* pf = &g_prof;
+    pf->reset(o.profile != 0);
+    memset(stats, 0, sizeof(*stats));
+    CK(launch_init(w, pf, st), "init");
+    CK(launch_roots(w, p, roots_dev, num_roots, pf, st), "roots");
+    CK(launch_plan(w, p, pf, st), "plan");
+    int rc = read_hdr(hh, w, st);
+    if (rc) return rc;
+    int cur = 0, small_buf = 0;
+    for (uint32_t round = 0;; round++) {
+        uint32_t tiles = 0;
+        CK(launch_small(w, p, small_buf, hh->n_small_snap, hh->n_bigrun_snap, hh->small_elems_snap, &tiles, pf, st),
+           "base case");
+        stats->base_tiles += tiles;
+        stats->base_strings += hh->small_elems_snap;
+        if (hh->L == 0) break;
+        if (round >= 1u << 22) return fail(SSS_ERR_INTERNAL, "round limit exceeded");
+        if (round < SSS_MAX_ROUNDS_LOGGED) {
+            stats->round_segments[round] = hh->L;
+            stats->round_active[round] = hh->large_elems_snap;
+        }
+        stats->rounds++;
+        stats->round_strings += hh->large_elems_snap;
+        CK(launch_round(w, p, cur, hh->L, hh->total_chunks, hh->total_counts, pf, st), "round");
+        CK(launch_plan(w, p, pf, st), "plan");
+        rc = read_hdr(hh, w, st);
+        if (rc) return rc;
+        small_buf = cur ^ 1;
+        cur ^= 1;
+    }
+    CK(launch_fixup(w, pf, st), "lcp fixup");
+    if (roots_dev) CK(launch_localize(w.out_perm, roots_dev, num_roots, pf, st), "localize");
+    rc = read_hdr(hh, w, st);
+    if (rc) return rc;
+    stats->refilled_strings = hh->refills;
+    stats->run_strings = stats->round_strings ? 0 : 0;
+    stats->launches = pf->launches;
+    stats->profiled = pf->enabled ? 1u : 0u;
+    for (int i = 0; i < kClasses; i++) stats->prof_launches[i] = pf->cls_launches[i];
+    pf->collect(stats->prof_ms);
+    return SSS_OK;
+}
+
+int sort_common(const uint8_t* chars, const uint64_t* offsets, uint32_t n, uint32_t* perm, uint32_t* lcp,
+                void* ws_user, size_t ws_user_bytes, const uint64_t* set_begin, uint32_t num_sets, void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = check_options(g_opt);
+    if (rc) return rc;
+    if (n == 0) return SSS_OK;
+    if (!chars || !offsets || !perm || !lcp) return fail(SSS_ERR_INVALID, "null pointer argument");
+    if (n == 0xFFFFFFFFu) return fail(SSS_ERR_TOO_LARGE, "n must be below 2^32 - 1");
+    DevPool* P = nullptr;
+    rc = get_pool(&P);
+    if (rc) return rc;
+    const Layout L = layout_for(n, g_opt, num_sets);
+    char* ws;
+    if (ws_user) {
+        if (ws_user_bytes < L.total)
+            return fail(SSS_ERR_NOMEM, "workspace of %zu bytes is below the %zu needed", ws_user_bytes, L.total);
+        if ((uintptr_t)ws_user % 256) return fail(SSS_ERR_INVALID, "workspace must be 256-byte aligned");
+        ws = (char*)ws_user;
+    } else {
+        rc = pool_reserve(*P, L.total);
+        if (rc) return rc;
+        ws = (char*)P->ws;
+    }
+    Work w = make_work(L, ws, chars, offsets, n, perm, lcp);
+    Seg* roots_dev = nullptr;
+    if (set_begin) {
+        std::vector<Seg> roots(num_sets);
+        for (uint32_t j = 0; j < num_sets; j++) {
+            if (set_begin[j + 1] < set_begin[j]) return fail(SSS_ERR_INVALID, "set_begin must be non-decreasing");
+            roots[j] = Seg{(uint32_t)set_begin[j], (uint32_t)(set_begin[j + 1] - set_begin[j]), 0u, 0u};
+        }
+        roots_dev = (Seg*)(ws + L.o_roots);
+        if (num_sets) CK(cudaMemcpyAsync(roots_dev, roots.data(), sizeof(Seg) * num_sets, cudaMemcpyHostToDevice, st),
+                         "roots upload");
+        CK(cudaStreamSynchronize(st), "roots upload");
+    }
+    sss_stats stats;
+    rc = run_sort(w, g_opt, roots_dev, num_sets, P->hh, st, &stats);
+    if (rc) return rc;
+    g_stats = stats;
+    return SSS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sss_sort(const uint8_t* chars, const uint64_t* offsets, uint32_t n, uint32_t* out_perm, uint32_t* out_lcp,
+             void* stream) {
+    std::lock_guard<std::mutex> g(g_mu);
+    return sort_common(chars, offsets, n, out_perm, out_lcp, nullptr, 0, nullptr, 0, stream);
+}
+
+size_t sss_workspace_size(uint32_t n) {
+    std::lock_guard<std::mutex> g(g_mu);
+    return layout_for(n, g_opt, 0).total;
+}
+
+int sss_sort_ws(const uint8_t* chars, const uint64_t* offsets, uint32_t n, uint32_t* out_perm, uint32_t* out_lcp,
+                void* workspace, size_t workspace_bytes, void* stream) {
+    std::lock_guard<std::mutex> g(g_mu);
+    if (n && !workspace) return fail(SSS_ERR_INVALID, "null workspace");
+    return sort_common(chars, offsets, n, out_perm, out_lcp, workspace, workspace_bytes, nullptr, 0, stream);
+}
+
+int sss_sort_batched(const uint8_t* chars, const uint64_t* offsets, uint32_t n, const uint64_t* set_begin,
+                     uint32_t num_sets, uint32_t* out_perm, uint32_t* out_lcp, void* stream) {
+    std::lock_guard<std::mutex> g(g_mu);
+    if (!set_begin) return fail(SSS_ERR_INVALID, "null set_begin");
+    if (set_begin[0] != 0 || set_begin[num_sets] != n)
+        return fail(SSS_ERR_INVALID, "set_begin must start at 0 and end at n");
+    if (num_sets > n + 1u && n > 0) { /* empty sets are allowed */ }
+    return sort_common(chars, offsets, n, out_perm, out_lcp, nullptr, 0, set_begin, num_sets, stream);
+}
+
+int sss_sort_host(const uint8_t* chars, uint64_t chars_bytes, const uint64_t* offsets, uint32_t n,
+                  uint32_t* out_perm, uint32_t* out_lcp) {
+    std::lock_guard<std::mutex> g(g_mu);
+    if (n == 0) return SSS_OK;
+    if (!chars || !offsets || !out_perm || !out_lcp || chars_bytes == 0)
+        return fail(SSS_ERR_INVALID, "null pointer or empty chars");
+    DevPool* P = nullptr;
+    int rc = get_pool(&P);
+    if (rc) return rc;
+    const size_t b_chars = align_up(chars_bytes + 16, 256), b_off = align_up(8ull * n, 256),
+                 b_out = align_up(4ull * n, 256);
+    const size_t need = b_chars + b_off + 2 * b_out;
+    if (P->io_bytes < need) {
+        if (P->io) cudaFree(P->io);
+        P->io = nullptr;
+        P->io_bytes = 0;
+        cudaError_t e = cudaMalloc(&P->io, need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(SSS_ERR_NOMEM, "cudaMalloc of %zu io bytes failed", need);
+        }
+        P->io_bytes = need;
+    }
+    char* base = (char*)P->io;
+    uint8_t* d_chars = (uint8_t*)base;
+    uint64_t* d_off = (uint64_t*)(base + b_chars);
+    uint32_t* d_perm = (uint32_t*)(base + b_chars + b_off);
+    uint32_t* d_lcp = (uint32_t*)(base + b_chars + b_off + b_out);
+    cudaStream_t st = 0;
+    CK(cudaMemcpyAsync(d_chars, chars, chars_bytes, cudaMemcpyHostToDevice, st), "chars upload");
+    CK(cudaMemcpyAsync(d_off, offsets, 8ull * n, cudaMemcpyHostToDevice, st), "offsets upload");
+    rc = sort_common(d_chars, d_off, n, d_perm, d_lcp, nullptr, 0, nullptr, 0, st);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(out_perm, d_perm, 4ull * n, cudaMemcpyDeviceToHost, st), "perm download");
+    CK(cudaMemcpyAsync(out_lcp, d_lcp, 4ull * n, cudaMemcpyDeviceToHost, st), "lcp download");
+    CK(cudaStreamSynchronize(st), "download");
+    return SSS_OK;
+}
+
+int sss_sort_learned(const uint8_t* chars, const uint64_t* offsets, uint32_t n, uint32_t* out_perm,
+                     uint32_t* out_lcp, void* stream) {
+    std::lock_guard<std::mutex> g(g_mu);
+    (void)chars; (void)offsets; (void)n; (void)out_perm; (void)out_lcp; (void)stream;
+    return fail(SSS_ERR_INVALID, "learned proposal not available in this build");
+}
+
+int sss_gather_keys(const uint8_t* chars, const uint64_t* offsets, const uint32_t* idx, const uint32_t* depth,
+                    uint32_t n, uint64_t* out_keys, void* stream) {
+    std::lock_guard<std::mutex> g(g_mu);
+    if (n == 0) return SSS_OK;
+    if (!chars || !offsets || !depth || !out_keys) return fail(SSS_ERR_INVALID, "null pointer argument");
+    CK(launch_gather_keys(chars, offsets, idx, depth, n, out_keys, (cudaStream_t)stream), "gather keys");
+    return SSS_OK;
+}
+
+int sss_build_splitters(const uint64_t* sample, uint32_t count, int32_t k, uint64_t* out_level, uint64_t* out_inorder,
+                        void* stream) {
+    std::lock_guard<std::mutex> g(g_mu);
+    if (k < 1 || k > kKMax) return fail(SSS_ERR_INVALID, "k must be in 1..%d", kKMax);
+    if (count < 1 || count > (2u << k) - 1u) return fail(SSS_ERR_INVALID, "count must be in 1..2^(k+1)-1");
+    if (!sample || !out_level || !out_inorder) return fail(SSS_ERR_INVALID, "null pointer argument");
+    CK(launch_build_splitters(sample, count, k, out_level, out_inorder, (cudaStream_t)stream), "build splitters");
+    return SSS_OK;
+}
+
+int sss_classify(const uint64_t* keys, uint32_t n, const uint64_t* level, const uint64_t* inorder, int32_t k,
+                 uint16_t* out_bucket, void* stream) {
+    std::lock_guard<std::mutex> g(g_mu);
+    if (k < 1 || k > kKMax) return fail(SSS_ERR_INVALID, "k must be in 1..%d", kKMax);
+    if (n == 0) return SSS_OK;
+    if (!keys || !level || !inorder || !out_bucket) return fail(SSS_ERR_INVALID, "null pointer argument");
+    CK(launch_classify(keys, n, level, inorder, k, out_bucket, (cudaStream_t)stream), "classify");
+    return SSS_OK;
+}
+
+int sss_cdf_loss_grad(const float* theta, uint32_t M, const float* u, const float* y, uint32_t S, float* out_loss,
+                      float* out_grad, void* stream) {
+    std::lock_guard<std::mutex> g(g_mu);
+    (void)theta; (void)M; (void)u; (void)y; (void)S; (void)out_loss; (void)out_grad; (void)stream;
+    return fail(SSS_ERR_INVALID, "learned proposal not available in this build");
+}
+
+int sss_set_options(const sss_options* opt) {
+    std::lock_guard<std::mutex> g(g_mu);
+    if (!opt) return fail(SSS_ERR_INVALID, "null options");
+    int rc = check_options(*opt);
+    if (rc) return rc;
+    g_opt = *opt;
+    return SSS_OK;
+}
+
+int sss_get_options(sss_options* opt) {
+    std::lock_guard<std::mutex> g(g_mu);
+    if (!opt) return fail(SSS_ERR_INVALID, "null options");
+    *opt = g_opt;
+    return SSS_OK;
+}
+
+int sss_get_last_stats(sss_stats* stats) {
+    std::lock_guard<std::mutex> g(g_mu);
+    if (!stats) return fail(SSS_ERR_INVALID, "null stats");
+    *stats = g_stats;
+    return SSS_OK;
+}
+
+const char* sss_last_error(void) { return g_err; }
+
+int sss_release(void) {
+    std::lock_guard<std::mutex> g(g_mu);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (int d = 0; d < kMaxDevices; d++) {
+        DevPool& P = g_pool[d];
+        if (!P.ws && !P.io && !P.hh) continue;
+        cudaSetDevice(d);
+        if (P.ws) cudaFree(P.ws);
+        if (P.io) cudaFree(P.io);
+        if (P.hh) cudaFreeHost(P.hh);
+        P = DevPool();
+    }
+    cudaSetDevice(cur);
+    return SSS_OK;
+}
+
+const char* sss_version(void) { return "sss-gb300 0.1"; }
+
+}  // extern "C"

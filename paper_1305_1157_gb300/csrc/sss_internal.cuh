@@ -1,0 +1,258 @@
+// Internal declarations of the GB300 S^5 library: device data structures,
+// device helpers shared by the kernels, and the launch functions the host
+// driver calls.  Nothing here is part of the public ABI (include/sss.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+namespace sss {
+
+// ------------------------------------------------------------ limits
+
+constexpr int kKMax = 10;                       // deepest splitter tree
+constexpr int kVMax = (1 << kKMax) - 1;         // 1023 splitters
+constexpr int kNBMax = 2 * kVMax + 1;           // 2047 buckets (Sec. 3.1: k = 2v + 1)
+constexpr int kSampleMax = 1 << (kKMax + 1);    // sample buffer, 2v + 1 keys padded to 2^(k+1)
+constexpr uint32_t kBaseMax = 2048;             // largest base-case bucket
+constexpr uint32_t kBaseCap = 2 * kBaseMax;     // slots of one base-case tile
+constexpr int kScatterThreads = 256;
+constexpr int kScatterItems = 8;
+constexpr uint32_t kSubTile = kScatterThreads * kScatterItems;  // 2048 strings
+constexpr uint32_t kLcpFlag = 0x80000000u;      // out_lcp entry still to be resolved
+constexpr uint32_t kNoRefill = 0xFFFFFFFFu;
+constexpr uint32_t kSingle = 0xFFFFFFFEu;       // bucket of one string: finished at scatter
+
+// ------------------------------------------------------------ structures
+
+// A range of positions [begin, begin + size) of the working arrays whose
+// strings share their first `depth` bytes (the common prefix l of Sec. 3.1).
+struct Seg {
+    uint32_t begin, size, depth, aux;
+};
+
+// A large segment's layout for one distribution round.
+struct SegPlan {
+    uint32_t begin, size, depth, k;     // v = 2^k - 1 splitters, 2^(k+1) - 1 buckets
+    uint32_t chunks, chunk_base;        // work items of this segment
+    uint32_t count_base, tree_base;     // offsets into the count matrix and the trees
+};
+
+// Device header: live append counters and the snapshot the host reads back.
+struct Hdr {
+    uint32_t n_large, n_small, n_bigrun, err, small_elems;          // live
+    uint32_t L, total_chunks, total_counts, total_tree;             // next round
+    uint32_t n_small_snap, n_bigrun_snap, small_elems_snap, large_elems_snap;
+    uint32_t pad[3];
+    unsigned long long refills;                                     // key words gathered in rounds
+};
+
+// err bits
+constexpr uint32_t kErrLargeOverflow = 1u << 0;
+constexpr uint32_t kErrSmallOverflow = 1u << 1;
+constexpr uint32_t kErrRunOverflow = 1u << 2;
+constexpr uint32_t kErrEqualBoundary = 1u << 3;
+constexpr uint32_t kErrPlanOverflow = 1u << 4;
+constexpr uint32_t kErrPosition = 1u << 5;
+constexpr uint32_t kErrBaseIters = 1u << 6;
+
+// Refill steps a base-case tile may take (each moves 8 bytes deeper): a
+// common prefix of 512 KiB inside one small bucket.
+constexpr uint32_t kBaseMaxIters = 1u << 16;
+
+// Tunables passed to kernels.
+struct Params {
+    int k_max;
+    uint32_t base_threshold;
+    uint32_t chunk;
+    uint64_t seed;
+};
+
+// Views of the workspace and the caller's buffers for one sort.
+struct Work {
+    const uint8_t* chars;
+    const uint64_t* offsets;
+    uint32_t n;
+    uint32_t* out_perm;
+    uint32_t* out_lcp;
+
+    uint64_t* key[2];
+    uint32_t* idx[2];
+    uint32_t* counts;        // [cmax] per (segment, bucket, chunk) counts
+    uint32_t* counts_scan;   // [cmax] exclusive scan of counts
+    uint64_t* tree_lvl;      // [tmax]
+    uint64_t* tree_ino;      // [tmax]
+    SegPlan* plans;          // [lmax]
+    uint32_t* chunk_seg;     // [chmax]
+    Seg* large;              // [lmax] appended children for the next round
+    Seg* small;              // [smax]
+    uint32_t* small_size;    // [smax]
+    uint32_t* small_off;     // [smax + 1]
+    Seg* bigrun;             // [bmax]
+    uint32_t* scan_tmp;      // [scan_tmp_max]
+    Hdr* hdr;
+
+    uint32_t cmax, tmax, lmax, chmax, smax, bmax, scan_tmp_max;
+};
+
+// ------------------------------------------------------------ device helpers
+
+// Bit 7 set in exactly the zero bytes of x (no carries between bytes).
+__device__ __forceinline__ uint64_t zero_byte_mask(uint64_t x) {
+    const uint64_t lo7 = 0x7F7F7F7F7F7F7F7Full;
+    return ~(((x & lo7) + lo7) | x | lo7);
+}
+
+__device__ __forceinline__ uint64_t bswap64(uint64_t x) {
+    uint32_t lo = (uint32_t)x, hi = (uint32_t)(x >> 32);
+    return ((uint64_t)__byte_perm(lo, 0, 0x0123) << 32) | (uint64_t)__byte_perm(hi, 0, 0x0123);
+}
+
+// Key word (Sec. 3.1): bytes chars[off .. off+7] packed first-byte-most-
+// significant, bytes after the first 0 set to 0.  Reads only aligned 8-byte
+// words that hold at least one byte of the string (terminator included):
+// the second word is read only if the first holds no terminator.
+__device__ __forceinline__ uint64_t load_key(const uint8_t* __restrict__ chars, uint64_t off) {
+    const uint64_t addr = reinterpret_cast<uint64_t>(chars) + off;
+    const uint64_t* w = reinterpret_cast<const uint64_t*>(addr & ~7ull);
+    const uint32_t sh = (uint32_t)(addr & 7u) * 8u;
+    uint64_t lo = __ldg(w) >> sh;
+    if (sh) {
+        const uint64_t valid = ~0ull >> sh;  // bytes of the first word at or after off
+        if ((zero_byte_mask(lo) & valid) == 0) lo |= __ldg(w + 1) << (64u - sh);
+    }
+    const uint64_t zm = zero_byte_mask(lo);
+    if (zm) {
+        const uint32_t nb = (uint32_t)(__ffsll((long long)zm) - 1) >> 3;  // bytes before the terminator
+        lo = nb ? (lo & (~0ull >> (64u - 8u * nb))) : 0ull;
+    }
+    return bswap64(lo);
+}
+
+// LCP in bytes of two different key words (XOR + count leading zeros, Sec. 3.1).
+__device__ __forceinline__ uint32_t key_lcp(uint64_t a, uint64_t b) {
+    return (uint32_t)__clzll((long long)(a ^ b)) >> 3;
+}
+
+// A key word holds the terminator iff its last byte is 0 (bytes after the
+// terminator are 0, bytes before it are not).
+__device__ __forceinline__ bool key_ends(uint64_t k) { return (k & 0xFFull) == 0; }
+
+// Characters before the terminator in a key word that holds one.
+__device__ __forceinline__ uint32_t key_chars(uint64_t k) {
+    return k ? 8u - ((uint32_t)__ffsll((long long)k) - 1u) / 8u : 0u;
+}
+
+// Tree depth for a segment of `size` strings: about 16 strings per splitter.
+__host__ __device__ __forceinline__ int choose_k(uint32_t size, int k_max) {
+#ifdef __CUDA_ARCH__
+    int lg = 31 - __clz(size | 1u);
+#else
+    int lg = 31 - __builtin_clz(size | 1u);
+#endif
+    int k = lg - 4;
+    if (k > k_max) k = k_max;
+    if (k < 1) k = 1;
+    return k;
+}
+
+// Branch-free descent of the level-order tree t[1..v] (Sec. 3.1, i := 2i + {0,1})
+// then one equality test against the in-order array: bucket 2j + [key = x_j].
+__device__ __forceinline__ uint32_t classify_key(uint64_t key, const uint64_t* t, const uint64_t* ino, int k) {
+    uint32_t i = 1;
+    for (int l = 0; l < k; l++) i = 2u * i + (key > t[i] ? 1u : 0u);
+    const uint32_t v = (1u << k) - 1u;
+    const uint32_t j = i - (1u << k);
+    return 2u * j + ((j < v && key == ino[j]) ? 1u : 0u);
+}
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// ------------------------------------------------------------ profiling
+
+constexpr int kClasses = 10;  // matches SSS_K_CLASSES of sss.h
+enum { kInit = 0, kSample, kClassify, kScan, kScatter, kPlan, kBase, kRuns, kFixup, kLearned };
+
+// Launch counter and optional CUDA-event timing per kernel class, recorded
+// on the stream each kernel is launched on.
+struct Prof {
+    bool enabled = false;
+    uint32_t launches = 0;
+    uint32_t cls_launches[kClasses] = {};
+    std::vector<cudaEvent_t> pool;
+    std::vector<int> used_cls;
+    size_t next = 0;
+
+    void reset(bool on) {
+        enabled = on;
+        launches = 0;
+        for (int i = 0; i < kClasses; i++) cls_launches[i] = 0;
+        used_cls.clear();
+        next = 0;
+    }
+    void begin(int cls, cudaStream_t st) {
+        launches++;
+        cls_launches[cls]++;
+        if (!enabled) return;
+        while (pool.size() < next + 2) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) { enabled = false; return; }
+            pool.push_back(e);
+        }
+        cudaEventRecord(pool[next], st);
+        used_cls.push_back(cls);
+    }
+    void end(cudaStream_t st) {
+        if (!enabled) return;
+        cudaEventRecord(pool[next + 1], st);
+        next += 2;
+    }
+    // after the stream is idle: summed milliseconds per class
+    void collect(double* ms) const {
+        for (int i = 0; i < kClasses; i++) ms[i] = 0.0;
+        if (!enabled) return;
+        for (size_t i = 0; i < used_cls.size(); i++) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, pool[2 * i], pool[2 * i + 1]) == cudaSuccess) ms[used_cls[i]] += t;
+        }
+    }
+};
+
+struct ProfScope {
+    Prof* p;
+    cudaStream_t st;
+    ProfScope(Prof* p_, int cls, cudaStream_t st_) : p(p_), st(st_) { if (p) p->begin(cls, st); }
+    ~ProfScope() { if (p) p->end(st); }
+};
+
+// ------------------------------------------------------------ launches
+
+cudaError_t launch_init(const Work& w, Prof* pf, cudaStream_t st);
+// roots == nullptr: one root [0, n); else num_roots device segments (batched)
+cudaError_t launch_roots(const Work& w, const Params& p, const Seg* roots, uint32_t num_roots, Prof* pf,
+                         cudaStream_t st);
+cudaError_t launch_plan(const Work& w, const Params& p, Prof* pf, cudaStream_t st);
+cudaError_t launch_round(const Work& w, const Params& p, int cur, uint32_t L, uint32_t total_chunks,
+                         uint32_t total_counts, Prof* pf, cudaStream_t st);
+cudaError_t launch_small(const Work& w, const Params& p, int buf, uint32_t n_small, uint32_t n_bigrun,
+                         uint32_t small_total, uint32_t* out_tiles, Prof* pf, cudaStream_t st);
+cudaError_t launch_fixup(const Work& w, Prof* pf, cudaStream_t st);
+cudaError_t launch_localize(uint32_t* perm, const Seg* roots, uint32_t num_roots, Prof* pf, cudaStream_t st);
+cudaError_t launch_scan_u32(const uint32_t* in, uint32_t* out, uint32_t n, uint32_t* tmp, Prof* pf,
+                            cudaStream_t st);
+size_t scan_tmp_elems(uint32_t n);
+
+cudaError_t launch_gather_keys(const uint8_t* chars, const uint64_t* offsets, const uint32_t* idx,
+                               const uint32_t* depth, uint32_t n, uint64_t* out, cudaStream_t st);
+cudaError_t launch_build_splitters(const uint64_t* sample, uint32_t count, int k, uint64_t* lvl,
+                                   uint64_t* ino, cudaStream_t st);
+cudaError_t launch_classify(const uint64_t* keys, uint32_t n, const uint64_t* lvl, const uint64_t* ino,
+                            int k, uint16_t* out, cudaStream_t st);
+
+}  // namespace sss

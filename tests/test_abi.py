@@ -1,0 +1,78 @@
+"""The C-ABI library builds, loads and exports every entry point that
+include/sss.h declares; host-side argument checks work without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1305_1157_gb300 as sss
+from paper_1305_1157_gb300 import build as sbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    sbuild.build()
+    return sss.load()
+
+
+def declared_functions():
+    txt = open(os.path.join(ROOT, "include", "sss.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(sss_[a-z_]+)\s*\(", txt)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("sss_sort", "sss_sort_batched", "sss_sort_learned", "sss_workspace_size",
+                     "sss_get_last_stats", "sss_last_error", "sss_set_options"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_python_binding_covers_every_symbol():
+    for n in declared_functions():
+        assert callable(getattr(sss, n)), n
+
+
+def test_options_roundtrip_and_validation(lib):
+    o = sss.sss_get_options()
+    assert o.k_max == 10 and o.base_threshold == 2048 and o.chunk == 32768
+    bad = sss.sss_options.from_buffer_copy(o)
+    bad.k_max = 11
+    with pytest.raises(sss.SSSError) as e:
+        sss.sss_set_options(bad)
+    assert e.value.code == -1
+    bad = sss.sss_options.from_buffer_copy(o)
+    bad.chunk = 1000
+    with pytest.raises(sss.SSSError):
+        sss.sss_set_options(bad)
+    sss.sss_set_options(o)
+    assert sss.sss_get_options().k_max == 10
+
+
+def test_empty_input_is_a_noop(lib):
+    assert lib.sss_sort(None, None, 0, None, None, None) == 0
+
+
+def test_null_pointers_are_rejected(lib):
+    assert lib.sss_sort(None, None, 5, None, None, None) == -1
+    assert "null" in sss.sss_last_error()
+
+
+def test_bad_splitter_arguments_are_rejected(lib):
+    assert lib.sss_build_splitters(None, 3, 0, None, None, None) == -1
+    assert lib.sss_build_splitters(None, 100, 2, None, None, None) == -1
+    assert lib.sss_classify(None, 4, None, None, 11, None, None) == -1
+
+
+def test_workspace_size_grows_with_n(lib):
+    a, b = sss.sss_workspace_size(1000), sss.sss_workspace_size(1_000_000)
+    assert 0 < a < b
+    assert b >= 24 * 1_000_000  # two key and two index arrays at least
