@@ -61,17 +61,19 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=4_000_000,
                     help="strings of the workload the CPU oracle sorts for its baseline")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle child (no D, no cpu_baseline)")
+    ap.add_argument("--n", type=int, default=None,
+                    help="sort only the first n strings of the workload's generator (profiling runs)")
     return ap.parse_args()
 
 
 # ------------------------------------------------------------------ oracle child
 
-def _oracle_child(workload: str, sample: int, q):
+def _oracle_child(workload: str, sample: int, n, q):
     """Runs in a spawned process: D of the whole workload and the oracle's
     time on a bounded sample of it."""
     import oracle
     try:
-        s = gen.workload(workload)
+        s = gen.workload(workload, n=n)
         m = min(sample, s.n)
         sub = gen.workload(workload, n=m) if m < s.n else s
         t0 = time.perf_counter()
@@ -242,7 +244,7 @@ def main():
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
 
-    s = gen.workload(args.workload)
+    s = gen.workload(args.workload, n=args.n)
     n = s.n
     chars = torch.from_numpy(s.chars).to(dev)
     offsets = torch.from_numpy(s.offsets.view(np.int64)).to(dev)
