@@ -92,7 +92,7 @@ def start_oracle_child(args):
         return None, None
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
-    p = ctx.Process(target=_oracle_child, args=(args.workload, args.cpu_sample, q), daemon=True)
+    p = ctx.Process(target=_oracle_child, args=(args.workload, args.cpu_sample, args.n, q), daemon=True)
     p.start()
     return p, q
 
