@@ -122,6 +122,26 @@ int sss_sort_ws(const uint8_t* chars, const uint64_t* offsets, uint32_t n,
                 uint32_t* out_perm, uint32_t* out_lcp,
                 void* workspace, size_t workspace_bytes, void* stream);
 
+/* Allocation-free variant of sss_sort, for at most 65,536 strings.  The
+ * paper has no counterpart: it exists for callers that cannot call
+ * cudaMalloc -- code running under a framework's caching allocator that owns
+ * nearly all device memory (a stray cudaMalloc fails or fragments it),
+ * latency-critical loops (cudaMalloc and cudaFree can synchronise the whole
+ * device), or hosts whose policy forbids allocation after start-up.
+ * Scratch is a 4 MiB static device array inside this library, held by every
+ * GPU that loads the library until the process exits; the call itself
+ * allocates nothing (no cudaMalloc, cudaFree or pinned host memory; the
+ * per-round header is read into static host memory, and profiling is off).
+ * Inputs, outputs and stream as for sss_sort.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress); make that
+ * first call before any stream capture on the device.  Every call shares the
+ * one array and re-initialises what it reads, so calls that overlap on the
+ * GPU (other streams, other threads bypassing the library mutex by sharing a
+ * stream) race on it.  n above 65,536, or options whose scratch would exceed
+ * the array, return SSS_ERR_TOO_LARGE. */
+int sss_sort_noalloc(const uint8_t* chars, const uint64_t* offsets, uint32_t n,
+                     uint32_t* out_perm, uint32_t* out_lcp, void* stream);
+
 /* As sss_sort with every buffer in host memory: chars (host, chars_bytes
  * long), offsets (host), out_perm and out_lcp (host).  Copies the inputs to
  * the device, sorts, copies the results back and returns after the copy. */

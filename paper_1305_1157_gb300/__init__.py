@@ -19,7 +19,7 @@ import os
 from . import build as _build
 
 __all__ = [
-    "SSSError", "sss_sort", "sss_sort_ws", "sss_sort_host", "sss_sort_batched", "sss_sort_learned",
+    "SSSError", "sss_sort", "sss_sort_ws", "sss_sort_noalloc", "sss_sort_host", "sss_sort_batched", "sss_sort_learned",
     "sss_workspace_size", "sss_gather_keys", "sss_build_splitters", "sss_classify", "sss_cdf_loss_grad",
     "sss_set_options", "sss_get_options", "sss_get_last_stats", "sss_last_error", "sss_release",
     "sss_version", "sss_options", "sss_stats", "load", "lib_path", "sort",
@@ -75,6 +75,7 @@ _SIG = {
     "sss_workspace_size": ([ctypes.c_uint32], ctypes.c_size_t),
     "sss_sort_ws": ([_P, _P, ctypes.c_uint32, _P, _P, _P, ctypes.c_size_t, _P], ctypes.c_int),
     "sss_sort_host": ([_P, ctypes.c_uint64, _P, ctypes.c_uint32, _P, _P], ctypes.c_int),
+    "sss_sort_noalloc": ([_P, _P, ctypes.c_uint32, _P, _P, _P], ctypes.c_int),
     "sss_sort_batched": ([_P, _P, ctypes.c_uint32, _P, ctypes.c_uint32, _P, _P, _P], ctypes.c_int),
     "sss_sort_learned": ([_P, _P, ctypes.c_uint32, _P, _P, _P], ctypes.c_int),
     "sss_gather_keys": ([_P, _P, _P, _P, ctypes.c_uint32, _P, _P], ctypes.c_int),
@@ -148,6 +149,13 @@ def sss_workspace_size(n) -> int:
 def sss_sort_ws(chars, offsets, n, out_perm, out_lcp, workspace, workspace_bytes, stream=None):
     _check(load().sss_sort_ws(_addr(chars), _addr(offsets), n, _addr(out_perm), _addr(out_lcp),
                               _addr(workspace), workspace_bytes, _stream(stream)))
+
+
+def sss_sort_noalloc(chars, offsets, n, out_perm, out_lcp, stream=None):
+    """sss_sort for at most 65,536 strings without allocating: scratch is a
+    static device array of the library (see include/sss.h)."""
+    _check(load().sss_sort_noalloc(_addr(chars), _addr(offsets), n, _addr(out_perm), _addr(out_lcp),
+                                   _stream(stream)))
 
 
 def sss_sort_host(chars, chars_bytes, offsets, n, out_perm, out_lcp):

@@ -417,3 +417,53 @@ int sss_release(void) {
 const char* sss_version(void) { return "sss-gb300 0.1"; }
 
 }  // extern "C"
+
+// ------------------------------------------------------------ allocation-free sort
+//
+// sss_sort_noalloc serves callers that must not allocate device memory: its
+// scratch is one static device array of kNoAllocScratchBytes, which every GPU
+// that loads this library holds until the process exits.
+
+namespace {
+
+constexpr uint32_t kNoAllocMaxStrings = 1u << 16;
+constexpr size_t kNoAllocScratchBytes = (size_t)4 << 20;
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+void* g_noalloc_ptr[kMaxDevices];  // device address of g_noalloc_scratch, per device
+Hdr g_noalloc_hdr[kMaxDevices];    // pageable host copy of the round header, per device
+
+}  // namespace
+
+extern "C" int sss_sort_noalloc(const uint8_t* chars, const uint64_t* offsets, uint32_t n, uint32_t* out_perm,
+                                uint32_t* out_lcp, void* stream) {
+    std::lock_guard<std::mutex> g(g_mu);
+    int rc = check_options(g_opt);
+    if (rc) return rc;
+    if (n == 0) return SSS_OK;
+    if (!chars || !offsets || !out_perm || !out_lcp) return fail(SSS_ERR_INVALID, "null pointer argument");
+    if (n > kNoAllocMaxStrings)
+        return fail(SSS_ERR_TOO_LARGE, "sss_sort_noalloc sorts at most %u strings, got %u", kNoAllocMaxStrings, n);
+    const Layout L = layout_for(n, g_opt, 0);
+    if (L.total > kNoAllocScratchBytes)
+        return fail(SSS_ERR_TOO_LARGE, "%zu scratch bytes needed under the current options, %zu available",
+                    L.total, kNoAllocScratchBytes);
+    int dev = 0;
+    CK(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return fail(SSS_ERR_INVALID, "device %d out of range", dev);
+    if (!g_noalloc_ptr[dev]) {
+        // first call on this device: host code needs the array's device address
+        void* p = nullptr;
+        CK(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress(noalloc scratch)");
+        g_noalloc_ptr[dev] = p;
+    }
+    Work w = make_work(L, (char*)g_noalloc_ptr[dev], chars, offsets, n, out_perm, out_lcp);
+    sss_options o = g_opt;
+    o.profile = 0;  // no timing events
+    sss_stats stats;
+    rc = run_sort(w, o, nullptr, 0, &g_noalloc_hdr[dev], (cudaStream_t)stream, &stats);
+    if (rc) return rc;
+    g_stats = stats;
+    return SSS_OK;
+}
