@@ -54,12 +54,16 @@ typedef enum {
     SSS_ERR_INTERNAL = -6   /* a device-side consistency check failed */
 } sss_status;
 
-/* Tuning knobs.  Defaults: k_max 10, base_threshold 2048, chunk 32768,
- * seed 0x5eed, cdf_segments 4096, cdf_steps 64, cdf_lr 0.05, profile 0. */
+/* Tuning knobs.  Defaults: k_max 10, base_threshold 128, medium_threshold
+ * 8192, chunk 32768, seed 0x5eed, cdf_segments 4096, cdf_steps 64,
+ * cdf_lr 0.05, profile 0. */
 typedef struct sss_options {
-    int32_t k_max;           /* largest splitter tree depth k: v = 2^k - 1 splitters, 1..10 */
-    uint32_t base_threshold; /* buckets of at most this many strings go to the base case, 16..2048 */
-    uint32_t chunk;          /* strings per classify/scatter work item, multiple of 2048, >= 2048 */
+    int32_t k_max;             /* largest splitter tree depth k: v = 2^k - 1 splitters, 1..10 */
+    uint32_t base_threshold;   /* buckets of at most this many strings go to the base case, 16..128 */
+    uint32_t medium_threshold; /* buckets of at most this many strings get one CTA for their
+                                  next round, base_threshold..8192 */
+    uint32_t chunk;            /* largest work item (strings) of a device-wide round,
+                                  multiple of 2048 */
     uint64_t seed;           /* seed of the pseudo-random sample positions */
     uint32_t cdf_segments;   /* learned CDF: number of linear pieces, 16..4096 (power of two) */
     uint32_t cdf_steps;      /* learned CDF: gradient steps per fit */
@@ -83,7 +87,8 @@ enum {
     SSS_K_RUNS = 7,     /* large runs of equal strings */
     SSS_K_FIXUP = 8,    /* LCP at bucket boundaries, batched index rebasing */
     SSS_K_LEARNED = 9,  /* learned CDF fit and proposal */
-    SSS_K_CLASSES = 10
+    SSS_K_MEDIUM = 10,  /* one CTA per medium bucket: a whole round in shared memory */
+    SSS_K_CLASSES = 11
 };
 
 /* Statistics of the last successful sort call. */
@@ -91,6 +96,8 @@ typedef struct sss_stats {
     uint32_t rounds;                 /* distribution rounds run */
     uint32_t base_tiles;             /* base-case work tiles launched */
     uint64_t round_strings;          /* sum over rounds of strings distributed */
+    uint64_t medium_strings;         /* of those, strings in per-CTA (medium) rounds */
+    uint64_t base_iterations;        /* base-case sort passes summed over tiles */
     uint64_t base_strings;           /* strings finished by the base case */
     uint64_t run_strings;            /* strings finished as large runs of equal strings */
     uint64_t learned_keys;           /* keys the learned model proposed a bucket for */
@@ -100,7 +107,7 @@ typedef struct sss_stats {
     uint32_t profiled;               /* 1 if the prof_* fields below were measured */
     uint32_t prof_launches[SSS_K_CLASSES]; /* launches per kernel class */
     double prof_ms[SSS_K_CLASSES];   /* summed device time per kernel class (ms) */
-    uint32_t round_segments[SSS_MAX_ROUNDS_LOGGED]; /* large segments per round */
+    uint32_t round_segments[SSS_MAX_ROUNDS_LOGGED]; /* large + medium segments per round */
     uint32_t round_active[SSS_MAX_ROUNDS_LOGGED];   /* strings distributed per round */
 } sss_stats;
 

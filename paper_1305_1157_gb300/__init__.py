@@ -28,7 +28,8 @@ __all__ = [
 STATUS = {0: "SSS_OK", -1: "SSS_ERR_INVALID", -2: "SSS_ERR_NOMEM", -3: "SSS_ERR_CUDA",
           -4: "SSS_ERR_TIMEOUT", -5: "SSS_ERR_TOO_LARGE", -6: "SSS_ERR_INTERNAL"}
 MAX_ROUNDS_LOGGED = 64
-K_CLASSES = ["init", "sample", "classify", "scan", "scatter", "plan", "base", "runs", "fixup", "learned"]
+K_CLASSES = ["init", "sample", "classify", "scan", "scatter", "plan", "base", "runs", "fixup", "learned",
+             "medium"]
 
 
 class SSSError(RuntimeError):
@@ -38,14 +39,16 @@ class SSSError(RuntimeError):
 
 
 class sss_options(ctypes.Structure):
-    _fields_ = [("k_max", ctypes.c_int32), ("base_threshold", ctypes.c_uint32), ("chunk", ctypes.c_uint32),
+    _fields_ = [("k_max", ctypes.c_int32), ("base_threshold", ctypes.c_uint32),
+                ("medium_threshold", ctypes.c_uint32), ("chunk", ctypes.c_uint32),
                 ("seed", ctypes.c_uint64), ("cdf_segments", ctypes.c_uint32), ("cdf_steps", ctypes.c_uint32),
                 ("cdf_lr", ctypes.c_float), ("profile", ctypes.c_uint32)]
 
 
 class sss_stats(ctypes.Structure):
     _fields_ = [("rounds", ctypes.c_uint32), ("base_tiles", ctypes.c_uint32),
-                ("round_strings", ctypes.c_uint64), ("base_strings", ctypes.c_uint64),
+                ("round_strings", ctypes.c_uint64), ("medium_strings", ctypes.c_uint64),
+                ("base_iterations", ctypes.c_uint64), ("base_strings", ctypes.c_uint64),
                 ("run_strings", ctypes.c_uint64), ("learned_keys", ctypes.c_uint64),
                 ("learned_misses", ctypes.c_uint64), ("refilled_strings", ctypes.c_uint64),
                 ("launches", ctypes.c_uint32), ("profiled", ctypes.c_uint32),
@@ -57,6 +60,7 @@ class sss_stats(ctypes.Structure):
     def as_dict(self):
         r = self.rounds
         return {"rounds": r, "base_tiles": self.base_tiles, "round_strings": self.round_strings,
+                "medium_strings": self.medium_strings, "base_iterations": self.base_iterations,
                 "base_strings": self.base_strings, "run_strings": self.run_strings,
                 "learned_keys": self.learned_keys, "learned_misses": self.learned_misses,
                 "refilled_strings": self.refilled_strings, "launches": self.launches,

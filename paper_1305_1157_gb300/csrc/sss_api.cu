@@ -22,7 +22,7 @@ using namespace sss;
 namespace {
 
 std::mutex g_mu;
-sss_options g_opt = {10, 2048u, 32768u, 0x5eedull, 4096u, 64u, 0.05f, 0u};
+sss_options g_opt = {10, 128u, 8192u, 32768u, 0x5eedull, 4096u, 64u, 0.05f, 0u};
 sss_stats g_stats;
 Prof g_prof;
 char g_err[512] = "no error";
@@ -61,23 +61,50 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 struct Layout {
     size_t total = 0;
     size_t o_key0, o_key1, o_idx0, o_idx1, o_counts, o_counts_scan, o_tlvl, o_tino, o_plans, o_chunk_seg,
-        o_large, o_small, o_small_size, o_small_off, o_bigrun, o_scan_tmp, o_hdr, o_roots;
-    uint32_t cmax, tmax, lmax, chmax, smax, bmax, scan_tmp_max;
+        o_large, o_med0, o_med1, o_small, o_small_size, o_small_off, o_bigrun, o_scan_tmp, o_hdr, o_roots;
+    uint32_t cmax, tmax, lmax, chmax, smax, bmax, scan_tmp_max, mmax;
 };
+
+uint32_t g_sms = 0;  // SM count of the first device used (sizes the count matrix)
+
+uint32_t sms_for_layout() {
+    if (!g_sms) {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+            g_sms = (uint32_t)sms;
+        else
+            g_sms = 160;  // no device (host-only size query): a bound above GB300's 152
+        cudaGetLastError();
+    }
+    return g_sms;
+}
 
 Layout layout_for(uint32_t n, const sss_options& o, uint32_t num_roots) {
     Layout L;
     const uint64_t nn = n ? n : 1;
     const uint64_t T = o.base_threshold;
-    const uint64_t lmax = nn / (T + 1) + 2;
-    const uint64_t chmax = nn / o.chunk + lmax + 1;
-    const uint64_t cmax = (uint64_t)kNBMax * (nn / o.chunk + 1) + nn / 4 + 64;
-    const uint64_t tmax = 2 * lmax + nn / 16 + 64;
+    const uint64_t M = o.medium_threshold;
+    const uint64_t sms = sms_for_layout();
+    // large segments exceed M strings; device-wide rounds use at least
+    // ceil(total / (sms * kChunksPerSM)) strings per chunk, so their chunks
+    // number at most sms * kChunksPerSM + (one partial chunk per segment)
+    const uint64_t lmax = nn / (M + 1) + 2;
+    // chunks are >= max(ceil(total / (sms * kChunksPerSM)), kSubTile) strings
+    // unless capped by the chunk option
+    uint64_t full_chunks = sms * kChunksPerSM;
+    if (full_chunks < nn / o.chunk + 1) full_chunks = nn / o.chunk + 1;
+    if (full_chunks > nn / kSubTile + 1) full_chunks = nn / kSubTile + 1;
+    const uint64_t chmax = full_chunks + lmax + 1;
+    const uint64_t cmax = (uint64_t)kNBMax * chmax + 64;
+    const uint64_t tmax = nn / 16 + 2 * lmax + 64;  // 2^k <= size / 16 per segment
+    const uint64_t mmax = nn / (T + 1) + 2;
     const uint64_t smax = nn / 2 + num_roots + 2;
     const uint64_t bmax = nn / (T + 1) + 2;
     const uint64_t scan_tmp = scan_tmp_elems((uint32_t)(cmax > smax ? cmax : smax)) + 1;
     L.cmax = (uint32_t)cmax; L.tmax = (uint32_t)tmax; L.lmax = (uint32_t)lmax; L.chmax = (uint32_t)chmax;
     L.smax = (uint32_t)smax; L.bmax = (uint32_t)bmax; L.scan_tmp_max = (uint32_t)scan_tmp;
+    L.mmax = (uint32_t)mmax;
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t r = off; off = align_up(off + bytes, 256); return r; };
     L.o_key0 = take(8 * nn);
@@ -91,6 +118,8 @@ Layout layout_for(uint32_t n, const sss_options& o, uint32_t num_roots) {
     L.o_plans = take(sizeof(SegPlan) * lmax);
     L.o_chunk_seg = take(4 * chmax);
     L.o_large = take(sizeof(Seg) * lmax);
+    L.o_med0 = take(sizeof(Seg) * mmax);
+    L.o_med1 = take(sizeof(Seg) * mmax);
     L.o_small = take(sizeof(Seg) * smax);
     L.o_small_size = take(4 * smax);
     L.o_small_off = take(4 * (smax + 1));
@@ -118,6 +147,8 @@ Work make_work(const Layout& L, char* ws, const uint8_t* chars, const uint64_t* 
     w.plans = (SegPlan*)(ws + L.o_plans);
     w.chunk_seg = (uint32_t*)(ws + L.o_chunk_seg);
     w.large = (Seg*)(ws + L.o_large);
+    w.med[0] = (Seg*)(ws + L.o_med0);
+    w.med[1] = (Seg*)(ws + L.o_med1);
     w.small = (Seg*)(ws + L.o_small);
     w.small_size = (uint32_t*)(ws + L.o_small_size);
     w.small_off = (uint32_t*)(ws + L.o_small_off);
@@ -125,7 +156,7 @@ Work make_work(const Layout& L, char* ws, const uint8_t* chars, const uint64_t* 
     w.scan_tmp = (uint32_t*)(ws + L.o_scan_tmp);
     w.hdr = (Hdr*)(ws + L.o_hdr);
     w.cmax = L.cmax; w.tmax = L.tmax; w.lmax = L.lmax; w.chmax = L.chmax;
-    w.smax = L.smax; w.bmax = L.bmax; w.scan_tmp_max = L.scan_tmp_max;
+    w.smax = L.smax; w.bmax = L.bmax; w.scan_tmp_max = L.scan_tmp_max; w.mmax = L.mmax;
     return w;
 }
 
@@ -133,6 +164,8 @@ int check_options(const sss_options& o) {
     if (o.k_max < 1 || o.k_max > kKMax) return fail(SSS_ERR_INVALID, "k_max must be in 1..%d", kKMax);
     if (o.base_threshold < 16 || o.base_threshold > kBaseMax)
         return fail(SSS_ERR_INVALID, "base_threshold must be in 16..%u", kBaseMax);
+    if (o.medium_threshold < o.base_threshold || o.medium_threshold > kMedMax)
+        return fail(SSS_ERR_INVALID, "medium_threshold must be in base_threshold..%u", kMedMax);
     if (o.chunk < kSubTile || o.chunk % kSubTile) return fail(SSS_ERR_INVALID, "chunk must be a positive multiple of %u", kSubTile);
     if (o.cdf_segments < 16 || o.cdf_segments > 4096 || (o.cdf_segments & (o.cdf_segments - 1)))
         return fail(SSS_ERR_INVALID, "cdf_segments must be a power of two in 16..4096");
@@ -171,7 +204,7 @@ int read_hdr(Hdr* hh, const Work& w, cudaStream_t st) {
 // The whole sort on an initialised Work (see the file comment).
 int run_sort(const Work& w, const sss_options& o, const Seg* roots_dev, uint32_t num_roots, Hdr* hh,
              cudaStream_t st, sss_stats* stats) {
-    Params p{o.k_max, o.base_threshold, o.chunk, o.seed};
+    Params p{o.k_max, o.base_threshold, o.medium_threshold, o.chunk, o.seed, device_sms(), 0u};
     Prof* pf = &g_prof;
     pf->reset(o.profile != 0);
     memset(stats, 0, sizeof(*stats));
@@ -180,34 +213,37 @@ int run_sort(const Work& w, const sss_options& o, const Seg* roots_dev, uint32_t
     CK(launch_plan(w, p, pf, st), "plan");
     int rc = read_hdr(hh, w, st);
     if (rc) return rc;
-    int cur = 0, small_buf = 0;
+    int cur = 0, small_buf = 0, med_in = 0;
     for (uint32_t round = 0;; round++) {
         uint32_t tiles = 0;
         CK(launch_small(w, p, small_buf, hh->n_small_snap, hh->n_bigrun_snap, hh->small_elems_snap, &tiles, pf, st),
            "base case");
         stats->base_tiles += tiles;
         stats->base_strings += hh->small_elems_snap;
-        if (hh->L == 0) break;
+        if (hh->L == 0 && hh->n_med_snap == 0) break;
         if (round >= 1u << 22) return fail(SSS_ERR_INTERNAL, "round limit exceeded");
         if (round < SSS_MAX_ROUNDS_LOGGED) {
-            stats->round_segments[round] = hh->L;
-            stats->round_active[round] = hh->large_elems_snap;
+            stats->round_segments[round] = hh->L + hh->n_med_snap;
+            stats->round_active[round] = hh->large_elems_snap + hh->med_elems_snap;
         }
         stats->rounds++;
-        stats->round_strings += hh->large_elems_snap;
-        CK(launch_round(w, p, cur, hh->L, hh->total_chunks, hh->total_counts, pf, st), "round");
+        stats->round_strings += (uint64_t)hh->large_elems_snap + hh->med_elems_snap;
+        stats->medium_strings += hh->med_elems_snap;
+        CK(launch_round(w, p, cur, hh->L, hh->total_chunks, hh->total_counts, hh->n_med_snap, med_in, pf, st),
+           "round");
         CK(launch_plan(w, p, pf, st), "plan");
         rc = read_hdr(hh, w, st);
         if (rc) return rc;
         small_buf = cur ^ 1;
         cur ^= 1;
+        med_in ^= 1;
     }
     CK(launch_fixup(w, pf, st), "lcp fixup");
     if (roots_dev) CK(launch_localize(w.out_perm, roots_dev, num_roots, pf, st), "localize");
     rc = read_hdr(hh, w, st);
     if (rc) return rc;
     stats->refilled_strings = hh->refills;
-    stats->run_strings = stats->round_strings ? 0 : 0;
+    stats->base_iterations = hh->base_iters;
     stats->launches = pf->launches;
     stats->profiled = pf->enabled ? 1u : 0u;
     for (int i = 0; i < kClasses; i++) stats->prof_launches[i] = pf->cls_launches[i];

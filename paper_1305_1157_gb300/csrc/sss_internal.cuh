@@ -16,8 +16,13 @@ constexpr int kKMax = 10;                       // deepest splitter tree
 constexpr int kVMax = (1 << kKMax) - 1;         // 1023 splitters
 constexpr int kNBMax = 2 * kVMax + 1;           // 2047 buckets (Sec. 3.1: k = 2v + 1)
 constexpr int kSampleMax = 1 << (kKMax + 1);    // sample buffer, 2v + 1 keys padded to 2^(k+1)
-constexpr uint32_t kBaseMax = 2048;             // largest base-case bucket
-constexpr uint32_t kBaseCap = 2 * kBaseMax;     // slots of one base-case tile
+constexpr int kBaseE = 8;                       // base case: slots per lane
+constexpr uint32_t kBaseCap = 32u * kBaseE;     // slots of one warp tile (256)
+constexpr uint32_t kBaseMax = kBaseCap / 2;     // largest base-case bucket (128)
+constexpr uint32_t kMedMax = 8192;              // largest bucket one CTA distributes alone
+constexpr int kMedKMax = 9;                     // its deepest tree: choose_k(8192) = 9
+constexpr int kMedNB = (2 << kMedKMax) - 1;     // 1023 buckets
+constexpr int kChunksPerSM = 8;                 // device-wide rounds: target work items per SM
 constexpr int kScatterThreads = 256;
 constexpr int kScatterItems = 8;
 constexpr uint32_t kSubTile = kScatterThreads * kScatterItems;  // 2048 strings
@@ -33,20 +38,24 @@ struct Seg {
     uint32_t begin, size, depth, aux;
 };
 
-// A large segment's layout for one distribution round.
+// A large segment's layout for one device-wide distribution round.
 struct SegPlan {
     uint32_t begin, size, depth, k;     // v = 2^k - 1 splitters, 2^(k+1) - 1 buckets
     uint32_t chunks, chunk_base;        // work items of this segment
     uint32_t count_base, tree_base;     // offsets into the count matrix and the trees
+    uint32_t chunk, pad0, pad1, pad2;   // strings per work item in this round
 };
 
 // Device header: live append counters and the snapshot the host reads back.
 struct Hdr {
-    uint32_t n_large, n_small, n_bigrun, err, small_elems;          // live
-    uint32_t L, total_chunks, total_counts, total_tree;             // next round
-    uint32_t n_small_snap, n_bigrun_snap, small_elems_snap, large_elems_snap;
-    uint32_t pad[3];
-    unsigned long long refills;                                     // key words gathered in rounds
+    // live, appended to by the round kernels
+    uint32_t n_large, n_med, n_small, n_bigrun, err, small_elems, med_elems, pad0;
+    // snapshot for the host, written by k_plan
+    uint32_t L, total_chunks, total_counts, total_tree;
+    uint32_t n_med_snap, n_small_snap, n_bigrun_snap, small_elems_snap;
+    uint32_t large_elems_snap, med_elems_snap, chunk, pad1;
+    unsigned long long refills;   // key words gathered in rounds
+    unsigned long long base_iters;  // base-case refill iterations summed over tiles
 };
 
 // err bits
@@ -57,6 +66,7 @@ constexpr uint32_t kErrEqualBoundary = 1u << 3;
 constexpr uint32_t kErrPlanOverflow = 1u << 4;
 constexpr uint32_t kErrPosition = 1u << 5;
 constexpr uint32_t kErrBaseIters = 1u << 6;
+constexpr uint32_t kErrMedOverflow = 1u << 7;
 
 // Refill steps a base-case tile may take (each moves 8 bytes deeper): a
 // common prefix of 512 KiB inside one small bucket.
@@ -65,9 +75,12 @@ constexpr uint32_t kBaseMaxIters = 1u << 16;
 // Tunables passed to kernels.
 struct Params {
     int k_max;
-    uint32_t base_threshold;
-    uint32_t chunk;
+    uint32_t base_threshold;  // <= kBaseMax: bucket goes to the warp-tile base case
+    uint32_t med_threshold;   // <= kMedMax: bucket gets one CTA for its next round
+    uint32_t chunk;           // largest work item of a device-wide round
     uint64_t seed;
+    uint32_t num_sms;
+    uint32_t pad;
 };
 
 // Views of the workspace and the caller's buffers for one sort.
@@ -86,7 +99,8 @@ struct Work {
     uint64_t* tree_ino;      // [tmax]
     SegPlan* plans;          // [lmax]
     uint32_t* chunk_seg;     // [chmax]
-    Seg* large;              // [lmax] appended children for the next round
+    Seg* large;              // [lmax] children for the next device-wide round
+    Seg* med[2];             // [mmax] children for the next per-CTA round (alternating)
     Seg* small;              // [smax]
     uint32_t* small_size;    // [smax]
     uint32_t* small_off;     // [smax + 1]
@@ -94,7 +108,7 @@ struct Work {
     uint32_t* scan_tmp;      // [scan_tmp_max]
     Hdr* hdr;
 
-    uint32_t cmax, tmax, lmax, chmax, smax, bmax, scan_tmp_max;
+    uint32_t cmax, tmax, lmax, chmax, smax, bmax, scan_tmp_max, mmax;
 };
 
 // ------------------------------------------------------------ device helpers
@@ -176,8 +190,8 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
 
 // ------------------------------------------------------------ profiling
 
-constexpr int kClasses = 10;  // matches SSS_K_CLASSES of sss.h
-enum { kInit = 0, kSample, kClassify, kScan, kScatter, kPlan, kBase, kRuns, kFixup, kLearned };
+constexpr int kClasses = 11;  // matches SSS_K_CLASSES of sss.h
+enum { kInit = 0, kSample, kClassify, kScan, kScatter, kPlan, kBase, kRuns, kFixup, kLearned, kMedium };
 
 // Launch counter and optional CUDA-event timing per kernel class, recorded
 // on the stream each kernel is launched on.
@@ -238,8 +252,10 @@ cudaError_t launch_init(const Work& w, Prof* pf, cudaStream_t st);
 cudaError_t launch_roots(const Work& w, const Params& p, const Seg* roots, uint32_t num_roots, Prof* pf,
                          cudaStream_t st);
 cudaError_t launch_plan(const Work& w, const Params& p, Prof* pf, cudaStream_t st);
+// device-wide kernels for the L planned segments and one CTA per segment of
+// med list med_in; children go to lists (med list med_in ^ 1)
 cudaError_t launch_round(const Work& w, const Params& p, int cur, uint32_t L, uint32_t total_chunks,
-                         uint32_t total_counts, Prof* pf, cudaStream_t st);
+                         uint32_t total_counts, uint32_t n_med, int med_in, Prof* pf, cudaStream_t st);
 cudaError_t launch_small(const Work& w, const Params& p, int buf, uint32_t n_small, uint32_t n_bigrun,
                          uint32_t small_total, uint32_t* out_tiles, Prof* pf, cudaStream_t st);
 cudaError_t launch_fixup(const Work& w, Prof* pf, cudaStream_t st);
@@ -247,6 +263,7 @@ cudaError_t launch_localize(uint32_t* perm, const Seg* roots, uint32_t num_roots
 cudaError_t launch_scan_u32(const uint32_t* in, uint32_t* out, uint32_t n, uint32_t* tmp, Prof* pf,
                             cudaStream_t st);
 size_t scan_tmp_elems(uint32_t n);
+uint32_t device_sms();
 
 cudaError_t launch_gather_keys(const uint8_t* chars, const uint64_t* offsets, const uint32_t* idx,
                                const uint32_t* depth, uint32_t n, uint64_t* out, cudaStream_t st);

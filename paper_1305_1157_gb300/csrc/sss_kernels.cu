@@ -1,25 +1,28 @@
-// Distribution-round kernels of super scalar string sample sort (S^5,
-// Sec. 3.1 of Bingmann & Sanders) for sm_103a.
+// Kernels of super scalar string sample sort (S^5, Sec. 3.1 of Bingmann &
+// Sanders) for sm_103a.
 //
-// One round over all large segments at once:
-//   k_sample    one CTA per segment: pseudo-random sample of 2v+1 key
-//               words, in-shared-memory sort, recursive duplicate-skipping
-//               splitter choice, perfect tree in level order + in order
-//   k_classify  one CTA per work chunk: tree in shared memory, branch-free
-//               descent + one equality test per key, warp-aggregated
-//               shared-memory histogram, per-chunk bucket counts out
-//   scan        exclusive prefix sum over the bucket-major count matrix
-//   k_scatter   one CTA per chunk: classifies again, stable rank of each
-//               string inside its bucket (warp match + per-warp counters),
-//               out-of-place move into the shadow arrays (the two arrays swap
-//               roles each round), new key word gathered where the common
-//               prefix grows; chunk 0 of every segment turns its buckets
-//               into child segments (Eq. (1) depth rule) and marks the
-//               bucket boundaries whose LCP is resolved at the end
-//   k_plan      one CTA: lays out the next round (tree depth per segment,
-//               work chunks, count-matrix offsets)
-// Buckets of at most base_threshold strings go to k_base, a shared-memory
-// segmented sort that also emits the LCP entries.
+// Segments (ranges of the working arrays whose strings share a prefix of
+// `depth` bytes) are handled by size class, after the paper's split into
+// fully parallel S^5, sequential S^5 and a base case (Sec. 3.1
+// "Parallelization of S^5"):
+//
+//   large  (> med_threshold)  device-wide round, all such segments at once:
+//          k_sample (one CTA per segment: sample, sort, splitter tree),
+//          k_classify (one CTA per work chunk: tree in shared memory,
+//          descent, warp-aggregated histogram), exclusive scan of the
+//          bucket-major count matrix, k_scatter (one CTA per chunk: stable
+//          move into the shadow arrays, key refill, child segments)
+//   medium (> base_threshold) k_med_round: one CTA runs a whole round for
+//          its segment in shared memory (sample, tree, classify into a
+//          bucket array, local scan, stable move, child segments)
+//   small  (<= base_threshold) k_base_warp: one warp sorts a tile of packed
+//          small segments in registers by (run, key word, index), moving
+//          runs of equal key words 8 bytes deeper until all are decided,
+//          and writes out_perm and the LCP entries
+//
+// Between rounds k_plan lays out the next device-wide round.  Equality
+// buckets whose splitter ends the string are finished runs (k_bigrun when
+// large); k_fixup resolves the LCP at bucket boundaries at the end.
 #include "sss_internal.cuh"
 
 namespace sss {
@@ -67,6 +70,71 @@ __device__ uint32_t block_excl_sum(uint32_t x, uint32_t* wsum, uint32_t* total) 
     return r;
 }
 
+// ------------------------------------------------------------ child segments
+
+// Where a bucket of `size` strings goes next (Sec. 3.1 "Parallelization of
+// S^5": size classes).  isrun: all its strings are equal (finished).
+__device__ __forceinline__ void append_child(const Work& w, const Params& p, int med_out, uint32_t start,
+                                             uint32_t size, uint32_t cdepth, bool isrun, uint32_t runlcp) {
+    Hdr* h = w.hdr;
+    if (size <= 1) return;
+    if (isrun && size > p.base_threshold) {
+        uint32_t s = atomicAdd(&h->n_bigrun, 1u);
+        if (s < w.bmax) w.bigrun[s] = Seg{start, size, cdepth, runlcp};
+        else atomicOr(&h->err, kErrRunOverflow);
+    } else if (size <= p.base_threshold) {
+        uint32_t s = atomicAdd(&h->n_small, 1u);
+        if (s < w.smax) {
+            w.small[s] = Seg{start, size, cdepth, 0u};
+            w.small_size[s] = size;
+            atomicAdd(&h->small_elems, size);
+        } else {
+            atomicOr(&h->err, kErrSmallOverflow);
+        }
+    } else if (size <= p.med_threshold) {
+        uint32_t s = atomicAdd(&h->n_med, 1u);
+        if (s < w.mmax) {
+            w.med[med_out][s] = Seg{start, size, cdepth, 0u};
+            atomicAdd(&h->med_elems, size);
+        } else {
+            atomicOr(&h->err, kErrMedOverflow);
+        }
+    } else {
+        uint32_t s = atomicAdd(&h->n_large, 1u);
+        if (s < w.lmax) w.large[s] = Seg{start, size, cdepth, 0u};
+        else atomicOr(&h->err, kErrLargeOverflow);
+    }
+}
+
+// Child depth of bucket b of a segment at depth `depth` (Eq. (1), Sec. 3.1):
+// b_0 and b_2v keep it, the equality bucket of x_i adds w = 8 (or is a run of
+// equal strings when x_i holds the terminator), an inner even bucket adds
+// lcp(x_{i-1}, x_i).
+struct BucketInfo {
+    uint32_t cdepth, runlcp;
+    bool isrun;
+};
+
+__device__ __forceinline__ BucketInfo bucket_info(uint32_t b, uint32_t nb, uint32_t depth, const uint64_t* ino,
+                                                  uint32_t size) {
+    BucketInfo bi{depth, 0u, false};
+    if (b & 1u) {
+        const uint64_t x = ino[b >> 1];
+        if (key_ends(x)) { bi.isrun = true; bi.runlcp = depth + key_chars(x); }
+        else bi.cdepth = depth + 8u;
+    } else if (b != 0 && b != nb - 1 && size > 0) {
+        const uint32_t i = b >> 1;
+        bi.cdepth = depth + key_lcp(ino[i - 1], ino[i]);
+    }
+    return bi;
+}
+
+// What the scatter does with a string of the bucket: finish it (single),
+// copy its key word, or gather the word at the child's depth.
+__device__ __forceinline__ uint32_t refill_code(const BucketInfo& bi, uint32_t size, uint32_t depth) {
+    return size == 1 ? kSingle : ((size == 0 || bi.isrun || bi.cdepth == depth) ? kNoRefill : bi.cdepth);
+}
+
 // ------------------------------------------------------------ init
 
 __global__ void k_init(Work w) {
@@ -80,32 +148,25 @@ __global__ void k_init(Work w) {
 
 __global__ void k_hdr_reset(Work w) {
     Hdr* h = w.hdr;
-    h->n_large = 0; h->n_small = 0; h->n_bigrun = 0; h->err = 0; h->small_elems = 0;
+    h->n_large = 0; h->n_med = 0; h->n_small = 0; h->n_bigrun = 0; h->err = 0;
+    h->small_elems = 0; h->med_elems = 0;
     h->refills = 0ull;
+    h->base_iters = 0ull;
 }
 
-// Roots: one segment per set (a single sort is one set).  Set j occupies
-// [roots[j].begin, +size) at depth 0; singletons finish here.
-__global__ void k_roots(Work w, const Seg* roots, uint32_t num_roots, Seg single, uint32_t base_threshold) {
-    Hdr* h = w.hdr;
+// Roots: one segment per set (a single sort is one set) at depth 0.
+__global__ void k_roots(Work w, Params p, const Seg* roots, uint32_t num_roots, Seg single) {
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < num_roots; j += gridDim.x * blockDim.x) {
         const Seg g = roots ? roots[j] : single;
-        if (g.size == 0) continue;
-        if (g.size == 1) {
-            w.out_perm[g.begin] = g.begin;
-        } else if (g.size > base_threshold) {
-            uint32_t s = atomicAdd(&h->n_large, 1u);
-            if (s < w.lmax) w.large[s] = g; else atomicOr(&h->err, kErrLargeOverflow);
-        } else {
-            uint32_t s = atomicAdd(&h->n_small, 1u);
-            if (s < w.smax) { w.small[s] = g; w.small_size[s] = g.size; atomicAdd(&h->small_elems, g.size); }
-            else atomicOr(&h->err, kErrSmallOverflow);
-        }
+        if (g.size == 1) w.out_perm[g.begin] = g.begin;
+        else append_child(w, p, 0, g.begin, g.size, 0u, false, 0u);
     }
 }
 
 // ------------------------------------------------------------ plan
 
+// One CTA: layout of the next device-wide round.  The chunk size is chosen so
+// that the round has about kChunksPerSM work items per SM.
 __global__ void __launch_bounds__(1024) k_plan(Work w, Params p) {
     __shared__ uint32_t wsum[33];
     Hdr* h = w.hdr;
@@ -113,28 +174,34 @@ __global__ void __launch_bounds__(1024) k_plan(Work w, Params p) {
     const uint32_t L = min(L_all, w.lmax);
     const uint32_t per = (L + blockDim.x - 1) / blockDim.x;
     const uint32_t lo = min(L, threadIdx.x * per), hi = min(L, lo + per);
-    uint32_t sc = 0, sn = 0, st = 0, sa = 0;
+    uint32_t sa = 0;
+    for (uint32_t s = lo; s < hi; s++) sa += w.large[s].size;
+    uint32_t ta;
+    block_excl_sum(sa, wsum, &ta);
+    const uint32_t target = max(1u, p.num_sms * (uint32_t)kChunksPerSM);
+    uint32_t chunk = (uint32_t)(((uint64_t)ta + target - 1) / target);
+    chunk = (chunk + kSubTile - 1) / kSubTile * kSubTile;
+    chunk = min(max(chunk, kSubTile), p.chunk);
+    uint32_t sc = 0, sn = 0, st = 0;
     for (uint32_t s = lo; s < hi; s++) {
-        Seg g = w.large[s];
-        int k = choose_k(g.size, p.k_max);
-        uint32_t ch = (g.size + p.chunk - 1) / p.chunk;
+        const Seg g = w.large[s];
+        const int k = choose_k(g.size, p.k_max);
+        const uint32_t ch = (g.size + chunk - 1) / chunk;
         sc += ch;
         sn += ((2u << k) - 1u) * ch;
         st += 1u << k;
-        sa += g.size;
     }
-    uint32_t tc, tn, tt, ta;
+    uint32_t tc, tn, tt;
     uint32_t bc = block_excl_sum(sc, wsum, &tc);
     uint32_t bn = block_excl_sum(sn, wsum, &tn);
     uint32_t bt = block_excl_sum(st, wsum, &tt);
-    block_excl_sum(sa, wsum, &ta);
     const bool ok = tc <= w.chmax && tn <= w.cmax && tt <= w.tmax && L_all <= w.lmax;
     if (ok) {
         for (uint32_t s = lo; s < hi; s++) {
-            Seg g = w.large[s];
-            int k = choose_k(g.size, p.k_max);
-            uint32_t ch = (g.size + p.chunk - 1) / p.chunk;
-            w.plans[s] = SegPlan{g.begin, g.size, g.depth, (uint32_t)k, ch, bc, bn, bt};
+            const Seg g = w.large[s];
+            const int k = choose_k(g.size, p.k_max);
+            const uint32_t ch = (g.size + chunk - 1) / chunk;
+            w.plans[s] = SegPlan{g.begin, g.size, g.depth, (uint32_t)k, ch, bc, bn, bt, chunk, 0u, 0u, 0u};
             for (uint32_t c = 0; c < ch; c++) w.chunk_seg[bc + c] = s;
             bc += ch;
             bn += ((2u << k) - 1u) * ch;
@@ -148,14 +215,19 @@ __global__ void __launch_bounds__(1024) k_plan(Work w, Params p) {
         h->total_chunks = ok ? tc : 0u;
         h->total_counts = ok ? tn : 0u;
         h->total_tree = ok ? tt : 0u;
+        h->chunk = chunk;
         h->large_elems_snap = ok ? ta : 0u;
+        h->n_med_snap = min(h->n_med, w.mmax);
+        h->med_elems_snap = h->med_elems;
         h->n_small_snap = h->n_small;
         h->n_bigrun_snap = h->n_bigrun;
         h->small_elems_snap = h->small_elems;
         h->n_large = 0;
+        h->n_med = 0;
         h->n_small = 0;
         h->n_bigrun = 0;
         h->small_elems = 0;
+        h->med_elems = 0;
     }
 }
 
@@ -232,7 +304,8 @@ __device__ void select_splitters(const uint64_t* s, uint32_t cnt, int k, uint64_
     }
 }
 
-// Writes the tree lvl[1..v] to out_lvl[0..v) and its in-order sequence to out_ino[0..v).
+// Writes the tree lvl[1..v] to out_lvl[0..v) and its in-order sequence to
+// out_ino[0..v).  Ends with __syncthreads.
 __device__ void emit_tree(const uint64_t* lvl, int k, uint64_t* out_lvl, uint64_t* out_ino) {
     const uint32_t v = (1u << k) - 1u;
     for (uint32_t i = 1 + threadIdx.x; i <= v; i += blockDim.x) {
@@ -242,6 +315,15 @@ __device__ void emit_tree(const uint64_t* lvl, int k, uint64_t* out_lvl, uint64_
         out_lvl[i - 1] = lvl[i];
         out_ino[pos] = lvl[i];
     }
+    __syncthreads();
+}
+
+// Pseudo-random sample position j of a segment (Sec. 3.1: the sample is drawn
+// pseudo-randomly).
+__device__ __forceinline__ uint32_t sample_pos(uint64_t seed, uint32_t begin, uint32_t size, uint32_t j) {
+    const uint64_t base = seed ^ ((uint64_t)begin * 0x9E3779B97F4A7C15ull) ^ ((uint64_t)size << 32);
+    const uint32_t r = (uint32_t)(mix64(base + (uint64_t)j * 0xD1B54A32D192ED03ull) >> 32);
+    return (uint32_t)(((uint64_t)r * size) >> 32);
 }
 
 __global__ void __launch_bounds__(1024) k_sample(Work w, Params p, int cur) {
@@ -253,16 +335,8 @@ __global__ void __launch_bounds__(1024) k_sample(Work w, Params p, int cur) {
     const uint32_t pw = 2u << k;
     const uint32_t cnt = pw - 1u;  // alpha (v + 1) - 1 with alpha = 2
     const uint64_t* keys = w.key[cur];
-    const uint64_t base = p.seed ^ ((uint64_t)P.begin * 0x9E3779B97F4A7C15ull) ^ ((uint64_t)P.size << 32);
-    for (uint32_t j = threadIdx.x; j < pw; j += blockDim.x) {
-        uint64_t x = ~0ull;
-        if (j < cnt) {
-            uint32_t r = (uint32_t)(mix64(base + (uint64_t)j * 0xD1B54A32D192ED03ull) >> 32);
-            uint32_t off = (uint32_t)(((uint64_t)r * P.size) >> 32);
-            x = keys[P.begin + off];
-        }
-        samp[j] = x;
-    }
+    for (uint32_t j = threadIdx.x; j < pw; j += blockDim.x)
+        samp[j] = j < cnt ? keys[P.begin + sample_pos(p.seed, P.begin, P.size, j)] : ~0ull;
     __syncthreads();
     bitonic_sort_u64(samp, pw);
     select_splitters(samp, cnt, k, lvl, ra, rb);
@@ -289,6 +363,31 @@ __global__ void __launch_bounds__(1024) k_build_splitters(const uint64_t* sample
 constexpr int kClassifyThreads = 256;
 constexpr int kClassifyUnroll = 4;
 
+// Adds the buckets of keys[lo, hi) to hist (warp-aggregated shared atomics);
+// bid (optional) receives each bucket at bid[e - lo].  Loop bounds are
+// uniform over the block.
+__device__ __forceinline__ void classify_range(const uint64_t* __restrict__ keys, uint32_t lo, uint32_t hi,
+                                               const uint64_t* t, const uint64_t* ino, int k, uint32_t nb,
+                                               uint32_t* hist, uint16_t* bid) {
+    const uint32_t lane = threadIdx.x & 31u;
+    for (uint32_t base = lo; base < hi; base += blockDim.x * kClassifyUnroll) {
+        uint64_t kk[kClassifyUnroll];
+#pragma unroll
+        for (int u = 0; u < kClassifyUnroll; u++) {
+            const uint32_t e = base + u * blockDim.x + threadIdx.x;
+            kk[u] = e < hi ? keys[e] : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < kClassifyUnroll; u++) {
+            const uint32_t e = base + u * blockDim.x + threadIdx.x;
+            const uint32_t b = e < hi ? classify_key(kk[u], t, ino, k) : nb;
+            if (bid && e < hi) bid[e - lo] = (uint16_t)b;
+            const uint32_t peers = __match_any_sync(FULL_MASK, b);
+            if (lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&hist[b], (uint32_t)__popc(peers));
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kClassifyThreads) k_classify(Work w, Params p, int cur) {
     __shared__ uint64_t t[kVMax + 1];
     __shared__ uint64_t ino[kVMax];
@@ -305,63 +404,138 @@ __global__ void __launch_bounds__(kClassifyThreads) k_classify(Work w, Params p,
     }
     for (uint32_t b = threadIdx.x; b <= nb; b += blockDim.x) hist[b] = 0;
     __syncthreads();
-    const uint32_t lo = P.begin + ci * p.chunk;
-    const uint32_t hi = min(lo + p.chunk, P.begin + P.size);
-    const uint64_t* keys = w.key[cur];
-    const uint32_t lane = threadIdx.x & 31u;
-    for (uint32_t base = lo; base < hi; base += kClassifyThreads * kClassifyUnroll) {
-        uint64_t kk[kClassifyUnroll];
-#pragma unroll
-        for (int u = 0; u < kClassifyUnroll; u++) {
-            uint32_t e = base + u * kClassifyThreads + threadIdx.x;
-            kk[u] = e < hi ? keys[e] : 0ull;
-        }
-#pragma unroll
-        for (int u = 0; u < kClassifyUnroll; u++) {
-            uint32_t e = base + u * kClassifyThreads + threadIdx.x;
-            uint32_t b = e < hi ? classify_key(kk[u], t, ino, k) : nb;
-            uint32_t peers = __match_any_sync(FULL_MASK, b);
-            if (lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&hist[b], (uint32_t)__popc(peers));
-        }
-    }
+    const uint32_t lo = P.begin + ci * P.chunk;
+    const uint32_t hi = min(lo + P.chunk, P.begin + P.size);
+    classify_range(w.key[cur], lo, hi, t, ino, k, nb, hist, nullptr);
     __syncthreads();
     for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x)
         w.counts[P.count_base + b * P.chunks + ci] = hist[b];
 }
 
-// ------------------------------------------------------------ scatter
+// ------------------------------------------------------------ stable scatter
 
 constexpr int kScatterWarps = kScatterThreads / 32;
-constexpr int kBucketsPerThread = (kNBMax + kScatterThreads) / kScatterThreads;  // 8
+
+template <int NBCAP>
+struct ScatterState {
+    uint32_t run_pos[NBCAP + 1];  // next output position of each bucket
+    uint32_t rdep[NBCAP + 1];     // refill code of each bucket
+    uint16_t whist[kScatterWarps][NBCAP + 1];
+};
+
+// Stable move of the strings [lo, hi) of one segment (Sec. 3.1: out-of-place
+// redistribution into the shadow arrays).  Sub-tiles of 2048 strings are
+// taken in order; warp w owns 256 consecutive strings of a sub-tile and
+// ranks equal buckets by lane (match + popc), per-warp counters give the
+// offset of each warp.  Needs: ss.run_pos/rdep set, ss.whist zero (columns
+// 0..nb), the tree in t/ino (or bucket ids in bid[e - lo]), 256 threads.
+// Returns this thread's number of key words gathered again.
+template <int NBCAP, bool kFromBid>
+__device__ uint32_t scatter_range(const Work& w, int cur, uint32_t lo, uint32_t hi, uint32_t nb,
+                                  ScatterState<NBCAP>& ss, const uint64_t* t, const uint64_t* ino, int k,
+                                  const uint16_t* bid, uint32_t seg_end) {
+    constexpr int kBucketsPerThread = (NBCAP + kScatterThreads) / kScatterThreads;
+    const uint64_t* key_in = w.key[cur];
+    const uint32_t* idx_in = w.idx[cur];
+    uint64_t* key_out = w.key[cur ^ 1];
+    uint32_t* idx_out = w.idx[cur ^ 1];
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t lt = lanemask_lt();
+    uint32_t nref = 0;
+    for (uint32_t sub = lo; sub < hi; sub += kSubTile) {
+        uint64_t kk[kScatterItems];
+        uint32_t ii[kScatterItems], bb[kScatterItems], loc[kScatterItems];
+        const uint32_t wbase = sub + warp * (32u * kScatterItems) + lane;
+#pragma unroll
+        for (int j = 0; j < kScatterItems; j++) {
+            const uint32_t e = wbase + j * 32u;
+            const bool ok = e < hi;
+            kk[j] = ok ? key_in[e] : 0ull;
+            ii[j] = ok ? idx_in[e] : 0u;
+            if (kFromBid) bb[j] = ok ? bid[e - lo] : nb;
+        }
+        if (!kFromBid) {
+#pragma unroll
+            for (int j = 0; j < kScatterItems; j++) {
+                const uint32_t e = wbase + j * 32u;
+                bb[j] = e < hi ? classify_key(kk[j], t, ino, k) : nb;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kScatterItems; j++) {
+            const uint32_t b = bb[j];
+            const uint32_t peers = __match_any_sync(FULL_MASK, b);
+            const uint32_t leader = (uint32_t)__ffs(peers) - 1u;
+            uint32_t off = 0;
+            if (lane == leader) {
+                off = ss.whist[warp][b];
+                ss.whist[warp][b] = (uint16_t)(off + (uint32_t)__popc(peers));
+            }
+            off = __shfl_sync(FULL_MASK, off, leader);
+            loc[j] = off + (uint32_t)__popc(peers & lt);
+        }
+        __syncthreads();
+        uint32_t accs[kBucketsPerThread];
+#pragma unroll
+        for (int q = 0; q < kBucketsPerThread; q++) {
+            const uint32_t b = threadIdx.x + q * kScatterThreads;
+            uint32_t acc = 0;
+            if (b < nb) {
+#pragma unroll
+                for (int ww = 0; ww < kScatterWarps; ww++) {
+                    const uint32_t cnt = ss.whist[ww][b];
+                    ss.whist[ww][b] = (uint16_t)acc;
+                    acc += cnt;
+                }
+            }
+            accs[q] = acc;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kScatterItems; j++) {
+            const uint32_t e = wbase + j * 32u;
+            if (e < hi) {
+                const uint32_t b = bb[j];
+                const uint32_t pos = ss.run_pos[b] + ss.whist[warp][b] + loc[j];
+                const uint32_t rd = ss.rdep[b];
+                if (pos >= seg_end) {
+                    atomicOr(&w.hdr->err, kErrPosition);
+                } else if (rd == kSingle) {
+                    w.out_perm[pos] = ii[j];
+                } else {
+                    idx_out[pos] = ii[j];
+                    key_out[pos] = rd == kNoRefill ? kk[j] : load_key(w.chars, w.offsets[ii[j]] + rd);
+                    nref += rd != kNoRefill;
+                }
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < kBucketsPerThread; q++) {
+            const uint32_t b = threadIdx.x + q * kScatterThreads;
+            if (b < nb) ss.run_pos[b] += accs[q];
+            if (b <= nb) {
+#pragma unroll
+                for (int ww = 0; ww < kScatterWarps; ww++) ss.whist[ww][b] = 0;
+            }
+        }
+        __syncthreads();
+    }
+    return nref;
+}
+
+__device__ __forceinline__ void add_refills(const Work& w, uint32_t nref) {
+    nref = __reduce_add_sync(FULL_MASK, nref);
+    if ((threadIdx.x & 31u) == 0 && nref) atomicAdd(&w.hdr->refills, (unsigned long long)nref);
+}
 
 struct ScatterSmem {
     uint64_t t[kVMax + 1];
     uint64_t ino[kVMax];
-    uint32_t run_pos[kNBMax + 1];
-    uint32_t rdep[kNBMax + 1];
-    uint16_t whist[kScatterWarps][kNBMax + 1];
+    ScatterState<kNBMax> ss;
 };
 
-__device__ __forceinline__ void append_child(const Work& w, uint32_t start, uint32_t size, uint32_t cdepth, bool isrun,
-                                             uint32_t runlcp, uint32_t base_threshold) {
-    Hdr* h = w.hdr;
-    if (size <= 1) return;
-    if (isrun && size > base_threshold) {
-        uint32_t s = atomicAdd(&h->n_bigrun, 1u);
-        if (s < w.bmax) w.bigrun[s] = Seg{start, size, cdepth, runlcp};
-        else atomicOr(&h->err, kErrRunOverflow);
-    } else if (size <= base_threshold) {
-        uint32_t s = atomicAdd(&h->n_small, 1u);
-        if (s < w.smax) { w.small[s] = Seg{start, size, cdepth, 0u}; w.small_size[s] = size; atomicAdd(&h->small_elems, size); }
-        else atomicOr(&h->err, kErrSmallOverflow);
-    } else {
-        uint32_t s = atomicAdd(&h->n_large, 1u);
-        if (s < w.lmax) w.large[s] = Seg{start, size, cdepth, 0u};
-        else atomicOr(&h->err, kErrLargeOverflow);
-    }
-}
-
-__global__ void __launch_bounds__(kScatterThreads) k_scatter(Work w, Params p, int cur) {
+__global__ void __launch_bounds__(kScatterThreads) k_scatter(Work w, Params p, int cur, int med_out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ScatterSmem& sm = *reinterpret_cast<ScatterSmem*>(smem_raw);
     const uint32_t c = blockIdx.x;
@@ -379,304 +553,281 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter(Work w, Params p, i
     const uint32_t S0 = S[0];
     const uint32_t seg_end = P.begin + P.size;
     for (uint32_t b = threadIdx.x; b <= nb; b += blockDim.x) {
-        for (int q = 0; q < kScatterWarps; q++) sm.whist[q][b] = 0;
+        for (int q = 0; q < kScatterWarps; q++) sm.ss.whist[q][b] = 0;
         if (b == nb) continue;
         const uint32_t start = P.begin + (S[b * P.chunks] - S0);
         const uint32_t end = (b + 1 < nb) ? P.begin + (S[(b + 1) * P.chunks] - S0) : seg_end;
         const uint32_t size = end - start;
-        sm.run_pos[b] = P.begin + (S[b * P.chunks + ci] - S0);
-        bool isrun = false;
-        uint32_t cdepth = P.depth, runlcp = 0;
-        if (b & 1u) {
-            const uint64_t x = sm.ino[b >> 1];
-            if (key_ends(x)) { isrun = true; runlcp = P.depth + key_chars(x); }
-            else cdepth = P.depth + 8u;
-        } else if (b != 0 && b != nb - 1 && size > 0) {
-            const uint32_t i = b >> 1;
-            cdepth = P.depth + key_lcp(sm.ino[i - 1], sm.ino[i]);
-        }
-        sm.rdep[b] = size == 1 ? kSingle : ((size == 0 || isrun || cdepth == P.depth) ? kNoRefill : cdepth);
+        sm.ss.run_pos[b] = P.begin + (S[b * P.chunks + ci] - S0);
+        const BucketInfo bi = bucket_info(b, nb, P.depth, sm.ino, size);
+        sm.ss.rdep[b] = refill_code(bi, size, P.depth);
         if (ci == 0 && size > 0) {
             if (start > P.begin) w.out_lcp[start] = kLcpFlag | P.depth;
-            append_child(w, start, size, cdepth, isrun, runlcp, p.base_threshold);
+            append_child(w, p, med_out, start, size, bi.cdepth, bi.isrun, bi.runlcp);
         }
     }
     __syncthreads();
+    const uint32_t lo = P.begin + ci * P.chunk;
+    const uint32_t hi = min(lo + P.chunk, seg_end);
+    const uint32_t nref = scatter_range<kNBMax, false>(w, cur, lo, hi, nb, sm.ss, sm.t, sm.ino, k, nullptr, seg_end);
+    add_refills(w, nref);
+}
 
-    const uint32_t lo = P.begin + ci * p.chunk;
-    const uint32_t hi = min(lo + p.chunk, seg_end);
-    const uint64_t* key_in = w.key[cur];
-    const uint32_t* idx_in = w.idx[cur];
-    uint64_t* key_out = w.key[cur ^ 1];
-    uint32_t* idx_out = w.idx[cur ^ 1];
-    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    const uint32_t lt = lanemask_lt();
-    uint32_t nref = 0;
+// ------------------------------------------------------------ medium round
 
-    for (uint32_t sub = lo; sub < hi; sub += kSubTile) {
-        uint64_t kk[kScatterItems];
-        uint32_t ii[kScatterItems], bb[kScatterItems], loc[kScatterItems];
-        const uint32_t wbase = sub + warp * (32u * kScatterItems) + lane;
-#pragma unroll
-        for (int j = 0; j < kScatterItems; j++) {
-            uint32_t e = wbase + j * 32u;
-            bool ok = e < hi;
-            kk[j] = ok ? key_in[e] : 0ull;
-            ii[j] = ok ? idx_in[e] : 0u;
-        }
-#pragma unroll
-        for (int j = 0; j < kScatterItems; j++) {
-            uint32_t e = wbase + j * 32u;
-            bb[j] = e < hi ? classify_key(kk[j], sm.t, sm.ino, k) : nb;
-        }
-#pragma unroll
-        for (int j = 0; j < kScatterItems; j++) {
-            const uint32_t b = bb[j];
-            const uint32_t peers = __match_any_sync(FULL_MASK, b);
-            const uint32_t leader = (uint32_t)__ffs(peers) - 1u;
-            uint32_t off = 0;
-            if (lane == leader) {
-                off = sm.whist[warp][b];
-                sm.whist[warp][b] = (uint16_t)(off + (uint32_t)__popc(peers));
-            }
-            off = __shfl_sync(FULL_MASK, off, leader);
-            loc[j] = off + (uint32_t)__popc(peers & lt);
-        }
-        __syncthreads();
-        uint32_t accs[kBucketsPerThread];
-#pragma unroll
-        for (int q = 0; q < kBucketsPerThread; q++) {
-            const uint32_t b = threadIdx.x + q * kScatterThreads;
-            uint32_t acc = 0;
-            if (b < nb) {
-#pragma unroll
-                for (int ww = 0; ww < kScatterWarps; ww++) {
-                    uint32_t cnt = sm.whist[ww][b];
-                    sm.whist[ww][b] = (uint16_t)acc;
-                    acc += cnt;
-                }
-            }
-            accs[q] = acc;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int j = 0; j < kScatterItems; j++) {
-            const uint32_t e = wbase + j * 32u;
-            if (e < hi) {
-                const uint32_t b = bb[j];
-                const uint32_t pos = sm.run_pos[b] + sm.whist[warp][b] + loc[j];
-                const uint32_t rd = sm.rdep[b];
-                if (pos >= seg_end) {
-                    atomicOr(&w.hdr->err, kErrPosition);
-                } else if (rd == kSingle) {
-                    w.out_perm[pos] = ii[j];
-                } else {
-                    idx_out[pos] = ii[j];
-                    key_out[pos] = rd == kNoRefill ? kk[j] : load_key(w.chars, w.offsets[ii[j]] + rd);
-                    nref += rd != kNoRefill;
-                }
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < kBucketsPerThread; q++) {
-            const uint32_t b = threadIdx.x + q * kScatterThreads;
-            if (b < nb) {
-                sm.run_pos[b] += accs[q];
-#pragma unroll
-                for (int ww = 0; ww < kScatterWarps; ww++) sm.whist[ww][b] = 0;
-            } else if (b == nb) {
-#pragma unroll
-                for (int ww = 0; ww < kScatterWarps; ww++) sm.whist[ww][b] = 0;
-            }
-        }
-        __syncthreads();
+struct MedSmem {
+    uint64_t samp[1 << (kMedKMax + 1)];
+    uint64_t lvl[1 << kMedKMax];
+    int32_t ra[1 << kMedKMax], rb[1 << kMedKMax];
+    uint64_t t[1 << kMedKMax];
+    uint64_t ino[1 << kMedKMax];
+    uint16_t bid[kMedMax];
+    uint32_t hist[kMedNB + 1];
+    uint32_t wsum[33];
+    ScatterState<kMedNB> ss;
+};
+
+// One CTA runs one whole distribution round for one medium segment (the
+// sequential S^5 of the paper, here on one SM): sample, tree, classify into a
+// shared bucket array, local prefix sum, stable move, child segments.
+__global__ void __launch_bounds__(kScatterThreads) k_med_round(Work w, Params p, int cur, int med_in, int med_out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    MedSmem& sm = *reinterpret_cast<MedSmem*>(smem_raw);
+    const Seg g = w.med[med_in][blockIdx.x];
+    const uint32_t m = g.size;
+    const int k = choose_k(m, min(p.k_max, kMedKMax));
+    const uint32_t v = (1u << k) - 1u, nb = 2u * v + 1u;
+    const uint32_t pw = 2u << k, cnt = pw - 1u;
+    const uint64_t* keys = w.key[cur];
+    for (uint32_t j = threadIdx.x; j < pw; j += blockDim.x)
+        sm.samp[j] = j < cnt ? keys[g.begin + sample_pos(p.seed, g.begin, m, j)] : ~0ull;
+    for (uint32_t b = threadIdx.x; b <= nb; b += blockDim.x) {
+        sm.hist[b] = 0;
+        for (int q = 0; q < kScatterWarps; q++) sm.ss.whist[q][b] = 0;
     }
-    nref = __reduce_add_sync(FULL_MASK, nref);
-    if (lane == 0 && nref) atomicAdd(&w.hdr->refills, (unsigned long long)nref);
+    __syncthreads();
+    bitonic_sort_u64(sm.samp, pw);
+    select_splitters(sm.samp, cnt, k, sm.lvl, sm.ra, sm.rb);
+    emit_tree(sm.lvl, k, sm.t + 1, sm.ino);
+    classify_range(keys, g.begin, g.begin + m, sm.t, sm.ino, k, nb, sm.hist, sm.bid);
+    __syncthreads();
+    // bucket starts: consecutive buckets per thread
+    constexpr int kPer = (kMedNB + 1) / kScatterThreads;
+    uint32_t cnts[kPer], sum = 0;
+#pragma unroll
+    for (int q = 0; q < kPer; q++) {
+        const uint32_t b = threadIdx.x * kPer + q;
+        cnts[q] = b < nb ? sm.hist[b] : 0u;
+        sum += cnts[q];
+    }
+    uint32_t start = g.begin + block_excl_sum(sum, sm.wsum, nullptr);
+#pragma unroll
+    for (int q = 0; q < kPer; q++) {
+        const uint32_t b = threadIdx.x * kPer + q;
+        if (b < nb) {
+            const uint32_t size = cnts[q];
+            const BucketInfo bi = bucket_info(b, nb, g.depth, sm.ino, size);
+            sm.ss.run_pos[b] = start;
+            sm.ss.rdep[b] = refill_code(bi, size, g.depth);
+            if (size > 0) {
+                if (start > g.begin) w.out_lcp[start] = kLcpFlag | g.depth;
+                append_child(w, p, med_out, start, size, bi.cdepth, bi.isrun, bi.runlcp);
+            }
+        }
+        start += cnts[q];
+    }
+    __syncthreads();
+    const uint32_t nref =
+        scatter_range<kMedNB, true>(w, cur, g.begin, g.begin + m, nb, sm.ss, sm.t, sm.ino, k, sm.bid, g.begin + m);
+    add_refills(w, nref);
 }
 
 // ------------------------------------------------------------ base case
 
-constexpr int kBaseThreads = 512;
+constexpr int kBaseWarps = 8;
 
-struct BaseSmem {
-    uint64_t K[kBaseCap];
-    uint32_t I[kBaseCap];
-    uint32_t G[kBaseCap];   // output position of each slot
-    uint32_t D[kBaseCap];   // depth of the run a slot belongs to
-    uint32_t H[kBaseCap];   // run heads / scan
-    uint32_t SB[kBaseMax + 2];  // slot base of each segment of the tile
-    uint16_t R[kBaseCap];   // run id (first slot of the run) carried with the element
-    uint32_t wsum[33];
+struct WarpTileSmem {
+    uint32_t sbase[kBaseWarps][kBaseMax + 2];  // first slot of each segment of the tile
+    uint32_t drun[kBaseWarps][kBaseCap];       // depth of the run that starts at a slot
 };
 
-__device__ __forceinline__ uint32_t upper_bound_u32(const uint32_t* a, uint32_t n, uint32_t x) {
-    uint32_t lo = 0, hi = n;
-    while (lo < hi) {
-        uint32_t m = (lo + hi) >> 1;
-        if (a[m] <= x) lo = m + 1; else hi = m;
-    }
-    return lo;
+__device__ __forceinline__ bool el_less(uint32_t ra, uint64_t ka, uint32_t ia, uint32_t rb, uint64_t kb,
+                                        uint32_t ib) {
+    return ra != rb ? ra < rb : (ka != kb ? ka < kb : ia < ib);
 }
 
-__device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t* a, uint32_t n, uint32_t x) {
-    uint32_t lo = 0, hi = n;
-    while (lo < hi) {
-        uint32_t m = (lo + hi) >> 1;
-        if (a[m] < x) lo = m + 1; else hi = m;
-    }
-    return lo;
-}
-
-__device__ __forceinline__ bool base_less(const BaseSmem& sm, uint32_t a, uint32_t b) {
-    if (sm.R[a] != sm.R[b]) return sm.R[a] < sm.R[b];
-    if (sm.K[a] != sm.K[b]) return sm.K[a] < sm.K[b];
-    return sm.I[a] < sm.I[b];
-}
-
-// Inclusive max-scan of H[0..cnt) in place; blocked, 8 slots per thread.
-__device__ void block_max_scan(uint32_t* H, uint32_t cnt, uint32_t* wsum) {
-    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    constexpr int kPer = kBaseCap / kBaseThreads;
-    uint32_t v[kPer];
-    uint32_t run = 0;
-#pragma unroll
-    for (int j = 0; j < kPer; j++) {
-        uint32_t i = threadIdx.x * kPer + j;
-        uint32_t x = i < cnt ? H[i] : 0u;
-        run = max(run, x);
-        v[j] = run;
-    }
-    uint32_t inc = run;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(FULL_MASK, inc, o);
-        if (lane >= (uint32_t)o) inc = max(inc, y);
-    }
-    if (lane == 31) wsum[warp] = inc;
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t s = lane < nw ? wsum[lane] : 0u;
-        uint32_t si = s;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(FULL_MASK, si, o);
-            if (lane >= (uint32_t)o) si = max(si, y);
-        }
-        uint32_t ex = __shfl_up_sync(FULL_MASK, si, 1);
-        if (lane < nw) wsum[lane] = lane ? ex : 0u;
-    }
-    __syncthreads();
-    uint32_t ex_in_warp = __shfl_up_sync(FULL_MASK, inc, 1);
-    if (lane == 0) ex_in_warp = 0;
-    const uint32_t prefix = max(wsum[warp], ex_in_warp);
-#pragma unroll
-    for (int j = 0; j < kPer; j++) {
-        uint32_t i = threadIdx.x * kPer + j;
-        if (i < cnt) H[i] = max(prefix, v[j]);
-    }
-    __syncthreads();
-}
-
-// One CTA per tile of packed small segments: segments whose packed start lies
-// in [t*T, (t+1)*T) (T = base_threshold), at most 2T - 1 strings.  Sorts
-// each segment by (key word at its depth, index); runs of equal key words
-// without terminator move 8 bytes deeper and are sorted again, until every
-// run is decided.  Writes out_perm and the LCP of every slot but a
-// segment's first.
-__global__ void __launch_bounds__(kBaseThreads) k_base(Work w, Params p, int buf, uint32_t ns, uint32_t total) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    BaseSmem& sm = *reinterpret_cast<BaseSmem*>(smem_raw);
-    const uint32_t T = p.base_threshold;
-    const uint32_t t0 = blockIdx.x * T;
+// One warp per tile of packed small segments: the segments whose packed
+// start lies in [t*T, (t+1)*T) (T = base_threshold <= 16E), at most 2T - 1
+// <= 32E strings.  Lane l holds slots lE .. lE+E-1.  Each element carries
+// (run, key word, index); runs are contiguous slot ranges, so sorting by
+// (run, key, index) sorts every run in place.  Bitonic network: strides
+// below E inside a lane, larger strides by shuffles.  After each sort a key
+// change between neighbours fixes their LCP, equal key words holding the
+// terminator are equal strings, and runs of equal key words without it move
+// 8 bytes deeper (new word gathered) and are sorted again.
+template <int E>
+__global__ void __launch_bounds__(32 * kBaseWarps) k_base_warp(Work w, uint32_t T, int buf, uint32_t ns,
+                                                               uint32_t total) {
+    constexpr uint32_t CAP = 32u * E;
+    __shared__ WarpTileSmem sm;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t tile = blockIdx.x * kBaseWarps + warp;
+    const uint32_t t0 = tile * T;
     if (t0 >= total) return;
     const uint32_t t1 = min(t0 + T, total);
-    const uint32_t lo = lower_bound_u32(w.small_off, ns, t0);
-    const uint32_t hi = lower_bound_u32(w.small_off, ns, t1);
+    // segments with packed start in [t0, t1)
+    uint32_t lo, hi;
+    {
+        uint32_t a = 0, b = ns;
+        while (a < b) { uint32_t m = (a + b) >> 1; if (w.small_off[m] < t0) a = m + 1; else b = m; }
+        lo = a;
+        b = ns;
+        while (a < b) { uint32_t m = (a + b) >> 1; if (w.small_off[m] < t1) a = m + 1; else b = m; }
+        hi = a;
+    }
     if (lo >= hi) return;
     const uint32_t slot0 = w.small_off[lo];
     const uint32_t cnt = (hi < ns ? w.small_off[hi] : total) - slot0;
     const uint32_t nseg = hi - lo;
-    for (uint32_t i = threadIdx.x; i < nseg; i += blockDim.x) sm.SB[i] = w.small_off[lo + i] - slot0;
-    __syncthreads();
+    uint32_t* sbase = sm.sbase[warp];
+    uint32_t* drun = sm.drun[warp];
+    for (uint32_t i = lane; i < nseg; i += 32) {
+        const uint32_t b = w.small_off[lo + i] - slot0;
+        sbase[i] = b;
+        drun[b] = w.small[lo + i].depth;
+    }
+    __syncwarp();
     const uint64_t* key_in = w.key[buf];
     const uint32_t* idx_in = w.idx[buf];
-    uint32_t pw = 1;
-    while (pw < cnt) pw <<= 1;
-    for (uint32_t q = threadIdx.x; q < pw; q += blockDim.x) {
-        if (q < cnt) {
-            const uint32_t i = upper_bound_u32(sm.SB, nseg, q) - 1u;
-            const Seg g = w.small[lo + i];
-            const uint32_t r = q - sm.SB[i];
-            sm.G[q] = g.begin + r;
-            sm.D[q] = g.depth;
-            sm.R[q] = (uint16_t)sm.SB[i];
-            sm.K[q] = key_in[g.begin + r];
-            sm.I[q] = idx_in[g.begin + r];
+    uint64_t K[E];
+    uint32_t I[E], R[E], G[E];
+#pragma unroll
+    for (int j = 0; j < E; j++) {
+        const uint32_t s = lane * E + j;
+        if (s < cnt) {
+            uint32_t a = 0, b = nseg;  // last segment with sbase <= s
+            while (a < b) { uint32_t m = (a + b) >> 1; if (sbase[m] <= s) a = m + 1; else b = m; }
+            const uint32_t i = a - 1;
+            const uint32_t gpos = w.small[lo + i].begin + (s - sbase[i]);
+            G[j] = gpos;
+            R[j] = sbase[i];
+            K[j] = key_in[gpos];
+            I[j] = idx_in[gpos];
         } else {
-            sm.R[q] = 0xFFFFu;
-            sm.K[q] = ~0ull;
-            sm.I[q] = 0xFFFFFFFFu;
+            G[j] = 0;
+            R[j] = 0xFFFFFFFFu;
+            K[j] = ~0ull;
+            I[j] = 0xFFFFFFFFu;
         }
     }
-    __syncthreads();
-    for (uint32_t iter = 0;; iter++) {
+    uint32_t iter = 0;
+    for (;; iter++) {
         if (iter >= kBaseMaxIters) {  // never expected: strings end, so runs end
-            if (threadIdx.x == 0) atomicOr(&w.hdr->err, kErrBaseIters);
+            if (lane == 0) atomicOr(&w.hdr->err, kErrBaseIters);
             return;
         }
-        // segmented sort: (run, key, index) order keeps every run in its slots
-        for (uint32_t size = 2; size <= pw; size <<= 1) {
-            for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
-                for (uint32_t i = threadIdx.x; i < pw / 2; i += blockDim.x) {
-                    const uint32_t a = 2u * i - (i & (stride - 1u));
-                    const uint32_t b = a + stride;
-                    const bool asc = (a & size) == 0;
-                    if (base_less(sm, b, a) == asc) {
-                        uint64_t tk = sm.K[a]; sm.K[a] = sm.K[b]; sm.K[b] = tk;
-                        uint32_t ti = sm.I[a]; sm.I[a] = sm.I[b]; sm.I[b] = ti;
-                        uint16_t tr = sm.R[a]; sm.R[a] = sm.R[b]; sm.R[b] = tr;
+        // ---- sort by (run, key, index)
+#pragma unroll
+        for (int size = 2; size <= (int)CAP; size <<= 1) {
+#pragma unroll
+            for (int st = size >> 1; st > 0; st >>= 1) {
+                if (st < E) {
+#pragma unroll
+                    for (int j = 0; j < E; j++) {
+                        if ((j & st) == 0) {
+                            const int jj = j | st;
+                            const bool asc = ((lane * E + j) & size) == 0;
+                            const bool sw = asc ? el_less(R[jj], K[jj], I[jj], R[j], K[j], I[j])
+                                                : el_less(R[j], K[j], I[j], R[jj], K[jj], I[jj]);
+                            if (sw) {
+                                uint32_t tr = R[j]; R[j] = R[jj]; R[jj] = tr;
+                                uint64_t tk = K[j]; K[j] = K[jj]; K[jj] = tk;
+                                uint32_t ti = I[j]; I[j] = I[jj]; I[jj] = ti;
+                            }
+                        }
+                    }
+                } else {
+                    const int lm = st / E;
+                    const bool lower = (lane & (uint32_t)lm) == 0;
+#pragma unroll
+                    for (int j = 0; j < E; j++) {
+                        const uint32_t pr = __shfl_xor_sync(FULL_MASK, R[j], lm);
+                        const uint64_t pk = __shfl_xor_sync(FULL_MASK, K[j], lm);
+                        const uint32_t pi = __shfl_xor_sync(FULL_MASK, I[j], lm);
+                        const bool asc = ((lane * E + j) & size) == 0;
+                        const bool take = (lower == asc) ? el_less(pr, pk, pi, R[j], K[j], I[j])
+                                                         : el_less(R[j], K[j], I[j], pr, pk, pi);
+                        if (take) { R[j] = pr; K[j] = pk; I[j] = pi; }
                     }
                 }
-                __syncthreads();
             }
         }
-        // decide neighbours: a key change fixes the LCP; equal keys holding the
-        // terminator are equal strings; equal keys without it stay in a run
-        for (uint32_t q = threadIdx.x; q < cnt; q += blockDim.x) {
+        // ---- decide neighbours
+        const uint64_t prevK = __shfl_up_sync(FULL_MASK, K[E - 1], 1);
+        uint32_t hv[E], dold[E];
+        uint32_t run = 0;
+#pragma unroll
+        for (int j = 0; j < E; j++) {
+            const uint32_t s = lane * E + j;
             bool head = true;
-            if (q != sm.R[q]) {
-                const uint64_t a = sm.K[q - 1], b = sm.K[q];
-                if (a != b) {
-                    w.out_lcp[sm.G[q]] = sm.D[q] + key_lcp(a, b);
-                } else {
-                    head = false;
-                    if (key_ends(b)) w.out_lcp[sm.G[q]] = sm.D[q] + key_chars(b);
+            dold[j] = 0;
+            if (s < cnt) {
+                dold[j] = drun[R[j]];
+                if (s != R[j]) {
+                    const uint64_t pk = j ? K[j - 1] : prevK;
+                    if (pk != K[j]) {
+                        w.out_lcp[G[j]] = dold[j] + key_lcp(pk, K[j]);
+                    } else {
+                        head = false;
+                        if (key_ends(K[j])) w.out_lcp[G[j]] = dold[j] + key_chars(K[j]);
+                    }
                 }
             }
-            sm.H[q] = head ? q : 0u;
+            run = max(run, head ? s : 0u);
+            hv[j] = run;
         }
-        __syncthreads();
-        block_max_scan(sm.H, cnt, sm.wsum);
+        // sub-run heads: inclusive max-scan over the slots
+        uint32_t inc = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL_MASK, inc, o);
+            if (lane >= (uint32_t)o) inc = max(inc, y);
+        }
+        uint32_t ex = __shfl_up_sync(FULL_MASK, inc, 1);
+        if (lane == 0) ex = 0;
+        uint32_t SR[E];
+#pragma unroll
+        for (int j = 0; j < E; j++) SR[j] = max(ex, hv[j]);
+        const uint32_t nextSR0 = __shfl_down_sync(FULL_MASK, SR[0], 1);
+        __syncwarp();  // every lane read drun before any lane writes it
         bool any = false;
-        for (uint32_t q = threadIdx.x; q < cnt; q += blockDim.x) {
-            const uint32_t head = sm.H[q];
-            const bool multi = (q != head) || (q + 1 < cnt && sm.H[q + 1] == q);
-            const bool act = multi && !key_ends(sm.K[q]);
-            if (act) {
-                const uint32_t d = sm.D[q] + 8u;
-                sm.D[q] = d;
-                sm.K[q] = load_key(w.chars, w.offsets[sm.I[q]] + d);
-                sm.R[q] = (uint16_t)head;
-                any = true;
-            } else {
-                sm.R[q] = (uint16_t)q;
+#pragma unroll
+        for (int j = 0; j < E; j++) {
+            const uint32_t s = lane * E + j;
+            if (s < cnt) {
+                const uint32_t nsr = (j + 1 < E) ? SR[(j + 1) % E] : nextSR0;
+                const bool multi = (s != SR[j]) || (s + 1 < cnt && nsr == s);
+                const bool act = multi && !key_ends(K[j]);
+                if (act) {
+                    const uint32_t d = dold[j] + 8u;
+                    if (s == SR[j]) drun[s] = d;
+                    K[j] = load_key(w.chars, w.offsets[I[j]] + d);
+                    R[j] = SR[j];
+                    any = true;
+                } else {
+                    R[j] = s;
+                }
             }
         }
-        if (!__syncthreads_or(any)) break;
+        __syncwarp();
+        if (!__any_sync(FULL_MASK, any)) break;
     }
-    for (uint32_t q = threadIdx.x; q < cnt; q += blockDim.x) w.out_perm[sm.G[q]] = sm.I[q];
+#pragma unroll
+    for (int j = 0; j < E; j++) {
+        const uint32_t s = lane * E + j;
+        if (s < cnt) w.out_perm[G[j]] = I[j];
+    }
+    if (lane == 0) atomicAdd(&w.hdr->base_iters, (unsigned long long)(iter + 1));
 }
 
 // Buckets too large for the base case whose strings are all equal.
@@ -789,23 +940,18 @@ cudaError_t launch_scan_u32(const uint32_t* in, uint32_t* out, uint32_t n, uint3
 
 // ------------------------------------------------------------ launches
 
-static int g_num_sms = 0;
-
-static int num_sms() {
-    if (!g_num_sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-        if (g_num_sms <= 0) g_num_sms = 148;
-    }
-    return g_num_sms;
-}
-
-static uint32_t grid_for(uint64_t n, uint32_t threads, uint32_t per_sm) {
+static uint32_t grid_for(uint64_t n, uint32_t threads, uint32_t per_sm, uint32_t num_sms) {
     uint64_t g = (n + threads - 1) / threads;
-    uint64_t cap = (uint64_t)num_sms() * per_sm;
+    uint64_t cap = (uint64_t)num_sms * per_sm;
     if (g > cap) g = cap;
     return g ? (uint32_t)g : 1u;
+}
+
+uint32_t device_sms() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? (uint32_t)sms : 148u;
 }
 
 cudaError_t launch_init(const Work& w, Prof* pf, cudaStream_t st) {
@@ -814,7 +960,7 @@ cudaError_t launch_init(const Work& w, Prof* pf, cudaStream_t st) {
         cudaError_t e = cudaMemsetAsync(w.idx[1], 0, sizeof(uint32_t) * (size_t)w.n, st);
         if (e != cudaSuccess) return e;
         ProfScope ps(pf, kInit, st);
-        k_init<<<grid_for(w.n, 256, 16), 256, 0, st>>>(w);
+        k_init<<<grid_for(w.n, 256, 16, device_sms()), 256, 0, st>>>(w);
     }
     return cudaGetLastError();
 }
@@ -828,9 +974,9 @@ cudaError_t launch_roots(const Work& w, const Params& p, const Seg* roots, uint3
     ProfScope ps(pf, kInit, st);
     if (roots) {
         if (num_roots)
-            k_roots<<<grid_for(num_roots, 256, 4), 256, 0, st>>>(w, roots, num_roots, Seg{}, p.base_threshold);
+            k_roots<<<grid_for(num_roots, 256, 4, p.num_sms), 256, 0, st>>>(w, p, roots, num_roots, Seg{});
     } else {
-        k_roots<<<1, 32, 0, st>>>(w, nullptr, 1u, Seg{0u, w.n, 0u, 0u}, p.base_threshold);
+        k_roots<<<1, 32, 0, st>>>(w, p, nullptr, 1u, Seg{0u, w.n, 0u, 0u});
     }
     return cudaGetLastError();
 }
@@ -842,39 +988,46 @@ cudaError_t launch_plan(const Work& w, const Params& p, Prof* pf, cudaStream_t s
 }
 
 cudaError_t launch_round(const Work& w, const Params& p, int cur, uint32_t L, uint32_t total_chunks,
-                         uint32_t total_counts, Prof* pf, cudaStream_t st) {
-    cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ScatterSmem));
-    {
-        ProfScope ps(pf, kSample, st);
-        k_sample<<<L, 1024, 0, st>>>(w, p, cur);
+                         uint32_t total_counts, uint32_t n_med, int med_in, Prof* pf, cudaStream_t st) {
+    if (L) {
+        cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ScatterSmem));
+        {
+            ProfScope ps(pf, kSample, st);
+            k_sample<<<L, 1024, 0, st>>>(w, p, cur);
+        }
+        {
+            ProfScope ps(pf, kClassify, st);
+            k_classify<<<total_chunks, kClassifyThreads, 0, st>>>(w, p, cur);
+        }
+        cudaError_t e = launch_scan_u32(w.counts, w.counts_scan, total_counts, w.scan_tmp, pf, st);
+        if (e != cudaSuccess) return e;
+        {
+            ProfScope ps(pf, kScatter, st);
+            k_scatter<<<total_chunks, kScatterThreads, sizeof(ScatterSmem), st>>>(w, p, cur, med_in ^ 1);
+        }
     }
-    {
-        ProfScope ps(pf, kClassify, st);
-        k_classify<<<total_chunks, kClassifyThreads, 0, st>>>(w, p, cur);
-    }
-    cudaError_t e = launch_scan_u32(w.counts, w.counts_scan, total_counts, w.scan_tmp, pf, st);
-    if (e != cudaSuccess) return e;
-    {
-        ProfScope ps(pf, kScatter, st);
-        k_scatter<<<total_chunks, kScatterThreads, sizeof(ScatterSmem), st>>>(w, p, cur);
+    if (n_med) {
+        cudaFuncSetAttribute(k_med_round, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MedSmem));
+        ProfScope ps(pf, kMedium, st);
+        k_med_round<<<n_med, kScatterThreads, sizeof(MedSmem), st>>>(w, p, cur, med_in, med_in ^ 1);
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_small(const Work& w, const Params& p, int buf, uint32_t n_small, uint32_t n_bigrun,
                          uint32_t small_total, uint32_t* out_tiles, Prof* pf, cudaStream_t st) {
-    cudaFuncSetAttribute(k_base, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BaseSmem));
     uint32_t tiles = 0;
     if (n_small) {
         cudaError_t e = launch_scan_u32(w.small_size, w.small_off, n_small, w.scan_tmp, pf, st);
         if (e != cudaSuccess) return e;
         tiles = (small_total + p.base_threshold - 1) / p.base_threshold;
         ProfScope ps(pf, kBase, st);
-        k_base<<<tiles, kBaseThreads, sizeof(BaseSmem), st>>>(w, p, buf, n_small, small_total);
+        k_base_warp<kBaseE><<<(tiles + kBaseWarps - 1) / kBaseWarps, 32 * kBaseWarps, 0, st>>>(
+            w, p.base_threshold, buf, n_small, small_total);
     }
     if (n_bigrun) {
         ProfScope ps(pf, kRuns, st);
-        k_bigrun<<<grid_for((uint64_t)n_bigrun * 256, 256, 4), 256, 0, st>>>(w, buf, n_bigrun);
+        k_bigrun<<<grid_for((uint64_t)n_bigrun * 256, 256, 4, p.num_sms), 256, 0, st>>>(w, buf, n_bigrun);
     }
     if (out_tiles) *out_tiles = tiles;
     return cudaGetLastError();
@@ -883,7 +1036,7 @@ cudaError_t launch_small(const Work& w, const Params& p, int buf, uint32_t n_sma
 cudaError_t launch_fixup(const Work& w, Prof* pf, cudaStream_t st) {
     if (w.n > 1) {
         ProfScope ps(pf, kFixup, st);
-        k_fixup<<<grid_for(w.n, 256, 16), 256, 0, st>>>(w);
+        k_fixup<<<grid_for(w.n, 256, 16, device_sms()), 256, 0, st>>>(w);
     }
     return cudaGetLastError();
 }
@@ -901,7 +1054,7 @@ __global__ void k_gather_keys(const uint8_t* chars, const uint64_t* offsets, con
 
 cudaError_t launch_gather_keys(const uint8_t* chars, const uint64_t* offsets, const uint32_t* idx,
                                const uint32_t* depth, uint32_t n, uint64_t* out, cudaStream_t st) {
-    if (n) k_gather_keys<<<grid_for(n, 256, 16), 256, 0, st>>>(chars, offsets, idx, depth, n, out);
+    if (n) k_gather_keys<<<grid_for(n, 256, 16, device_sms()), 256, 0, st>>>(chars, offsets, idx, depth, n, out);
     return cudaGetLastError();
 }
 
@@ -925,7 +1078,7 @@ __global__ void k_classify_keys(const uint64_t* keys, uint32_t n, const uint64_t
 
 cudaError_t launch_classify(const uint64_t* keys, uint32_t n, const uint64_t* lvl, const uint64_t* ino, int k,
                             uint16_t* out, cudaStream_t st) {
-    if (n) k_classify_keys<<<grid_for(n, 256, 8), 256, 0, st>>>(keys, n, lvl, ino, k, out);
+    if (n) k_classify_keys<<<grid_for(n, 256, 8, device_sms()), 256, 0, st>>>(keys, n, lvl, ino, k, out);
     return cudaGetLastError();
 }
 
@@ -940,7 +1093,8 @@ __global__ void k_localize(uint32_t* perm, const Seg* roots, uint32_t num_roots)
 cudaError_t launch_localize(uint32_t* perm, const Seg* roots, uint32_t num_roots, Prof* pf, cudaStream_t st) {
     if (num_roots) {
         ProfScope ps(pf, kFixup, st);
-        k_localize<<<grid_for((uint64_t)num_roots * 256, 256, 8), 256, 0, st>>>(perm, roots, num_roots);
+        k_localize<<<grid_for((uint64_t)num_roots * 256, 256, 8, device_sms()), 256, 0, st>>>(perm, roots,
+                                                                                               num_roots);
     }
     return cudaGetLastError();
 }

@@ -146,8 +146,15 @@ def test_generated_kinds(kind, n, seed):
 
 # options that push small inputs through many distribution rounds, tiny
 # trees and one-tile chunks
-SMALL_OPTS = [dict(base_threshold=16, k_max=2, chunk=2048), dict(base_threshold=16, k_max=10, chunk=2048),
-              dict(base_threshold=100, k_max=5, chunk=4096), dict(base_threshold=2048, k_max=10, chunk=32768)]
+SMALL_OPTS = [
+    # every bucket above 16 strings through device-wide rounds, tiny trees
+    dict(base_threshold=16, medium_threshold=16, k_max=2, chunk=2048),
+    # small base case, everything else per-CTA rounds
+    dict(base_threshold=16, medium_threshold=8192, k_max=10, chunk=2048),
+    dict(base_threshold=100, medium_threshold=300, k_max=5, chunk=4096),
+    # defaults
+    dict(base_threshold=128, medium_threshold=8192, k_max=10, chunk=32768),
+]
 
 
 @pytest.mark.parametrize("opts", SMALL_OPTS)
@@ -182,7 +189,7 @@ EDGE_CASES = {
 
 
 @pytest.mark.parametrize("name", sorted(EDGE_CASES))
-@pytest.mark.parametrize("opts", [SMALL_OPTS[0], SMALL_OPTS[3]])
+@pytest.mark.parametrize("opts", [SMALL_OPTS[0], SMALL_OPTS[1], SMALL_OPTS[3]])
 def test_edge_cases(name, opts):
     sss.sss_set_options(**opts)
     items = list(EDGE_CASES[name])
@@ -202,7 +209,7 @@ def test_random_bytes_many_duplicates_ragged():
     rng = random.Random(5)
     items = rand_strings(rng, 70_001, 24, list(range(1, 256)), prefixes=(b"", b"http://", b"\xff" * 9), dup_frac=0.3)
     s = gen.from_list(items)
-    sss.sss_set_options(base_threshold=64, k_max=6, chunk=2048)
+    sss.sss_set_options(base_threshold=64, medium_threshold=1000, k_max=6, chunk=2048)
     perm, lcp = gpu_sort(s)
     assert_same(s, perm, lcp)
 
@@ -244,7 +251,7 @@ def test_batched_matches_per_set_oracle():
     chars, offsets = to_dev(s)
     perm = torch.full((s.n,), -1, dtype=torch.int32, device="cuda")
     lcp = torch.full((s.n,), -1, dtype=torch.int32, device="cuda")
-    sss.sss_set_options(base_threshold=256, k_max=8, chunk=2048)
+    sss.sss_set_options(base_threshold=32, medium_threshold=600, k_max=8, chunk=2048)
     sss.sss_sort_batched(chars, offsets, s.n, set_begin, len(sizes), perm, lcp)
     torch.cuda.synchronize()
     perm, lcp = u32(perm), u32(lcp)
