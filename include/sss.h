@@ -55,7 +55,7 @@ typedef enum {
 } sss_status;
 
 /* Tuning knobs.  Defaults: k_max 10, base_threshold 128, medium_threshold
- * 8192, chunk 32768, seed 0x5eed, cdf_segments 4096, cdf_steps 64,
+ * 2048, chunk 32768, seed 0x5eed, cdf_segments 4096, cdf_steps 64,
  * cdf_lr 0.05, profile 0. */
 typedef struct sss_options {
     int32_t k_max;             /* largest splitter tree depth k: v = 2^k - 1 splitters, 1..10 */
@@ -98,6 +98,7 @@ typedef struct sss_stats {
     uint64_t round_strings;          /* sum over rounds of strings distributed */
     uint64_t medium_strings;         /* of those, strings in per-CTA (medium) rounds */
     uint64_t base_iterations;        /* base-case sort passes summed over tiles */
+    uint32_t base_segment_hist[8];   /* base-case buckets by floor(log2(size)) (2-3, 4-7, ..., >= 128) */
     uint64_t base_strings;           /* strings finished by the base case */
     uint64_t run_strings;            /* strings finished as large runs of equal strings */
     uint64_t learned_keys;           /* keys the learned model proposed a bucket for */
@@ -135,7 +136,7 @@ int sss_sort_ws(const uint8_t* chars, const uint64_t* offsets, uint32_t n,
  * nearly all device memory (a stray cudaMalloc fails or fragments it),
  * latency-critical loops (cudaMalloc and cudaFree can synchronise the whole
  * device), or hosts whose policy forbids allocation after start-up.
- * Scratch is a 4 MiB static device array inside this library, held by every
+ * Scratch is a 6 MiB static device array inside this library, held by every
  * GPU that loads the library until the process exits; the call itself
  * allocates nothing (no cudaMalloc, cudaFree or pinned host memory; the
  * per-round header is read into static host memory, and profiling is off).

@@ -48,7 +48,8 @@ class sss_options(ctypes.Structure):
 class sss_stats(ctypes.Structure):
     _fields_ = [("rounds", ctypes.c_uint32), ("base_tiles", ctypes.c_uint32),
                 ("round_strings", ctypes.c_uint64), ("medium_strings", ctypes.c_uint64),
-                ("base_iterations", ctypes.c_uint64), ("base_strings", ctypes.c_uint64),
+                ("base_iterations", ctypes.c_uint64), ("base_segment_hist", ctypes.c_uint32 * 8),
+                ("base_strings", ctypes.c_uint64),
                 ("run_strings", ctypes.c_uint64), ("learned_keys", ctypes.c_uint64),
                 ("learned_misses", ctypes.c_uint64), ("refilled_strings", ctypes.c_uint64),
                 ("launches", ctypes.c_uint32), ("profiled", ctypes.c_uint32),
@@ -61,6 +62,7 @@ class sss_stats(ctypes.Structure):
         r = self.rounds
         return {"rounds": r, "base_tiles": self.base_tiles, "round_strings": self.round_strings,
                 "medium_strings": self.medium_strings, "base_iterations": self.base_iterations,
+                "base_segment_hist": list(self.base_segment_hist),
                 "base_strings": self.base_strings, "run_strings": self.run_strings,
                 "learned_keys": self.learned_keys, "learned_misses": self.learned_misses,
                 "refilled_strings": self.refilled_strings, "launches": self.launches,

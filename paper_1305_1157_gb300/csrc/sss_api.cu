@@ -22,7 +22,7 @@ using namespace sss;
 namespace {
 
 std::mutex g_mu;
-sss_options g_opt = {10, 128u, 8192u, 32768u, 0x5eedull, 4096u, 64u, 0.05f, 0u};
+sss_options g_opt = {10, 128u, 2048u, 32768u, 0x5eedull, 4096u, 64u, 0.05f, 0u};
 sss_stats g_stats;
 Prof g_prof;
 char g_err[512] = "no error";
@@ -60,7 +60,7 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct Layout {
     size_t total = 0;
-    size_t o_key0, o_key1, o_idx0, o_idx1, o_counts, o_counts_scan, o_tlvl, o_tino, o_plans, o_chunk_seg,
+    size_t o_key0, o_key1, o_idx0, o_idx1, o_off0, o_off1, o_counts, o_counts_scan, o_tlvl, o_tino, o_plans, o_chunk_seg,
         o_large, o_med0, o_med1, o_small, o_small_size, o_small_off, o_bigrun, o_scan_tmp, o_hdr, o_roots;
     uint32_t cmax, tmax, lmax, chmax, smax, bmax, scan_tmp_max, mmax;
 };
@@ -111,6 +111,8 @@ Layout layout_for(uint32_t n, const sss_options& o, uint32_t num_roots) {
     L.o_key1 = take(8 * nn);
     L.o_idx0 = take(4 * nn);
     L.o_idx1 = take(4 * nn);
+    L.o_off0 = take(8 * nn);
+    L.o_off1 = take(8 * nn);
     L.o_counts = take(4 * (cmax + 1));
     L.o_counts_scan = take(4 * (cmax + 1));
     L.o_tlvl = take(8 * tmax);
@@ -140,6 +142,8 @@ Work make_work(const Layout& L, char* ws, const uint8_t* chars, const uint64_t* 
     w.key[1] = (uint64_t*)(ws + L.o_key1);
     w.idx[0] = (uint32_t*)(ws + L.o_idx0);
     w.idx[1] = (uint32_t*)(ws + L.o_idx1);
+    w.off[0] = (uint64_t*)(ws + L.o_off0);
+    w.off[1] = (uint64_t*)(ws + L.o_off1);
     w.counts = (uint32_t*)(ws + L.o_counts);
     w.counts_scan = (uint32_t*)(ws + L.o_counts_scan);
     w.tree_lvl = (uint64_t*)(ws + L.o_tlvl);
@@ -244,6 +248,7 @@ int run_sort(const Work& w, const sss_options& o, const Seg* roots_dev, uint32_t
     if (rc) return rc;
     stats->refilled_strings = hh->refills;
     stats->base_iterations = hh->base_iters;
+    for (int i = 0; i < 8; i++) stats->base_segment_hist[i] = hh->small_hist[i];
     stats->launches = pf->launches;
     stats->profiled = pf->enabled ? 1u : 0u;
     for (int i = 0; i < kClasses; i++) stats->prof_launches[i] = pf->cls_launches[i];
@@ -463,7 +468,7 @@ const char* sss_version(void) { return "sss-gb300 0.1"; }
 namespace {
 
 constexpr uint32_t kNoAllocMaxStrings = 1u << 16;
-constexpr size_t kNoAllocScratchBytes = (size_t)4 << 20;
+constexpr size_t kNoAllocScratchBytes = (size_t)6 << 20;
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 

@@ -16,8 +16,7 @@ constexpr int kKMax = 10;                       // deepest splitter tree
 constexpr int kVMax = (1 << kKMax) - 1;         // 1023 splitters
 constexpr int kNBMax = 2 * kVMax + 1;           // 2047 buckets (Sec. 3.1: k = 2v + 1)
 constexpr int kSampleMax = 1 << (kKMax + 1);    // sample buffer, 2v + 1 keys padded to 2^(k+1)
-constexpr int kBaseE = 8;                       // base case: slots per lane
-constexpr uint32_t kBaseCap = 32u * kBaseE;     // slots of one warp tile (256)
+constexpr uint32_t kBaseCap = 256;              // slots of one base-case tile
 constexpr uint32_t kBaseMax = kBaseCap / 2;     // largest base-case bucket (128)
 constexpr uint32_t kMedMax = 8192;              // largest bucket one CTA distributes alone
 constexpr int kMedKMax = 9;                     // its deepest tree: choose_k(8192) = 9
@@ -56,6 +55,7 @@ struct Hdr {
     uint32_t large_elems_snap, med_elems_snap, chunk, pad1;
     unsigned long long refills;   // key words gathered in rounds
     unsigned long long base_iters;  // base-case refill iterations summed over tiles
+    uint32_t small_hist[8];         // base-case segments by floor(log2(size))
 };
 
 // err bits
@@ -91,8 +91,9 @@ struct Work {
     uint32_t* out_perm;
     uint32_t* out_lcp;
 
-    uint64_t* key[2];
-    uint32_t* idx[2];
+    uint64_t* key[2];        // cached key word of each position (ping-pong per round)
+    uint32_t* idx[2];        // string index of each position
+    uint64_t* off[2];        // byte offset of that string, so refills read chars directly
     uint32_t* counts;        // [cmax] per (segment, bucket, chunk) counts
     uint32_t* counts_scan;   // [cmax] exclusive scan of counts
     uint64_t* tree_lvl;      // [tmax]

@@ -15,10 +15,10 @@
 //   medium (> base_threshold) k_med_round: one CTA runs a whole round for
 //          its segment in shared memory (sample, tree, classify into a
 //          bucket array, local scan, stable move, child segments)
-//   small  (<= base_threshold) k_base_warp: one warp sorts a tile of packed
-//          small segments in registers by (run, key word, index), moving
-//          runs of equal key words 8 bytes deeper until all are decided,
-//          and writes out_perm and the LCP entries
+//   small  (<= base_threshold) k_base: one CTA sorts a tile of packed small
+//          segments, one thread per string, by ranking each element inside
+//          its run (key word, then index), moving runs of equal key words 8
+//          bytes deeper until all are decided; writes out_perm and the LCP
 //
 // Between rounds k_plan lays out the next device-wide round.  Equality
 // buckets whose splitter ends the string are finished runs (k_bigrun when
@@ -88,6 +88,7 @@ __device__ __forceinline__ void append_child(const Work& w, const Params& p, int
             w.small[s] = Seg{start, size, cdepth, 0u};
             w.small_size[s] = size;
             atomicAdd(&h->small_elems, size);
+            atomicAdd(&h->small_hist[min(31 - __clz(size), 7)], 1u);
         } else {
             atomicOr(&h->err, kErrSmallOverflow);
         }
@@ -140,8 +141,10 @@ __device__ __forceinline__ uint32_t refill_code(const BucketInfo& bi, uint32_t s
 __global__ void k_init(Work w) {
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < w.n; i += stride) {
+        const uint64_t o = w.offsets[i];
         w.idx[0][i] = i;
-        w.key[0][i] = load_key(w.chars, w.offsets[i]);
+        w.off[0][i] = o;
+        w.key[0][i] = load_key(w.chars, o);
         w.out_lcp[i] = 0u;
     }
 }
@@ -152,6 +155,7 @@ __global__ void k_hdr_reset(Work w) {
     h->small_elems = 0; h->med_elems = 0;
     h->refills = 0ull;
     h->base_iters = 0ull;
+    for (int i = 0; i < 8; i++) h->small_hist[i] = 0;
 }
 
 // Roots: one segment per set (a single sort is one set) at depth 0.
@@ -437,13 +441,15 @@ __device__ uint32_t scatter_range(const Work& w, int cur, uint32_t lo, uint32_t 
     constexpr int kBucketsPerThread = (NBCAP + kScatterThreads) / kScatterThreads;
     const uint64_t* key_in = w.key[cur];
     const uint32_t* idx_in = w.idx[cur];
+    const uint64_t* off_in = w.off[cur];
     uint64_t* key_out = w.key[cur ^ 1];
     uint32_t* idx_out = w.idx[cur ^ 1];
+    uint64_t* off_out = w.off[cur ^ 1];
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     const uint32_t lt = lanemask_lt();
     uint32_t nref = 0;
     for (uint32_t sub = lo; sub < hi; sub += kSubTile) {
-        uint64_t kk[kScatterItems];
+        uint64_t kk[kScatterItems], oo[kScatterItems];
         uint32_t ii[kScatterItems], bb[kScatterItems], loc[kScatterItems];
         const uint32_t wbase = sub + warp * (32u * kScatterItems) + lane;
 #pragma unroll
@@ -452,6 +458,7 @@ __device__ uint32_t scatter_range(const Work& w, int cur, uint32_t lo, uint32_t 
             const bool ok = e < hi;
             kk[j] = ok ? key_in[e] : 0ull;
             ii[j] = ok ? idx_in[e] : 0u;
+            oo[j] = ok ? off_in[e] : 0ull;
             if (kFromBid) bb[j] = ok ? bid[e - lo] : nb;
         }
         if (!kFromBid) {
@@ -504,7 +511,8 @@ __device__ uint32_t scatter_range(const Work& w, int cur, uint32_t lo, uint32_t 
                     w.out_perm[pos] = ii[j];
                 } else {
                     idx_out[pos] = ii[j];
-                    key_out[pos] = rd == kNoRefill ? kk[j] : load_key(w.chars, w.offsets[ii[j]] + rd);
+                    off_out[pos] = oo[j];
+                    key_out[pos] = rd == kNoRefill ? kk[j] : load_key(w.chars, oo[j] + rd);
                     nref += rd != kNoRefill;
                 }
             }
@@ -535,7 +543,7 @@ struct ScatterSmem {
     ScatterState<kNBMax> ss;
 };
 
-__global__ void __launch_bounds__(kScatterThreads) k_scatter(Work w, Params p, int cur, int med_out) {
+__global__ void __launch_bounds__(kScatterThreads, 3) k_scatter(Work w, Params p, int cur, int med_out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ScatterSmem& sm = *reinterpret_cast<ScatterSmem*>(smem_raw);
     const uint32_t c = blockIdx.x;
@@ -590,7 +598,7 @@ struct MedSmem {
 // One CTA runs one whole distribution round for one medium segment (the
 // sequential S^5 of the paper, here on one SM): sample, tree, classify into a
 // shared bucket array, local prefix sum, stable move, child segments.
-__global__ void __launch_bounds__(kScatterThreads) k_med_round(Work w, Params p, int cur, int med_in, int med_out) {
+__global__ void __launch_bounds__(kScatterThreads, 3) k_med_round(Work w, Params p, int cur, int med_in, int med_out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     MedSmem& sm = *reinterpret_cast<MedSmem*>(smem_raw);
     const Seg g = w.med[med_in][blockIdx.x];
@@ -644,190 +652,179 @@ __global__ void __launch_bounds__(kScatterThreads) k_med_round(Work w, Params p,
 
 // ------------------------------------------------------------ base case
 
-constexpr int kBaseWarps = 8;
+constexpr int kBaseThreads = kBaseCap;  // one thread per slot of a tile
 
-struct WarpTileSmem {
-    uint32_t sbase[kBaseWarps][kBaseMax + 2];  // first slot of each segment of the tile
-    uint32_t drun[kBaseWarps][kBaseCap];       // depth of the run that starts at a slot
+struct BaseSmem {
+    uint64_t K[kBaseCap];             // key word of the element in a slot
+    uint64_t O[kBaseCap];             // its string's byte offset
+    uint32_t I[kBaseCap];             // its string index
+    uint32_t drun[kBaseCap];          // depth of the run that starts at a slot
+    uint32_t RL[kBaseCap];            // length of the run that starts at a slot
+    uint32_t SR[kBaseCap];            // group of equal keys a slot belongs to
+    uint32_t sbase[kBaseMax + 2];     // first slot of each segment of the tile
+    uint32_t sbegin[kBaseMax + 2];    // its first position in the working arrays
+    uint16_t R[kBaseCap];             // first slot of the run a slot belongs to
+    uint32_t wmax[kBaseThreads / 32];
+    uint32_t lohi[2];
 };
 
-__device__ __forceinline__ bool el_less(uint32_t ra, uint64_t ka, uint32_t ia, uint32_t rb, uint64_t kb,
-                                        uint32_t ib) {
-    return ra != rb ? ra < rb : (ka != kb ? ka < kb : ia < ib);
+// First index i in [0, n) with a[i] >= x (n if none), a ascending; the warp
+// probes 32 positions per step.
+__device__ __forceinline__ uint32_t warp_lower_bound(const uint32_t* __restrict__ a, uint32_t n, uint32_t x) {
+    const uint32_t lane = threadIdx.x & 31u;
+    uint32_t lo = 0, hi = n;  // answer in [lo, hi]
+    while (hi - lo > 32u) {
+        const uint32_t p = lo + (uint32_t)(((uint64_t)(hi - lo) * (lane + 1u)) / 33u);
+        const uint32_t below = __ballot_sync(FULL_MASK, a[p] < x);
+        const uint32_t c = __popc(below);  // probes are increasing, so `below` is a prefix
+        const uint32_t plo = __shfl_sync(FULL_MASK, p, c ? c - 1u : 0u);
+        const uint32_t phi = __shfl_sync(FULL_MASK, p, c < 32u ? c : 31u);
+        if (c) lo = plo + 1u;
+        if (c < 32u) hi = phi;
+    }
+    const bool below = lo + lane < hi && a[lo + lane] < x;
+    return lo + (uint32_t)__popc(__ballot_sync(FULL_MASK, below));
 }
 
-// One warp per tile of packed small segments: the segments whose packed
-// start lies in [t*T, (t+1)*T) (T = base_threshold <= 16E), at most 2T - 1
-// <= 32E strings.  Lane l holds slots lE .. lE+E-1.  Each element carries
-// (run, key word, index); runs are contiguous slot ranges, so sorting by
-// (run, key, index) sorts every run in place.  Bitonic network: strides
-// below E inside a lane, larger strides by shuffles.  After each sort a key
-// change between neighbours fixes their LCP, equal key words holding the
-// terminator are equal strings, and runs of equal key words without it move
-// 8 bytes deeper (new word gathered) and are sorted again.
-template <int E>
-__global__ void __launch_bounds__(32 * kBaseWarps) k_base_warp(Work w, uint32_t T, int buf, uint32_t ns,
-                                                               uint32_t total) {
-    constexpr uint32_t CAP = 32u * E;
-    __shared__ WarpTileSmem sm;
-    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    const uint32_t tile = blockIdx.x * kBaseWarps + warp;
-    const uint32_t t0 = tile * T;
+// One CTA per tile of packed small segments: the segments whose packed start
+// lies in [t*T, (t+1)*T) (T = base_threshold <= kBaseMax), at most 2T - 1 <=
+// kBaseCap strings; thread s owns slot s.  A run is a contiguous slot range
+// whose strings share a prefix of drun[run] bytes, held in index order.
+// Each pass ranks every element of every active run among the run's
+// elements by (key word, slot) and moves it there (a stable sort of the
+// run); then a key change between neighbours fixes their LCP, equal key
+// words holding the terminator are equal strings, and groups of equal key
+// words without it become runs 8 bytes deeper (new words gathered) for the
+// next pass.
+__global__ void __launch_bounds__(kBaseThreads) k_base(Work w, uint32_t T, int buf, uint32_t ns, uint32_t total) {
+    __shared__ BaseSmem sm;
+    const uint32_t s = threadIdx.x;
+    const uint32_t lane = s & 31u, warp = s >> 5;
+    const uint32_t t0 = blockIdx.x * T;
     if (t0 >= total) return;
     const uint32_t t1 = min(t0 + T, total);
-    // segments with packed start in [t0, t1)
-    uint32_t lo, hi;
-    {
-        uint32_t a = 0, b = ns;
-        while (a < b) { uint32_t m = (a + b) >> 1; if (w.small_off[m] < t0) a = m + 1; else b = m; }
-        lo = a;
-        b = ns;
-        while (a < b) { uint32_t m = (a + b) >> 1; if (w.small_off[m] < t1) a = m + 1; else b = m; }
-        hi = a;
+    if (warp == 0) {
+        const uint32_t lo = warp_lower_bound(w.small_off, ns, t0);
+        const uint32_t hi = warp_lower_bound(w.small_off, ns, t1);
+        if (lane == 0) { sm.lohi[0] = lo; sm.lohi[1] = hi; }
     }
+    __syncthreads();
+    const uint32_t lo = sm.lohi[0], hi = sm.lohi[1];
     if (lo >= hi) return;
     const uint32_t slot0 = w.small_off[lo];
     const uint32_t cnt = (hi < ns ? w.small_off[hi] : total) - slot0;
     const uint32_t nseg = hi - lo;
-    uint32_t* sbase = sm.sbase[warp];
-    uint32_t* drun = sm.drun[warp];
-    for (uint32_t i = lane; i < nseg; i += 32) {
+    for (uint32_t i = s; i < nseg; i += blockDim.x) {
         const uint32_t b = w.small_off[lo + i] - slot0;
-        sbase[i] = b;
-        drun[b] = w.small[lo + i].depth;
+        const Seg g = w.small[lo + i];
+        sm.sbase[i] = b;
+        sm.sbegin[i] = g.begin;
+        sm.drun[b] = g.depth;
+        sm.RL[b] = g.size;
     }
-    __syncwarp();
-    const uint64_t* key_in = w.key[buf];
-    const uint32_t* idx_in = w.idx[buf];
-    uint64_t K[E];
-    uint32_t I[E], R[E], G[E];
-#pragma unroll
-    for (int j = 0; j < E; j++) {
-        const uint32_t s = lane * E + j;
-        if (s < cnt) {
-            uint32_t a = 0, b = nseg;  // last segment with sbase <= s
-            while (a < b) { uint32_t m = (a + b) >> 1; if (sbase[m] <= s) a = m + 1; else b = m; }
-            const uint32_t i = a - 1;
-            const uint32_t gpos = w.small[lo + i].begin + (s - sbase[i]);
-            G[j] = gpos;
-            R[j] = sbase[i];
-            K[j] = key_in[gpos];
-            I[j] = idx_in[gpos];
-        } else {
-            G[j] = 0;
-            R[j] = 0xFFFFFFFFu;
-            K[j] = ~0ull;
-            I[j] = 0xFFFFFFFFu;
-        }
+    __syncthreads();
+    bool act = s < cnt;  // the slot lies in a run to rank in this pass
+    uint32_t G = 0, id = 0;
+    uint64_t k = 0, o = 0;
+    if (act) {
+        uint32_t a = 0, b = nseg;  // last segment with sbase <= s
+        while (a < b) { uint32_t m = (a + b) >> 1; if (sm.sbase[m] <= s) a = m + 1; else b = m; }
+        const uint32_t i = a - 1;
+        G = sm.sbegin[i] + (s - sm.sbase[i]);
+        sm.R[s] = (uint16_t)sm.sbase[i];
+        k = w.key[buf][G];
+        id = w.idx[buf][G];
+        o = w.off[buf][G];
+        sm.K[s] = k;
     }
+    __syncthreads();
     uint32_t iter = 0;
     for (;; iter++) {
         if (iter >= kBaseMaxIters) {  // never expected: strings end, so runs end
-            if (lane == 0) atomicOr(&w.hdr->err, kErrBaseIters);
+            if (s == 0) atomicOr(&w.hdr->err, kErrBaseIters);
             return;
         }
-        // ---- sort by (run, key, index)
-#pragma unroll
-        for (int size = 2; size <= (int)CAP; size <<= 1) {
-#pragma unroll
-            for (int st = size >> 1; st > 0; st >>= 1) {
-                if (st < E) {
-#pragma unroll
-                    for (int j = 0; j < E; j++) {
-                        if ((j & st) == 0) {
-                            const int jj = j | st;
-                            const bool asc = ((lane * E + j) & size) == 0;
-                            const bool sw = asc ? el_less(R[jj], K[jj], I[jj], R[j], K[j], I[j])
-                                                : el_less(R[j], K[j], I[j], R[jj], K[jj], I[jj]);
-                            if (sw) {
-                                uint32_t tr = R[j]; R[j] = R[jj]; R[jj] = tr;
-                                uint64_t tk = K[j]; K[j] = K[jj]; K[jj] = tk;
-                                uint32_t ti = I[j]; I[j] = I[jj]; I[jj] = ti;
-                            }
-                        }
-                    }
+        // ---- rank inside the run: (key, slot) order keeps index order for ties
+        uint32_t np = s;
+        if (act) {
+            const uint32_t r = sm.R[s];
+            const uint32_t e = r + sm.RL[r];
+            uint32_t rank = 0, q = r;
+            for (; q + 4 <= e; q += 4) {
+                const uint64_t k0 = sm.K[q], k1 = sm.K[q + 1], k2 = sm.K[q + 2], k3 = sm.K[q + 3];
+                rank += (k0 < k || (k0 == k && q < s)) ? 1u : 0u;
+                rank += (k1 < k || (k1 == k && q + 1 < s)) ? 1u : 0u;
+                rank += (k2 < k || (k2 == k && q + 2 < s)) ? 1u : 0u;
+                rank += (k3 < k || (k3 == k && q + 3 < s)) ? 1u : 0u;
+            }
+            for (; q < e; q++) {
+                const uint64_t kq = sm.K[q];
+                rank += (kq < k || (kq == k && q < s)) ? 1u : 0u;
+            }
+            np = r + rank;
+        }
+        __syncthreads();
+        if (act) {
+            sm.K[np] = k;
+            sm.I[np] = id;
+            sm.O[np] = o;
+        }
+        __syncthreads();
+        // ---- decide neighbours inside the ranked runs
+        bool head = true;
+        uint32_t dold = 0;
+        if (act) {
+            k = sm.K[s];
+            id = sm.I[s];
+            o = sm.O[s];
+            const uint32_t r = sm.R[s];
+            dold = sm.drun[r];
+            if (s != r) {
+                const uint64_t pk = sm.K[s - 1];
+                if (pk != k) {
+                    w.out_lcp[G] = dold + key_lcp(pk, k);
                 } else {
-                    const int lm = st / E;
-                    const bool lower = (lane & (uint32_t)lm) == 0;
-#pragma unroll
-                    for (int j = 0; j < E; j++) {
-                        const uint32_t pr = __shfl_xor_sync(FULL_MASK, R[j], lm);
-                        const uint64_t pk = __shfl_xor_sync(FULL_MASK, K[j], lm);
-                        const uint32_t pi = __shfl_xor_sync(FULL_MASK, I[j], lm);
-                        const bool asc = ((lane * E + j) & size) == 0;
-                        const bool take = (lower == asc) ? el_less(pr, pk, pi, R[j], K[j], I[j])
-                                                         : el_less(R[j], K[j], I[j], pr, pk, pi);
-                        if (take) { R[j] = pr; K[j] = pk; I[j] = pi; }
-                    }
+                    head = false;
+                    if (key_ends(k)) w.out_lcp[G] = dold + key_chars(k);
                 }
             }
         }
-        // ---- decide neighbours
-        const uint64_t prevK = __shfl_up_sync(FULL_MASK, K[E - 1], 1);
-        uint32_t hv[E], dold[E];
-        uint32_t run = 0;
+        // groups of equal keys: inclusive max-scan of the heads over the slots
+        uint32_t inc = head ? s : 0u;
 #pragma unroll
-        for (int j = 0; j < E; j++) {
-            const uint32_t s = lane * E + j;
-            bool head = true;
-            dold[j] = 0;
-            if (s < cnt) {
-                dold[j] = drun[R[j]];
-                if (s != R[j]) {
-                    const uint64_t pk = j ? K[j - 1] : prevK;
-                    if (pk != K[j]) {
-                        w.out_lcp[G[j]] = dold[j] + key_lcp(pk, K[j]);
-                    } else {
-                        head = false;
-                        if (key_ends(K[j])) w.out_lcp[G[j]] = dold[j] + key_chars(K[j]);
-                    }
-                }
-            }
-            run = max(run, head ? s : 0u);
-            hv[j] = run;
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL_MASK, inc, d);
+            if (lane >= (uint32_t)d) inc = max(inc, y);
         }
-        // sub-run heads: inclusive max-scan over the slots
-        uint32_t inc = run;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(FULL_MASK, inc, o);
-            if (lane >= (uint32_t)o) inc = max(inc, y);
-        }
-        uint32_t ex = __shfl_up_sync(FULL_MASK, inc, 1);
-        if (lane == 0) ex = 0;
-        uint32_t SR[E];
-#pragma unroll
-        for (int j = 0; j < E; j++) SR[j] = max(ex, hv[j]);
-        const uint32_t nextSR0 = __shfl_down_sync(FULL_MASK, SR[0], 1);
-        __syncwarp();  // every lane read drun before any lane writes it
-        bool any = false;
-#pragma unroll
-        for (int j = 0; j < E; j++) {
-            const uint32_t s = lane * E + j;
-            if (s < cnt) {
-                const uint32_t nsr = (j + 1 < E) ? SR[(j + 1) % E] : nextSR0;
-                const bool multi = (s != SR[j]) || (s + 1 < cnt && nsr == s);
-                const bool act = multi && !key_ends(K[j]);
-                if (act) {
-                    const uint32_t d = dold[j] + 8u;
-                    if (s == SR[j]) drun[s] = d;
-                    K[j] = load_key(w.chars, w.offsets[I[j]] + d);
-                    R[j] = SR[j];
-                    any = true;
-                } else {
-                    R[j] = s;
+        if (lane == 31) sm.wmax[warp] = inc;
+        __syncthreads();
+        uint32_t sr = inc;
+        for (uint32_t v = 0; v < warp; v++) sr = max(sr, sm.wmax[v]);
+        sm.SR[s] = sr;
+        __syncthreads();
+        const bool multi = (s != sr) || (s + 1 < cnt && sm.SR[s + 1] == s);
+        const bool go = act && multi && !key_ends(k);
+        if (act) {
+            if (go) {
+                const uint32_t d = dold + 8u;
+                if (s == sr) {
+                    sm.drun[s] = d;
+                    sm.RL[s] = 0;
                 }
+                sm.R[s] = (uint16_t)sr;
+                k = load_key(w.chars, o + d);
+                sm.K[s] = k;
+            } else {
+                sm.R[s] = (uint16_t)s;
             }
         }
-        __syncwarp();
-        if (!__any_sync(FULL_MASK, any)) break;
+        __syncthreads();
+        if (go) atomicAdd(&sm.RL[sr], 1u);
+        act = go;
+        if (!__syncthreads_or(go)) break;
     }
-#pragma unroll
-    for (int j = 0; j < E; j++) {
-        const uint32_t s = lane * E + j;
-        if (s < cnt) w.out_perm[G[j]] = I[j];
-    }
-    if (lane == 0) atomicAdd(&w.hdr->base_iters, (unsigned long long)(iter + 1));
+    if (s < cnt) w.out_perm[G] = id;
+    if (s == 0) atomicAdd(&w.hdr->base_iters, (unsigned long long)(iter + 1));
 }
 
 // Buckets too large for the base case whose strings are all equal.
@@ -956,8 +953,10 @@ uint32_t device_sms() {
 
 cudaError_t launch_init(const Work& w, Prof* pf, cudaStream_t st) {
     if (w.n) {
-        // the shadow index array only ever holds valid string indices
+        // the shadow arrays only ever hold valid string indices and offsets
         cudaError_t e = cudaMemsetAsync(w.idx[1], 0, sizeof(uint32_t) * (size_t)w.n, st);
+        if (e != cudaSuccess) return e;
+        e = cudaMemsetAsync(w.off[1], 0, sizeof(uint64_t) * (size_t)w.n, st);  // offsets of string 0
         if (e != cudaSuccess) return e;
         ProfScope ps(pf, kInit, st);
         k_init<<<grid_for(w.n, 256, 16, device_sms()), 256, 0, st>>>(w);
@@ -1022,8 +1021,7 @@ cudaError_t launch_small(const Work& w, const Params& p, int buf, uint32_t n_sma
         if (e != cudaSuccess) return e;
         tiles = (small_total + p.base_threshold - 1) / p.base_threshold;
         ProfScope ps(pf, kBase, st);
-        k_base_warp<kBaseE><<<(tiles + kBaseWarps - 1) / kBaseWarps, 32 * kBaseWarps, 0, st>>>(
-            w, p.base_threshold, buf, n_small, small_total);
+        k_base<<<tiles, kBaseThreads, 0, st>>>(w, p.base_threshold, buf, n_small, small_total);
     }
     if (n_bigrun) {
         ProfScope ps(pf, kRuns, st);
