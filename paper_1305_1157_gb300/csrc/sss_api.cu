@@ -60,7 +60,7 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct Layout {
     size_t total = 0;
-    size_t o_key0, o_key1, o_idx0, o_idx1, o_off0, o_off1, o_counts, o_counts_scan, o_tlvl, o_tino, o_plans, o_chunk_seg,
+    size_t o_key0, o_key1, o_key20, o_key21, o_idx0, o_idx1, o_off0, o_off1, o_counts, o_counts_scan, o_tlvl, o_tino, o_plans, o_chunk_seg,
         o_large, o_med0, o_med1, o_small, o_small_size, o_small_off, o_bigrun, o_scan_tmp, o_hdr, o_roots;
     uint32_t cmax, tmax, lmax, chmax, smax, bmax, scan_tmp_max, mmax;
 };
@@ -109,6 +109,8 @@ Layout layout_for(uint32_t n, const sss_options& o, uint32_t num_roots) {
     auto take = [&](size_t bytes) { size_t r = off; off = align_up(off + bytes, 256); return r; };
     L.o_key0 = take(8 * nn);
     L.o_key1 = take(8 * nn);
+    L.o_key20 = take(8 * nn);
+    L.o_key21 = take(8 * nn);
     L.o_idx0 = take(4 * nn);
     L.o_idx1 = take(4 * nn);
     L.o_off0 = take(8 * nn);
@@ -140,6 +142,8 @@ Work make_work(const Layout& L, char* ws, const uint8_t* chars, const uint64_t* 
     w.chars = chars; w.offsets = offsets; w.n = n; w.out_perm = perm; w.out_lcp = lcp;
     w.key[0] = (uint64_t*)(ws + L.o_key0);
     w.key[1] = (uint64_t*)(ws + L.o_key1);
+    w.key2[0] = (uint64_t*)(ws + L.o_key20);
+    w.key2[1] = (uint64_t*)(ws + L.o_key21);
     w.idx[0] = (uint32_t*)(ws + L.o_idx0);
     w.idx[1] = (uint32_t*)(ws + L.o_idx1);
     w.off[0] = (uint64_t*)(ws + L.o_off0);

@@ -21,7 +21,10 @@ constexpr uint32_t kBaseMax = kBaseCap / 2;     // largest base-case bucket (128
 constexpr uint32_t kMedMax = 8192;              // largest bucket one CTA distributes alone
 constexpr int kMedKMax = 9;                     // its deepest tree: choose_k(8192) = 9
 constexpr int kMedNB = (2 << kMedKMax) - 1;     // 1023 buckets
-constexpr int kChunksPerSM = 8;                 // device-wide rounds: target work items per SM
+#ifndef SSS_CHUNKS_PER_SM
+#define SSS_CHUNKS_PER_SM 8
+#endif
+constexpr int kChunksPerSM = SSS_CHUNKS_PER_SM; // device-wide rounds: target work items per SM
 constexpr int kScatterThreads = 256;
 constexpr int kScatterItems = 8;
 constexpr uint32_t kSubTile = kScatterThreads * kScatterItems;  // 2048 strings
@@ -92,8 +95,9 @@ struct Work {
     uint32_t* out_lcp;
 
     uint64_t* key[2];        // cached key word of each position (ping-pong per round)
+    uint64_t* key2[2];       // the next 8 characters, valid when off's top bit is set
     uint32_t* idx[2];        // string index of each position
-    uint64_t* off[2];        // byte offset of that string, so refills read chars directly
+    uint64_t* off[2];        // byte offset of that string (refills read chars directly); top bit: key2 valid
     uint32_t* counts;        // [cmax] per (segment, bucket, chunk) counts
     uint32_t* counts_scan;   // [cmax] exclusive scan of counts
     uint64_t* tree_lvl;      // [tmax]
@@ -125,25 +129,91 @@ __device__ __forceinline__ uint64_t bswap64(uint64_t x) {
     return ((uint64_t)__byte_perm(lo, 0, 0x0123) << 32) | (uint64_t)__byte_perm(hi, 0, 0x0123);
 }
 
+// The first byte at or after `valid_from` (a byte index) that is zero, as a
+// mask of the bytes before it (all ones if there is none).
+__device__ __forceinline__ uint64_t keep_before_zero(uint64_t x) {
+    const uint64_t zm = zero_byte_mask(x);
+    if (!zm) return ~0ull;
+    const uint32_t nb = (uint32_t)(__ffsll((long long)zm) - 1) >> 3;  // bytes before the terminator
+    return nb ? (~0ull >> (64u - 8u * nb)) : 0ull;
+}
+
+// Key words (Sec. 3.1) of the 16 bytes at chars[off ..]: k1 = bytes
+// off..off+7, k2 = bytes off+8..off+15, each packed first-byte-most-
+// significant, every byte after the first 0 set to 0 (k2 = 0 when k1 holds
+// the terminator).  Reads only aligned 8-byte words; a word beyond the first
+// is read either because no terminator came before it (so it holds a string
+// byte) or, speculatively, because it lies in the same 4 KiB page as the
+// first word (which holds a string byte).  So no page the string does not
+// reach is ever touched.
+__device__ __forceinline__ void load_key2(const uint8_t* __restrict__ chars, uint64_t off, uint64_t& k1,
+                                          uint64_t& k2) {
+    const uint64_t addr = reinterpret_cast<uint64_t>(chars) + off;
+    const uint64_t a8 = addr & ~7ull;
+    const uint64_t* w = reinterpret_cast<const uint64_t*>(a8);
+    const uint32_t sh = (uint32_t)(addr & 7u) * 8u;
+    uint64_t w0, w1, w2;
+    if ((a8 & 4095u) <= 4096u - 24u) {  // all three words in one page
+        w0 = __ldg(w);
+        w1 = __ldg(w + 1);
+        w2 = sh ? __ldg(w + 2) : 0ull;
+    } else {
+        w0 = __ldg(w);
+        w1 = 0ull;
+        w2 = 0ull;
+        if ((zero_byte_mask(w0 >> sh) & (~0ull >> sh)) == 0) {
+            w1 = __ldg(w + 1);
+            if (sh && zero_byte_mask(w1) == 0) w2 = __ldg(w + 2);
+        }
+    }
+    uint64_t r1 = sh ? (w0 >> sh) | (w1 << (64u - sh)) : w0;
+    uint64_t r2 = sh ? (w1 >> sh) | (w2 << (64u - sh)) : w1;
+    const uint64_t m1 = keep_before_zero(r1);
+    if (m1 != ~0ull) {
+        r1 &= m1;
+        r2 = 0ull;
+    } else {
+        r2 &= keep_before_zero(r2);
+    }
+    k1 = bswap64(r1);
+    k2 = bswap64(r2);
+}
+
 // Key word (Sec. 3.1): bytes chars[off .. off+7] packed first-byte-most-
-// significant, bytes after the first 0 set to 0.  Reads only aligned 8-byte
-// words that hold at least one byte of the string (terminator included):
-// the second word is read only if the first holds no terminator.
+// significant, bytes after the first 0 set to 0 (same reading rule as
+// load_key2).
 __device__ __forceinline__ uint64_t load_key(const uint8_t* __restrict__ chars, uint64_t off) {
     const uint64_t addr = reinterpret_cast<uint64_t>(chars) + off;
-    const uint64_t* w = reinterpret_cast<const uint64_t*>(addr & ~7ull);
+    const uint64_t a8 = addr & ~7ull;
+    const uint64_t* w = reinterpret_cast<const uint64_t*>(a8);
     const uint32_t sh = (uint32_t)(addr & 7u) * 8u;
-    uint64_t lo = __ldg(w) >> sh;
-    if (sh) {
-        const uint64_t valid = ~0ull >> sh;  // bytes of the first word at or after off
-        if ((zero_byte_mask(lo) & valid) == 0) lo |= __ldg(w + 1) << (64u - sh);
+    uint64_t lo;
+    if (sh && (a8 & 4095u) <= 4096u - 16u) {
+        lo = (__ldg(w) >> sh) | (__ldg(w + 1) << (64u - sh));
+    } else {
+        lo = __ldg(w) >> sh;
+        if (sh && (zero_byte_mask(lo) & (~0ull >> sh)) == 0) lo |= __ldg(w + 1) << (64u - sh);
     }
-    const uint64_t zm = zero_byte_mask(lo);
-    if (zm) {
-        const uint32_t nb = (uint32_t)(__ffsll((long long)zm) - 1) >> 3;  // bytes before the terminator
-        lo = nb ? (lo & (~0ull >> (64u - 8u * nb))) : 0ull;
+    return bswap64(lo & keep_before_zero(lo));
+}
+
+// Characters cached per string: the key word at the current depth (k1) and,
+// when the top bit of the carried offset is set, the next word (k2).  A
+// refill that moves delta <= 8 bytes deeper takes its word from the cache
+// (and empties it); otherwise 16 bytes are gathered (caching of characters,
+// Sec. 2.2, with 16 characters instead of 8).
+constexpr uint64_t kK2Valid = 1ull << 63;
+constexpr uint64_t kOffMask = ~kK2Valid;
+
+__device__ __forceinline__ void refill(const uint8_t* __restrict__ chars, uint64_t& k1, uint64_t& k2,
+                                       uint64_t& o, uint32_t new_depth, uint32_t delta) {
+    if ((o & kK2Valid) && delta <= 8u) {
+        k1 = delta == 8u ? k2 : (k1 << (8u * delta)) | (k2 >> (64u - 8u * delta));
+        o &= kOffMask;
+    } else {
+        load_key2(chars, (o & kOffMask) + new_depth, k1, k2);
+        o |= kK2Valid;
     }
-    return bswap64(lo);
 }
 
 // LCP in bytes of two different key words (XOR + count leading zeros, Sec. 3.1).

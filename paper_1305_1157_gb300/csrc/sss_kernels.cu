@@ -142,9 +142,12 @@ __global__ void k_init(Work w) {
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < w.n; i += stride) {
         const uint64_t o = w.offsets[i];
+        uint64_t k1, k2;
+        load_key2(w.chars, o, k1, k2);
         w.idx[0][i] = i;
-        w.off[0][i] = o;
-        w.key[0][i] = load_key(w.chars, o);
+        w.off[0][i] = o | kK2Valid;
+        w.key[0][i] = k1;
+        w.key2[0][i] = k2;
         w.out_lcp[i] = 0u;
     }
 }
@@ -419,6 +422,9 @@ __global__ void __launch_bounds__(kClassifyThreads) k_classify(Work w, Params p,
 // ------------------------------------------------------------ stable scatter
 
 constexpr int kScatterWarps = kScatterThreads / 32;
+#ifndef SSS_SCATTER_MIN_BLOCKS
+#define SSS_SCATTER_MIN_BLOCKS 2
+#endif
 
 template <int NBCAP>
 struct ScatterState {
@@ -437,19 +443,21 @@ struct ScatterState {
 template <int NBCAP, bool kFromBid>
 __device__ uint32_t scatter_range(const Work& w, int cur, uint32_t lo, uint32_t hi, uint32_t nb,
                                   ScatterState<NBCAP>& ss, const uint64_t* t, const uint64_t* ino, int k,
-                                  const uint16_t* bid, uint32_t seg_end) {
+                                  const uint16_t* bid, uint32_t seg_end, uint32_t depth) {
     constexpr int kBucketsPerThread = (NBCAP + kScatterThreads) / kScatterThreads;
     const uint64_t* key_in = w.key[cur];
     const uint32_t* idx_in = w.idx[cur];
     const uint64_t* off_in = w.off[cur];
+    const uint64_t* key2_in = w.key2[cur];
     uint64_t* key_out = w.key[cur ^ 1];
     uint32_t* idx_out = w.idx[cur ^ 1];
     uint64_t* off_out = w.off[cur ^ 1];
+    uint64_t* key2_out = w.key2[cur ^ 1];
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     const uint32_t lt = lanemask_lt();
     uint32_t nref = 0;
     for (uint32_t sub = lo; sub < hi; sub += kSubTile) {
-        uint64_t kk[kScatterItems], oo[kScatterItems];
+        uint64_t kk[kScatterItems], oo[kScatterItems], k2[kScatterItems];
         uint32_t ii[kScatterItems], bb[kScatterItems], loc[kScatterItems];
         const uint32_t wbase = sub + warp * (32u * kScatterItems) + lane;
 #pragma unroll
@@ -459,6 +467,7 @@ __device__ uint32_t scatter_range(const Work& w, int cur, uint32_t lo, uint32_t 
             kk[j] = ok ? key_in[e] : 0ull;
             ii[j] = ok ? idx_in[e] : 0u;
             oo[j] = ok ? off_in[e] : 0ull;
+            k2[j] = ok ? key2_in[e] : 0ull;
             if (kFromBid) bb[j] = ok ? bid[e - lo] : nb;
         }
         if (!kFromBid) {
@@ -510,10 +519,15 @@ __device__ uint32_t scatter_range(const Work& w, int cur, uint32_t lo, uint32_t 
                 } else if (rd == kSingle) {
                     w.out_perm[pos] = ii[j];
                 } else {
+                    uint64_t k = kk[j], kx = k2[j], o = oo[j];
+                    if (rd != kNoRefill) {
+                        refill(w.chars, k, kx, o, rd, rd - depth);
+                        nref++;
+                    }
                     idx_out[pos] = ii[j];
-                    off_out[pos] = oo[j];
-                    key_out[pos] = rd == kNoRefill ? kk[j] : load_key(w.chars, oo[j] + rd);
-                    nref += rd != kNoRefill;
+                    off_out[pos] = o;
+                    key_out[pos] = k;
+                    key2_out[pos] = kx;
                 }
             }
         }
@@ -543,7 +557,7 @@ struct ScatterSmem {
     ScatterState<kNBMax> ss;
 };
 
-__global__ void __launch_bounds__(kScatterThreads, 3) k_scatter(Work w, Params p, int cur, int med_out) {
+__global__ void __launch_bounds__(kScatterThreads, SSS_SCATTER_MIN_BLOCKS) k_scatter(Work w, Params p, int cur, int med_out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ScatterSmem& sm = *reinterpret_cast<ScatterSmem*>(smem_raw);
     const uint32_t c = blockIdx.x;
@@ -577,7 +591,8 @@ __global__ void __launch_bounds__(kScatterThreads, 3) k_scatter(Work w, Params p
     __syncthreads();
     const uint32_t lo = P.begin + ci * P.chunk;
     const uint32_t hi = min(lo + P.chunk, seg_end);
-    const uint32_t nref = scatter_range<kNBMax, false>(w, cur, lo, hi, nb, sm.ss, sm.t, sm.ino, k, nullptr, seg_end);
+    const uint32_t nref =
+        scatter_range<kNBMax, false>(w, cur, lo, hi, nb, sm.ss, sm.t, sm.ino, k, nullptr, seg_end, P.depth);
     add_refills(w, nref);
 }
 
@@ -598,7 +613,7 @@ struct MedSmem {
 // One CTA runs one whole distribution round for one medium segment (the
 // sequential S^5 of the paper, here on one SM): sample, tree, classify into a
 // shared bucket array, local prefix sum, stable move, child segments.
-__global__ void __launch_bounds__(kScatterThreads, 3) k_med_round(Work w, Params p, int cur, int med_in, int med_out) {
+__global__ void __launch_bounds__(kScatterThreads, SSS_SCATTER_MIN_BLOCKS) k_med_round(Work w, Params p, int cur, int med_in, int med_out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     MedSmem& sm = *reinterpret_cast<MedSmem*>(smem_raw);
     const Seg g = w.med[med_in][blockIdx.x];
@@ -646,7 +661,8 @@ __global__ void __launch_bounds__(kScatterThreads, 3) k_med_round(Work w, Params
     }
     __syncthreads();
     const uint32_t nref =
-        scatter_range<kMedNB, true>(w, cur, g.begin, g.begin + m, nb, sm.ss, sm.t, sm.ino, k, sm.bid, g.begin + m);
+        scatter_range<kMedNB, true>(w, cur, g.begin, g.begin + m, nb, sm.ss, sm.t, sm.ino, k, sm.bid, g.begin + m,
+                                    g.depth);
     add_refills(w, nref);
 }
 
@@ -656,6 +672,7 @@ constexpr int kBaseThreads = kBaseCap;  // one thread per slot of a tile
 
 struct BaseSmem {
     uint64_t K[kBaseCap];             // key word of the element in a slot
+    uint64_t K2[kBaseCap];            // the next 8 characters (valid per O's top bit)
     uint64_t O[kBaseCap];             // its string's byte offset
     uint32_t I[kBaseCap];             // its string index
     uint32_t drun[kBaseCap];          // depth of the run that starts at a slot
@@ -725,7 +742,7 @@ __global__ void __launch_bounds__(kBaseThreads) k_base(Work w, uint32_t T, int b
     __syncthreads();
     bool act = s < cnt;  // the slot lies in a run to rank in this pass
     uint32_t G = 0, id = 0;
-    uint64_t k = 0, o = 0;
+    uint64_t k = 0, k2 = 0, o = 0;
     if (act) {
         uint32_t a = 0, b = nseg;  // last segment with sbase <= s
         while (a < b) { uint32_t m = (a + b) >> 1; if (sm.sbase[m] <= s) a = m + 1; else b = m; }
@@ -733,6 +750,7 @@ __global__ void __launch_bounds__(kBaseThreads) k_base(Work w, uint32_t T, int b
         G = sm.sbegin[i] + (s - sm.sbase[i]);
         sm.R[s] = (uint16_t)sm.sbase[i];
         k = w.key[buf][G];
+        k2 = w.key2[buf][G];
         id = w.idx[buf][G];
         o = w.off[buf][G];
         sm.K[s] = k;
@@ -766,6 +784,7 @@ __global__ void __launch_bounds__(kBaseThreads) k_base(Work w, uint32_t T, int b
         __syncthreads();
         if (act) {
             sm.K[np] = k;
+            sm.K2[np] = k2;
             sm.I[np] = id;
             sm.O[np] = o;
         }
@@ -775,6 +794,7 @@ __global__ void __launch_bounds__(kBaseThreads) k_base(Work w, uint32_t T, int b
         uint32_t dold = 0;
         if (act) {
             k = sm.K[s];
+            k2 = sm.K2[s];
             id = sm.I[s];
             o = sm.O[s];
             const uint32_t r = sm.R[s];
@@ -812,7 +832,7 @@ __global__ void __launch_bounds__(kBaseThreads) k_base(Work w, uint32_t T, int b
                     sm.RL[s] = 0;
                 }
                 sm.R[s] = (uint16_t)sr;
-                k = load_key(w.chars, o + d);
+                refill(w.chars, k, k2, o, d, 8u);
                 sm.K[s] = k;
             } else {
                 sm.R[s] = (uint16_t)s;
