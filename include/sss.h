@@ -136,7 +136,7 @@ int sss_sort_ws(const uint8_t* chars, const uint64_t* offsets, uint32_t n,
  * nearly all device memory (a stray cudaMalloc fails or fragments it),
  * latency-critical loops (cudaMalloc and cudaFree can synchronise the whole
  * device), or hosts whose policy forbids allocation after start-up.
- * Scratch is a 6 MiB static device array inside this library, held by every
+ * Scratch is an 8 MiB static device array inside this library, held by every
  * GPU that loads the library until the process exits; the call itself
  * allocates nothing (no cudaMalloc, cudaFree or pinned host memory; the
  * per-round header is read into static host memory, and profiling is off).

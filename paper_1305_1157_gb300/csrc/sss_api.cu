@@ -60,7 +60,7 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct Layout {
     size_t total = 0;
-    size_t o_key0, o_key1, o_key20, o_key21, o_idx0, o_idx1, o_off0, o_off1, o_counts, o_counts_scan, o_tlvl, o_tino, o_plans, o_chunk_seg,
+    size_t o_rec0, o_rec1, o_counts, o_counts_scan, o_tlvl, o_tino, o_plans, o_chunk_seg,
         o_large, o_med0, o_med1, o_small, o_small_size, o_small_off, o_bigrun, o_scan_tmp, o_hdr, o_roots;
     uint32_t cmax, tmax, lmax, chmax, smax, bmax, scan_tmp_max, mmax;
 };
@@ -107,14 +107,8 @@ Layout layout_for(uint32_t n, const sss_options& o, uint32_t num_roots) {
     L.mmax = (uint32_t)mmax;
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t r = off; off = align_up(off + bytes, 256); return r; };
-    L.o_key0 = take(8 * nn);
-    L.o_key1 = take(8 * nn);
-    L.o_key20 = take(8 * nn);
-    L.o_key21 = take(8 * nn);
-    L.o_idx0 = take(4 * nn);
-    L.o_idx1 = take(4 * nn);
-    L.o_off0 = take(8 * nn);
-    L.o_off1 = take(8 * nn);
+    L.o_rec0 = take(sizeof(Rec) * nn);
+    L.o_rec1 = take(sizeof(Rec) * nn);
     L.o_counts = take(4 * (cmax + 1));
     L.o_counts_scan = take(4 * (cmax + 1));
     L.o_tlvl = take(8 * tmax);
@@ -140,14 +134,8 @@ Work make_work(const Layout& L, char* ws, const uint8_t* chars, const uint64_t* 
     Work w;
     memset(&w, 0, sizeof(w));
     w.chars = chars; w.offsets = offsets; w.n = n; w.out_perm = perm; w.out_lcp = lcp;
-    w.key[0] = (uint64_t*)(ws + L.o_key0);
-    w.key[1] = (uint64_t*)(ws + L.o_key1);
-    w.key2[0] = (uint64_t*)(ws + L.o_key20);
-    w.key2[1] = (uint64_t*)(ws + L.o_key21);
-    w.idx[0] = (uint32_t*)(ws + L.o_idx0);
-    w.idx[1] = (uint32_t*)(ws + L.o_idx1);
-    w.off[0] = (uint64_t*)(ws + L.o_off0);
-    w.off[1] = (uint64_t*)(ws + L.o_off1);
+    w.rec[0] = (Rec*)(ws + L.o_rec0);
+    w.rec[1] = (Rec*)(ws + L.o_rec1);
     w.counts = (uint32_t*)(ws + L.o_counts);
     w.counts_scan = (uint32_t*)(ws + L.o_counts_scan);
     w.tree_lvl = (uint64_t*)(ws + L.o_tlvl);
@@ -472,7 +460,7 @@ const char* sss_version(void) { return "sss-gb300 0.1"; }
 namespace {
 
 constexpr uint32_t kNoAllocMaxStrings = 1u << 16;
-constexpr size_t kNoAllocScratchBytes = (size_t)6 << 20;
+constexpr size_t kNoAllocScratchBytes = (size_t)8 << 20;
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 

@@ -34,6 +34,32 @@ constexpr uint32_t kSingle = 0xFFFFFFFEu;       // bucket of one string: finishe
 
 // ------------------------------------------------------------ structures
 
+// One string in the working arrays: its cached characters, where it lives,
+// and its index.  32 bytes, so a string moved to a scattered position is one
+// whole 32-byte sector write.
+struct __align__(32) Rec {
+    uint64_t key;   // key word at the segment's depth (Sec. 3.1)
+    uint64_t key2;  // the next 8 characters, valid when off's top bit is set
+    uint64_t off;   // byte offset of the string in chars; top bit: key2 valid
+    uint32_t idx;   // original index
+    uint32_t pad;
+};
+
+__device__ __forceinline__ Rec load_rec(const Rec* p) {
+    const ulonglong2* q = reinterpret_cast<const ulonglong2*>(p);
+    const ulonglong2 a = q[0], b = q[1];
+    Rec r;
+    r.key = a.x; r.key2 = a.y; r.off = b.x;
+    r.idx = (uint32_t)b.y; r.pad = (uint32_t)(b.y >> 32);
+    return r;
+}
+
+__device__ __forceinline__ void store_rec(Rec* p, const Rec& r) {
+    ulonglong2* q = reinterpret_cast<ulonglong2*>(p);
+    q[0] = make_ulonglong2(r.key, r.key2);
+    q[1] = make_ulonglong2(r.off, (uint64_t)r.idx);
+}
+
 // A range of positions [begin, begin + size) of the working arrays whose
 // strings share their first `depth` bytes (the common prefix l of Sec. 3.1).
 struct Seg {
@@ -94,10 +120,7 @@ struct Work {
     uint32_t* out_perm;
     uint32_t* out_lcp;
 
-    uint64_t* key[2];        // cached key word of each position (ping-pong per round)
-    uint64_t* key2[2];       // the next 8 characters, valid when off's top bit is set
-    uint32_t* idx[2];        // string index of each position
-    uint64_t* off[2];        // byte offset of that string (refills read chars directly); top bit: key2 valid
+    Rec* rec[2];             // the string at each position (ping-pong per round)
     uint32_t* counts;        // [cmax] per (segment, bucket, chunk) counts
     uint32_t* counts_scan;   // [cmax] exclusive scan of counts
     uint64_t* tree_lvl;      // [tmax]

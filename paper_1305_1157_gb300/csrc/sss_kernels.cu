@@ -142,12 +142,12 @@ __global__ void k_init(Work w) {
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < w.n; i += stride) {
         const uint64_t o = w.offsets[i];
-        uint64_t k1, k2;
-        load_key2(w.chars, o, k1, k2);
-        w.idx[0][i] = i;
-        w.off[0][i] = o | kK2Valid;
-        w.key[0][i] = k1;
-        w.key2[0][i] = k2;
+        Rec r;
+        load_key2(w.chars, o, r.key, r.key2);
+        r.off = o | kK2Valid;
+        r.idx = i;
+        r.pad = 0;
+        store_rec(&w.rec[0][i], r);
         w.out_lcp[i] = 0u;
     }
 }
@@ -341,9 +341,9 @@ __global__ void __launch_bounds__(1024) k_sample(Work w, Params p, int cur) {
     const int k = (int)P.k;
     const uint32_t pw = 2u << k;
     const uint32_t cnt = pw - 1u;  // alpha (v + 1) - 1 with alpha = 2
-    const uint64_t* keys = w.key[cur];
+    const Rec* recs = w.rec[cur];
     for (uint32_t j = threadIdx.x; j < pw; j += blockDim.x)
-        samp[j] = j < cnt ? keys[P.begin + sample_pos(p.seed, P.begin, P.size, j)] : ~0ull;
+        samp[j] = j < cnt ? recs[P.begin + sample_pos(p.seed, P.begin, P.size, j)].key : ~0ull;
     __syncthreads();
     bitonic_sort_u64(samp, pw);
     select_splitters(samp, cnt, k, lvl, ra, rb);
@@ -370,10 +370,10 @@ __global__ void __launch_bounds__(1024) k_build_splitters(const uint64_t* sample
 constexpr int kClassifyThreads = 256;
 constexpr int kClassifyUnroll = 4;
 
-// Adds the buckets of keys[lo, hi) to hist (warp-aggregated shared atomics);
+// Adds the buckets of the key words of recs[lo, hi) to hist (warp-aggregated shared atomics);
 // bid (optional) receives each bucket at bid[e - lo].  Loop bounds are
 // uniform over the block.
-__device__ __forceinline__ void classify_range(const uint64_t* __restrict__ keys, uint32_t lo, uint32_t hi,
+__device__ __forceinline__ void classify_range(const Rec* __restrict__ recs, uint32_t lo, uint32_t hi,
                                                const uint64_t* t, const uint64_t* ino, int k, uint32_t nb,
                                                uint32_t* hist, uint16_t* bid) {
     const uint32_t lane = threadIdx.x & 31u;
@@ -382,7 +382,7 @@ __device__ __forceinline__ void classify_range(const uint64_t* __restrict__ keys
 #pragma unroll
         for (int u = 0; u < kClassifyUnroll; u++) {
             const uint32_t e = base + u * blockDim.x + threadIdx.x;
-            kk[u] = e < hi ? keys[e] : 0ull;
+            kk[u] = e < hi ? recs[e].key : 0ull;
         }
 #pragma unroll
         for (int u = 0; u < kClassifyUnroll; u++) {
@@ -413,7 +413,7 @@ __global__ void __launch_bounds__(kClassifyThreads) k_classify(Work w, Params p,
     __syncthreads();
     const uint32_t lo = P.begin + ci * P.chunk;
     const uint32_t hi = min(lo + P.chunk, P.begin + P.size);
-    classify_range(w.key[cur], lo, hi, t, ino, k, nb, hist, nullptr);
+    classify_range(w.rec[cur], lo, hi, t, ino, k, nb, hist, nullptr);
     __syncthreads();
     for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x)
         w.counts[P.count_base + b * P.chunks + ci] = hist[b];
@@ -445,36 +445,38 @@ __device__ uint32_t scatter_range(const Work& w, int cur, uint32_t lo, uint32_t 
                                   ScatterState<NBCAP>& ss, const uint64_t* t, const uint64_t* ino, int k,
                                   const uint16_t* bid, uint32_t seg_end, uint32_t depth) {
     constexpr int kBucketsPerThread = (NBCAP + kScatterThreads) / kScatterThreads;
-    const uint64_t* key_in = w.key[cur];
-    const uint32_t* idx_in = w.idx[cur];
-    const uint64_t* off_in = w.off[cur];
-    const uint64_t* key2_in = w.key2[cur];
-    uint64_t* key_out = w.key[cur ^ 1];
-    uint32_t* idx_out = w.idx[cur ^ 1];
-    uint64_t* off_out = w.off[cur ^ 1];
-    uint64_t* key2_out = w.key2[cur ^ 1];
+    const Rec* rec_in = w.rec[cur];
+    Rec* rec_out = w.rec[cur ^ 1];
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     const uint32_t lt = lanemask_lt();
     uint32_t nref = 0;
     for (uint32_t sub = lo; sub < hi; sub += kSubTile) {
-        uint64_t kk[kScatterItems], oo[kScatterItems], k2[kScatterItems];
-        uint32_t ii[kScatterItems], bb[kScatterItems], loc[kScatterItems];
+        Rec rr[kScatterItems];
+        uint32_t bb[kScatterItems], loc[kScatterItems];
         const uint32_t wbase = sub + warp * (32u * kScatterItems) + lane;
 #pragma unroll
         for (int j = 0; j < kScatterItems; j++) {
             const uint32_t e = wbase + j * 32u;
             const bool ok = e < hi;
-            kk[j] = ok ? key_in[e] : 0ull;
-            ii[j] = ok ? idx_in[e] : 0u;
-            oo[j] = ok ? off_in[e] : 0ull;
-            k2[j] = ok ? key2_in[e] : 0ull;
+            if (ok) rr[j] = load_rec(rec_in + e);
+            else rr[j] = Rec{0ull, 0ull, 0ull, 0u, 0u};
             if (kFromBid) bb[j] = ok ? bid[e - lo] : nb;
         }
         if (!kFromBid) {
 #pragma unroll
             for (int j = 0; j < kScatterItems; j++) {
                 const uint32_t e = wbase + j * 32u;
-                bb[j] = e < hi ? classify_key(kk[j], t, ino, k) : nb;
+                bb[j] = e < hi ? classify_key(rr[j].key, t, ino, k) : nb;
+            }
+        }
+        // next key words of strings whose bucket moves deeper: all gathers are
+        // issued here, before any store, and complete during the ranking
+#pragma unroll
+        for (int j = 0; j < kScatterItems; j++) {
+            const uint32_t rd = bb[j] < nb ? ss.rdep[bb[j]] : kNoRefill;
+            if (rd != kNoRefill && rd != kSingle) {
+                refill(w.chars, rr[j].key, rr[j].key2, rr[j].off, rd, rd - depth);
+                nref++;
             }
         }
 #pragma unroll
@@ -517,17 +519,9 @@ __device__ uint32_t scatter_range(const Work& w, int cur, uint32_t lo, uint32_t 
                 if (pos >= seg_end) {
                     atomicOr(&w.hdr->err, kErrPosition);
                 } else if (rd == kSingle) {
-                    w.out_perm[pos] = ii[j];
+                    w.out_perm[pos] = rr[j].idx;
                 } else {
-                    uint64_t k = kk[j], kx = k2[j], o = oo[j];
-                    if (rd != kNoRefill) {
-                        refill(w.chars, k, kx, o, rd, rd - depth);
-                        nref++;
-                    }
-                    idx_out[pos] = ii[j];
-                    off_out[pos] = o;
-                    key_out[pos] = k;
-                    key2_out[pos] = kx;
+                    store_rec(rec_out + pos, rr[j]);
                 }
             }
         }
@@ -572,20 +566,36 @@ __global__ void __launch_bounds__(kScatterThreads, SSS_SCATTER_MIN_BLOCKS) k_sca
     }
     __syncthreads();
     const uint32_t* S = w.counts_scan + P.count_base;
-    const uint32_t S0 = S[0];
     const uint32_t seg_end = P.begin + P.size;
-    for (uint32_t b = threadIdx.x; b <= nb; b += blockDim.x) {
-        for (int q = 0; q < kScatterWarps; q++) sm.ss.whist[q][b] = 0;
-        if (b == nb) continue;
-        const uint32_t start = P.begin + (S[b * P.chunks] - S0);
-        const uint32_t end = (b + 1 < nb) ? P.begin + (S[(b + 1) * P.chunks] - S0) : seg_end;
-        const uint32_t size = end - start;
-        sm.ss.run_pos[b] = P.begin + (S[b * P.chunks + ci] - S0);
-        const BucketInfo bi = bucket_info(b, nb, P.depth, sm.ino, size);
-        sm.ss.rdep[b] = refill_code(bi, size, P.depth);
-        if (ci == 0 && size > 0) {
-            if (start > P.begin) w.out_lcp[start] = kLcpFlag | P.depth;
-            append_child(w, p, med_out, start, size, bi.cdepth, bi.isrun, bi.runlcp);
+    // bucket b starts at S[b * chunks] and this chunk's part of it at
+    // S[b * chunks + ci] (relative to S[0]): issue every load first
+    constexpr int kBPT = (kNBMax + kScatterThreads) / kScatterThreads;
+    uint32_t s_first[kBPT], s_next[kBPT], s_mine[kBPT];
+    const uint32_t S0 = S[0];
+#pragma unroll
+    for (int q = 0; q < kBPT; q++) {
+        const uint32_t b = threadIdx.x + q * kScatterThreads;
+        s_first[q] = b < nb ? S[b * P.chunks] : 0u;
+        s_mine[q] = b < nb ? S[b * P.chunks + ci] : 0u;
+        s_next[q] = b + 1 < nb ? S[(b + 1) * P.chunks] : 0u;
+    }
+#pragma unroll
+    for (int q = 0; q < kBPT; q++) {
+        const uint32_t b = threadIdx.x + q * kScatterThreads;
+        if (b <= nb) {
+            for (int ww = 0; ww < kScatterWarps; ww++) sm.ss.whist[ww][b] = 0;
+        }
+        if (b < nb) {
+            const uint32_t start = P.begin + (s_first[q] - S0);
+            const uint32_t end = (b + 1 < nb) ? P.begin + (s_next[q] - S0) : seg_end;
+            const uint32_t size = end - start;
+            sm.ss.run_pos[b] = P.begin + (s_mine[q] - S0);
+            const BucketInfo bi = bucket_info(b, nb, P.depth, sm.ino, size);
+            sm.ss.rdep[b] = refill_code(bi, size, P.depth);
+            if (ci == 0 && size > 0) {
+                if (start > P.begin) w.out_lcp[start] = kLcpFlag | P.depth;
+                append_child(w, p, med_out, start, size, bi.cdepth, bi.isrun, bi.runlcp);
+            }
         }
     }
     __syncthreads();
@@ -621,9 +631,9 @@ __global__ void __launch_bounds__(kScatterThreads, SSS_SCATTER_MIN_BLOCKS) k_med
     const int k = choose_k(m, min(p.k_max, kMedKMax));
     const uint32_t v = (1u << k) - 1u, nb = 2u * v + 1u;
     const uint32_t pw = 2u << k, cnt = pw - 1u;
-    const uint64_t* keys = w.key[cur];
+    const Rec* recs = w.rec[cur];
     for (uint32_t j = threadIdx.x; j < pw; j += blockDim.x)
-        sm.samp[j] = j < cnt ? keys[g.begin + sample_pos(p.seed, g.begin, m, j)] : ~0ull;
+        sm.samp[j] = j < cnt ? recs[g.begin + sample_pos(p.seed, g.begin, m, j)].key : ~0ull;
     for (uint32_t b = threadIdx.x; b <= nb; b += blockDim.x) {
         sm.hist[b] = 0;
         for (int q = 0; q < kScatterWarps; q++) sm.ss.whist[q][b] = 0;
@@ -632,7 +642,7 @@ __global__ void __launch_bounds__(kScatterThreads, SSS_SCATTER_MIN_BLOCKS) k_med
     bitonic_sort_u64(sm.samp, pw);
     select_splitters(sm.samp, cnt, k, sm.lvl, sm.ra, sm.rb);
     emit_tree(sm.lvl, k, sm.t + 1, sm.ino);
-    classify_range(keys, g.begin, g.begin + m, sm.t, sm.ino, k, nb, sm.hist, sm.bid);
+    classify_range(recs, g.begin, g.begin + m, sm.t, sm.ino, k, nb, sm.hist, sm.bid);
     __syncthreads();
     // bucket starts: consecutive buckets per thread
     constexpr int kPer = (kMedNB + 1) / kScatterThreads;
@@ -749,10 +759,11 @@ __global__ void __launch_bounds__(kBaseThreads) k_base(Work w, uint32_t T, int b
         const uint32_t i = a - 1;
         G = sm.sbegin[i] + (s - sm.sbase[i]);
         sm.R[s] = (uint16_t)sm.sbase[i];
-        k = w.key[buf][G];
-        k2 = w.key2[buf][G];
-        id = w.idx[buf][G];
-        o = w.off[buf][G];
+        const Rec r = load_rec(&w.rec[buf][G]);
+        k = r.key;
+        k2 = r.key2;
+        id = r.idx;
+        o = r.off;
         sm.K[s] = k;
     }
     __syncthreads();
@@ -853,7 +864,7 @@ __global__ void k_bigrun(Work w, int buf, uint32_t nrun) {
         const Seg g = w.bigrun[r];
         for (uint32_t i = threadIdx.x; i < g.size; i += blockDim.x) {
             const uint32_t q = g.begin + i;
-            w.out_perm[q] = w.idx[buf][q];
+            w.out_perm[q] = w.rec[buf][q].idx;
             if (i > 0) w.out_lcp[q] = g.aux;
         }
     }
@@ -974,9 +985,7 @@ uint32_t device_sms() {
 cudaError_t launch_init(const Work& w, Prof* pf, cudaStream_t st) {
     if (w.n) {
         // the shadow arrays only ever hold valid string indices and offsets
-        cudaError_t e = cudaMemsetAsync(w.idx[1], 0, sizeof(uint32_t) * (size_t)w.n, st);
-        if (e != cudaSuccess) return e;
-        e = cudaMemsetAsync(w.off[1], 0, sizeof(uint64_t) * (size_t)w.n, st);  // offsets of string 0
+        cudaError_t e = cudaMemsetAsync(w.rec[1], 0, sizeof(Rec) * (size_t)w.n, st);  // index 0, offset 0
         if (e != cudaSuccess) return e;
         ProfScope ps(pf, kInit, st);
         k_init<<<grid_for(w.n, 256, 16, device_sms()), 256, 0, st>>>(w);
