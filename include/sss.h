@@ -55,7 +55,7 @@ typedef enum {
 } sss_status;
 
 /* Tuning knobs.  Defaults: k_max 10, base_threshold 128, medium_threshold
- * 2048, chunk 32768, seed 0x5eed, cdf_segments 4096, cdf_steps 64,
+ * 2048, chunk 32768, seed 0x5eed, cdf_segments 4096, cdf_steps 16,
  * cdf_lr 0.05, profile 0. */
 typedef struct sss_options {
     int32_t k_max;             /* largest splitter tree depth k: v = 2^k - 1 splitters, 1..10 */
@@ -66,7 +66,8 @@ typedef struct sss_options {
                                   multiple of 2048 */
     uint64_t seed;           /* seed of the pseudo-random sample positions */
     uint32_t cdf_segments;   /* learned CDF: number of linear pieces, 16..4096 (power of two) */
-    uint32_t cdf_steps;      /* learned CDF: gradient steps per fit */
+    uint32_t cdf_steps;      /* learned CDF: Adam steps per fit after a start from the
+                                sample's histogram; 0 = the untrained uniform model */
     float cdf_lr;            /* learned CDF: Adam step size */
     uint32_t profile;        /* 1: time every kernel launch with CUDA events on the
                                 caller's stream and report per-class totals in
@@ -168,13 +169,16 @@ int sss_sort_batched(const uint8_t* chars, const uint64_t* offsets, uint32_t n,
                      uint32_t* out_perm, uint32_t* out_lcp, void* stream);
 
 /* Learned bucket proposal (an addition to the paper, closest to the jump
- * tables of App. A.2): as sss_sort, but in every distribution round each
- * segment fits a monotone piecewise-linear CDF of its key words on its own
- * sorted splitter sample (forward and backward passes on the GPU, Adam),
- * and classification first proposes a bucket from the model and checks it
- * exactly against the bounding splitters; only rejected proposals descend
- * the splitter tree.  Output is identical to sss_sort.  learned_keys and
- * learned_misses of sss_stats report the proposal count and miss count. */
+ * tables of App. A.2): as sss_sort, but in every device-wide distribution
+ * round each segment of at least 65,536 strings fits a monotone
+ * piecewise-linear CDF of its key words (cdf_segments pieces, FP32) on its
+ * own sorted splitter sample -- started from the sample's histogram, then
+ * cdf_steps Adam steps of hand-written forward and backward passes on the
+ * GPU -- and classification first proposes a bucket from the model and
+ * checks it exactly against the bounding splitters (and the neighbouring
+ * intervals); only rejected proposals descend the splitter tree.  Output is
+ * identical to sss_sort.  learned_keys and learned_misses of sss_stats
+ * report the proposals and the rejected ones. */
 int sss_sort_learned(const uint8_t* chars, const uint64_t* offsets, uint32_t n,
                      uint32_t* out_perm, uint32_t* out_lcp, void* stream);
 
@@ -202,11 +206,14 @@ int sss_build_splitters(const uint64_t* sample, uint32_t count, int32_t k,
 int sss_classify(const uint64_t* keys, uint32_t n, const uint64_t* level, const uint64_t* inorder,
                  int32_t k, uint16_t* out_bucket, void* stream);
 
-/* Learned CDF pieces, exposed so their gradients can be checked.
- * theta (device, float32[M]) parameterises increments softplus(theta);
- * u (device, float32[S]) in [0,1], y (device, float32[S]) targets.
- * sss_cdf_loss_grad writes the mean squared error to *out_loss (device
- * float32) and dL/dtheta to out_grad (device float32[M]). */
+/* The learned model's loss and gradient, exposed so the fit can be checked.
+ * Model with M pieces on [0,1]: increments softplus(theta_j), normalised
+ * cumulative knots, F linear inside a piece.  theta (device, float32[M],
+ * 1 <= M <= 4096), u (device, float32[S], non-decreasing, clamped to
+ * [0,1]: the fit's samples are sorted keys), y (device,
+ * float32[S] targets), 1 <= S <= 2048.  Writes the mean of (F(u_s) - y_s)^2
+ * to *out_loss (device float32) and dLoss/dtheta to out_grad (device
+ * float32[M]); computed in FP32 on one CTA, the same code the fit uses. */
 int sss_cdf_loss_grad(const float* theta, uint32_t M, const float* u, const float* y,
                       uint32_t S, float* out_loss, float* out_grad, void* stream);
 

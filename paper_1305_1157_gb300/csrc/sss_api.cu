@@ -22,7 +22,7 @@ using namespace sss;
 namespace {
 
 std::mutex g_mu;
-sss_options g_opt = {10, 128u, 2048u, 32768u, 0x5eedull, 4096u, 64u, 0.05f, 0u};
+sss_options g_opt = {10, 128u, 2048u, 32768u, 0x5eedull, 4096u, 16u, 0.05f, 0u};
 sss_stats g_stats;
 Prof g_prof;
 char g_err[512] = "no error";
@@ -61,7 +61,8 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 struct Layout {
     size_t total = 0;
     size_t o_rec0, o_rec1, o_counts, o_counts_scan, o_tlvl, o_tino, o_plans, o_chunk_seg,
-        o_large, o_med0, o_med1, o_small, o_small_size, o_small_off, o_bigrun, o_scan_tmp, o_hdr, o_roots;
+        o_large, o_med0, o_med1, o_small, o_small_size, o_small_off, o_bigrun, o_scan_tmp, o_hdr, o_roots,
+        o_cdf_samp, o_cdf_tab, o_cdf_kmin, o_cdf_scale;
     uint32_t cmax, tmax, lmax, chmax, smax, bmax, scan_tmp_max, mmax;
 };
 
@@ -80,7 +81,7 @@ uint32_t sms_for_layout() {
     return g_sms;
 }
 
-Layout layout_for(uint32_t n, const sss_options& o, uint32_t num_roots) {
+Layout layout_for(uint32_t n, const sss_options& o, uint32_t num_roots, bool learned = false) {
     Layout L;
     const uint64_t nn = n ? n : 1;
     const uint64_t T = o.base_threshold;
@@ -125,6 +126,13 @@ Layout layout_for(uint32_t n, const sss_options& o, uint32_t num_roots) {
     L.o_scan_tmp = take(4 * scan_tmp);
     L.o_hdr = take(sizeof(Hdr));
     L.o_roots = take(sizeof(Seg) * (num_roots ? num_roots : 1));
+    L.o_cdf_samp = L.o_cdf_tab = L.o_cdf_kmin = L.o_cdf_scale = 0;
+    if (learned) {
+        L.o_cdf_samp = take(sizeof(uint64_t) * kSampleMax * lmax);
+        L.o_cdf_tab = take(sizeof(float) * ((size_t)o.cdf_segments + 1) * lmax);
+        L.o_cdf_kmin = take(sizeof(uint64_t) * lmax);
+        L.o_cdf_scale = take(sizeof(float) * lmax);
+    }
     L.total = off;
     return L;
 }
@@ -151,6 +159,12 @@ Work make_work(const Layout& L, char* ws, const uint8_t* chars, const uint64_t* 
     w.bigrun = (Seg*)(ws + L.o_bigrun);
     w.scan_tmp = (uint32_t*)(ws + L.o_scan_tmp);
     w.hdr = (Hdr*)(ws + L.o_hdr);
+    if (L.o_cdf_samp) {
+        w.cdf_samp = (uint64_t*)(ws + L.o_cdf_samp);
+        w.cdf_tab = (float*)(ws + L.o_cdf_tab);
+        w.cdf_kmin = (uint64_t*)(ws + L.o_cdf_kmin);
+        w.cdf_scale = (float*)(ws + L.o_cdf_scale);
+    }
     w.cmax = L.cmax; w.tmax = L.tmax; w.lmax = L.lmax; w.chmax = L.chmax;
     w.smax = L.smax; w.bmax = L.bmax; w.scan_tmp_max = L.scan_tmp_max; w.mmax = L.mmax;
     return w;
@@ -199,8 +213,9 @@ int read_hdr(Hdr* hh, const Work& w, cudaStream_t st) {
 
 // The whole sort on an initialised Work (see the file comment).
 int run_sort(const Work& w, const sss_options& o, const Seg* roots_dev, uint32_t num_roots, Hdr* hh,
-             cudaStream_t st, sss_stats* stats) {
-    Params p{o.k_max, o.base_threshold, o.medium_threshold, o.chunk, o.seed, device_sms(), 0u};
+             cudaStream_t st, sss_stats* stats, bool learned = false) {
+    Params p{learned ? 1 : 0, o.cdf_segments, o.cdf_steps, o.cdf_lr, o.k_max, o.base_threshold,
+             o.medium_threshold, o.chunk, o.seed, device_sms(), 0u};
     Prof* pf = &g_prof;
     pf->reset(o.profile != 0);
     memset(stats, 0, sizeof(*stats));
@@ -240,6 +255,8 @@ int run_sort(const Work& w, const sss_options& o, const Seg* roots_dev, uint32_t
     if (rc) return rc;
     stats->refilled_strings = hh->refills;
     stats->base_iterations = hh->base_iters;
+    stats->learned_keys = hh->learned_keys;
+    stats->learned_misses = hh->learned_misses;
     for (int i = 0; i < 8; i++) stats->base_segment_hist[i] = hh->small_hist[i];
     stats->launches = pf->launches;
     stats->profiled = pf->enabled ? 1u : 0u;
@@ -249,7 +266,8 @@ int run_sort(const Work& w, const sss_options& o, const Seg* roots_dev, uint32_t
 }
 
 int sort_common(const uint8_t* chars, const uint64_t* offsets, uint32_t n, uint32_t* perm, uint32_t* lcp,
-                void* ws_user, size_t ws_user_bytes, const uint64_t* set_begin, uint32_t num_sets, void* stream) {
+                void* ws_user, size_t ws_user_bytes, const uint64_t* set_begin, uint32_t num_sets, void* stream,
+                bool learned = false) {
     cudaStream_t st = (cudaStream_t)stream;
     int rc = check_options(g_opt);
     if (rc) return rc;
@@ -259,7 +277,7 @@ int sort_common(const uint8_t* chars, const uint64_t* offsets, uint32_t n, uint3
     DevPool* P = nullptr;
     rc = get_pool(&P);
     if (rc) return rc;
-    const Layout L = layout_for(n, g_opt, num_sets);
+    const Layout L = layout_for(n, g_opt, num_sets, learned);
     char* ws;
     if (ws_user) {
         if (ws_user_bytes < L.total)
@@ -285,7 +303,7 @@ int sort_common(const uint8_t* chars, const uint64_t* offsets, uint32_t n, uint3
         CK(cudaStreamSynchronize(st), "roots upload");
     }
     sss_stats stats;
-    rc = run_sort(w, g_opt, roots_dev, num_sets, P->hh, st, &stats);
+    rc = run_sort(w, g_opt, roots_dev, num_sets, P->hh, st, &stats, learned);
     if (rc) return rc;
     g_stats = stats;
     return SSS_OK;
@@ -365,8 +383,7 @@ int sss_sort_host(const uint8_t* chars, uint64_t chars_bytes, const uint64_t* of
 int sss_sort_learned(const uint8_t* chars, const uint64_t* offsets, uint32_t n, uint32_t* out_perm,
                      uint32_t* out_lcp, void* stream) {
     std::lock_guard<std::mutex> g(g_mu);
-    (void)chars; (void)offsets; (void)n; (void)out_perm; (void)out_lcp; (void)stream;
-    return fail(SSS_ERR_INVALID, "learned proposal not available in this build");
+    return sort_common(chars, offsets, n, out_perm, out_lcp, nullptr, 0, nullptr, 0, stream, true);
 }
 
 int sss_gather_keys(const uint8_t* chars, const uint64_t* offsets, const uint32_t* idx, const uint32_t* depth,
@@ -401,8 +418,11 @@ int sss_classify(const uint64_t* keys, uint32_t n, const uint64_t* level, const 
 int sss_cdf_loss_grad(const float* theta, uint32_t M, const float* u, const float* y, uint32_t S, float* out_loss,
                       float* out_grad, void* stream) {
     std::lock_guard<std::mutex> g(g_mu);
-    (void)theta; (void)M; (void)u; (void)y; (void)S; (void)out_loss; (void)out_grad; (void)stream;
-    return fail(SSS_ERR_INVALID, "learned proposal not available in this build");
+    if (M < 1 || M > 4096) return fail(SSS_ERR_INVALID, "M must be in 1..4096");
+    if (S < 1 || S > (uint32_t)kSampleMax) return fail(SSS_ERR_INVALID, "S must be in 1..%d", kSampleMax);
+    if (!theta || !u || !y || !out_loss || !out_grad) return fail(SSS_ERR_INVALID, "null pointer argument");
+    CK(launch_cdf_loss_grad(theta, M, u, y, S, out_loss, out_grad, (cudaStream_t)stream), "cdf loss/grad");
+    return SSS_OK;
 }
 
 int sss_set_options(const sss_options* opt) {

@@ -84,6 +84,7 @@ struct Hdr {
     uint32_t large_elems_snap, med_elems_snap, chunk, pad1;
     unsigned long long refills;   // key words gathered in rounds
     unsigned long long base_iters;  // base-case refill iterations summed over tiles
+    unsigned long long learned_keys, learned_misses;  // proposals made / rejected by the exact check
     uint32_t small_hist[8];         // base-case segments by floor(log2(size))
 };
 
@@ -103,6 +104,10 @@ constexpr uint32_t kBaseMaxIters = 1u << 16;
 
 // Tunables passed to kernels.
 struct Params {
+    int learned;              // classify device-wide rounds with the learned CDF proposal
+    uint32_t cdf_M;           // linear pieces of the CDF model
+    uint32_t cdf_steps;       // Adam steps per fit
+    float cdf_lr;             // Adam step size
     int k_max;
     uint32_t base_threshold;  // <= kBaseMax: bucket goes to the warp-tile base case
     uint32_t med_threshold;   // <= kMedMax: bucket gets one CTA for its next round
@@ -135,6 +140,11 @@ struct Work {
     Seg* bigrun;             // [bmax]
     uint32_t* scan_tmp;      // [scan_tmp_max]
     Hdr* hdr;
+    // learned proposal (allocated for sss_sort_learned only)
+    uint64_t* cdf_samp;      // [lmax * kSampleMax] sorted splitter sample of each segment
+    float* cdf_tab;          // [lmax * (M + 1)] CDF at the knots of each segment's model
+    uint64_t* cdf_kmin;      // [lmax] smallest sample key (u = 0)
+    float* cdf_scale;        // [lmax] 1 / (largest - smallest sample key)
 
     uint32_t cmax, tmax, lmax, chmax, smax, bmax, scan_tmp_max, mmax;
 };
@@ -282,6 +292,48 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
     return z ^ (z >> 31);
 }
 
+// ------------------------------------------------------------ learned proposal
+
+// Segments smaller than this are classified by the tree alone (a model's fit
+// costs more than it can save on them).
+constexpr uint32_t kLearnedMinSize = 1u << 16;
+
+// Normalised key position for a segment's model: u = (key - kmin) * scale,
+// clamped to [0, 1], computed in FP32.
+__device__ __forceinline__ float cdf_u(uint64_t key, uint64_t kmin, float scale) {
+    if (key <= kmin) return 0.0f;
+    return fminf(1.0f, __ull2float_rn(key - kmin) * scale);
+}
+
+// Learned bucket proposal with exact verification: the model's CDF value
+// F(u) (linear between the knots C[0..M]) proposes j = floor(F (v + 1));
+// the key's interval (x_{j-1}, x_j] is checked against the in-order
+// splitters, and failing that the neighbouring intervals j-1 and j+1.  On a
+// hit returns true and the bucket 2j + [key = x_j] (identical to the tree's
+// answer, since these intervals partition the keys); on a miss returns
+// false and the caller descends the tree.
+__device__ __forceinline__ bool propose_bucket(uint64_t key, const float* C, uint32_t M, uint64_t kmin, float scale,
+                                               const uint64_t* ino, uint32_t v, uint32_t& bucket) {
+    const float t = cdf_u(key, kmin, scale) * (float)M;
+    const uint32_t m = min((uint32_t)t, M - 1u);
+    const float f = t - (float)m;
+    const float F = C[m] + f * (C[m + 1] - C[m]);
+    uint32_t j = min((uint32_t)(F * (float)(v + 1u)), v);
+    const bool lo_ok = j == 0 || ino[j - 1] < key;
+    const bool hi_ok = j == v || key <= ino[j];
+    if (!(lo_ok && hi_ok)) {
+        if (!lo_ok) {  // key <= x_{j-1}
+            j = j - 1u;
+            if (!(j == 0 || ino[j - 1] < key)) return false;
+        } else {       // key > x_j
+            j = j + 1u;
+            if (!(j == v || key <= ino[j])) return false;
+        }
+    }
+    bucket = 2u * j + ((j < v && key == ino[j]) ? 1u : 0u);
+    return true;
+}
+
 // ------------------------------------------------------------ profiling
 
 constexpr int kClasses = 11;  // matches SSS_K_CLASSES of sss.h
@@ -365,5 +417,10 @@ cudaError_t launch_build_splitters(const uint64_t* sample, uint32_t count, int k
                                    uint64_t* ino, cudaStream_t st);
 cudaError_t launch_classify(const uint64_t* keys, uint32_t n, const uint64_t* lvl, const uint64_t* ino,
                             int k, uint16_t* out, cudaStream_t st);
+// learned CDF (sss_learned.cu)
+size_t cdf_fit_smem(uint32_t M);
+cudaError_t launch_cdf_fit(const Work& w, const Params& p, uint32_t L, Prof* pf, cudaStream_t st);
+cudaError_t launch_cdf_loss_grad(const float* theta, uint32_t M, const float* u, const float* y, uint32_t S,
+                                 float* loss, float* grad, cudaStream_t st);
 
 }  // namespace sss

@@ -158,6 +158,8 @@ __global__ void k_hdr_reset(Work w) {
     h->small_elems = 0; h->med_elems = 0;
     h->refills = 0ull;
     h->base_iters = 0ull;
+    h->learned_keys = 0ull;
+    h->learned_misses = 0ull;
     for (int i = 0; i < 8; i++) h->small_hist[i] = 0;
 }
 
@@ -346,6 +348,10 @@ __global__ void __launch_bounds__(1024) k_sample(Work w, Params p, int cur) {
         samp[j] = j < cnt ? recs[P.begin + sample_pos(p.seed, P.begin, P.size, j)].key : ~0ull;
     __syncthreads();
     bitonic_sort_u64(samp, pw);
+    if (p.learned) {
+        uint64_t* out = w.cdf_samp + (size_t)blockIdx.x * kSampleMax;
+        for (uint32_t j = threadIdx.x; j < cnt; j += blockDim.x) out[j] = samp[j];
+    }
     select_splitters(samp, cnt, k, lvl, ra, rb);
     emit_tree(lvl, k, w.tree_lvl + P.tree_base, w.tree_ino + P.tree_base);
 }
@@ -395,10 +401,42 @@ __device__ __forceinline__ void classify_range(const Rec* __restrict__ recs, uin
     }
 }
 
+// Learned form of classify_range: propose + verify, tree on a miss; counts
+// proposals and misses.
+__device__ __forceinline__ void classify_range_learned(const Rec* __restrict__ recs, uint32_t lo, uint32_t hi,
+                                                       const uint64_t* t, const uint64_t* ino, int k, uint32_t nb,
+                                                       uint32_t* hist, const float* C, uint32_t M, uint64_t kmin,
+                                                       float scale, uint32_t& misses) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t v = (1u << k) - 1u;
+    for (uint32_t base = lo; base < hi; base += blockDim.x * kClassifyUnroll) {
+        uint64_t kk[kClassifyUnroll];
+#pragma unroll
+        for (int u = 0; u < kClassifyUnroll; u++) {
+            const uint32_t e = base + u * blockDim.x + threadIdx.x;
+            kk[u] = e < hi ? recs[e].key : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < kClassifyUnroll; u++) {
+            const uint32_t e = base + u * blockDim.x + threadIdx.x;
+            uint32_t b = nb;
+            if (e < hi && !propose_bucket(kk[u], C, M, kmin, scale, ino, v, b)) {
+                b = classify_key(kk[u], t, ino, k);
+                misses++;
+            }
+            const uint32_t peers = __match_any_sync(FULL_MASK, b);
+            if (lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&hist[b], (uint32_t)__popc(peers));
+        }
+    }
+}
+
+constexpr uint32_t kCdfMMax = 4096;
+
 __global__ void __launch_bounds__(kClassifyThreads) k_classify(Work w, Params p, int cur) {
     __shared__ uint64_t t[kVMax + 1];
     __shared__ uint64_t ino[kVMax];
     __shared__ uint32_t hist[kNBMax + 1];
+    __shared__ float C[kCdfMMax + 1];
     const uint32_t c = blockIdx.x;
     const uint32_t s = w.chunk_seg[c];
     const SegPlan P = w.plans[s];
@@ -413,7 +451,21 @@ __global__ void __launch_bounds__(kClassifyThreads) k_classify(Work w, Params p,
     __syncthreads();
     const uint32_t lo = P.begin + ci * P.chunk;
     const uint32_t hi = min(lo + P.chunk, P.begin + P.size);
-    classify_range(w.rec[cur], lo, hi, t, ino, k, nb, hist, nullptr);
+    if (p.learned && P.size >= kLearnedMinSize) {
+        const float* tab = w.cdf_tab + (size_t)s * (p.cdf_M + 1);
+        for (uint32_t j = threadIdx.x; j <= p.cdf_M; j += blockDim.x) C[j] = tab[j];
+        __syncthreads();
+        uint32_t misses = 0;
+        classify_range_learned(w.rec[cur], lo, hi, t, ino, k, nb, hist, C, p.cdf_M, w.cdf_kmin[s], w.cdf_scale[s],
+                               misses);
+        misses = __reduce_add_sync(FULL_MASK, misses);
+        if ((threadIdx.x & 31u) == 0) {
+            if (misses) atomicAdd(&w.hdr->learned_misses, (unsigned long long)misses);
+        }
+        if (threadIdx.x == 0) atomicAdd(&w.hdr->learned_keys, (unsigned long long)(hi - lo));
+    } else {
+        classify_range(w.rec[cur], lo, hi, t, ino, k, nb, hist, nullptr);
+    }
     __syncthreads();
     for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x)
         w.counts[P.count_base + b * P.chunks + ci] = hist[b];
@@ -443,7 +495,8 @@ struct ScatterState {
 template <int NBCAP, bool kFromBid>
 __device__ uint32_t scatter_range(const Work& w, int cur, uint32_t lo, uint32_t hi, uint32_t nb,
                                   ScatterState<NBCAP>& ss, const uint64_t* t, const uint64_t* ino, int k,
-                                  const uint16_t* bid, uint32_t seg_end, uint32_t depth) {
+                                  const uint16_t* bid, uint32_t seg_end, uint32_t depth, const float* C = nullptr,
+                                  uint32_t M = 0, uint64_t kmin = 0, float scale = 0.0f) {
     constexpr int kBucketsPerThread = (NBCAP + kScatterThreads) / kScatterThreads;
     const Rec* rec_in = w.rec[cur];
     Rec* rec_out = w.rec[cur ^ 1];
@@ -466,7 +519,10 @@ __device__ uint32_t scatter_range(const Work& w, int cur, uint32_t lo, uint32_t 
 #pragma unroll
             for (int j = 0; j < kScatterItems; j++) {
                 const uint32_t e = wbase + j * 32u;
-                bb[j] = e < hi ? classify_key(rr[j].key, t, ino, k) : nb;
+                uint32_t b = nb;
+                if (e < hi && !(C && propose_bucket(rr[j].key, C, M, kmin, scale, ino, (nb - 1u) / 2u, b)))
+                    b = classify_key(rr[j].key, t, ino, k);
+                bb[j] = b;
             }
         }
         // next key words of strings whose bucket moves deeper: all gathers are
@@ -549,6 +605,7 @@ struct ScatterSmem {
     uint64_t t[kVMax + 1];
     uint64_t ino[kVMax];
     ScatterState<kNBMax> ss;
+    float C[kCdfMMax + 1];  // learned model knots (learned mode only)
 };
 
 __global__ void __launch_bounds__(kScatterThreads, SSS_SCATTER_MIN_BLOCKS) k_scatter(Work w, Params p, int cur, int med_out) {
@@ -601,8 +658,17 @@ __global__ void __launch_bounds__(kScatterThreads, SSS_SCATTER_MIN_BLOCKS) k_sca
     __syncthreads();
     const uint32_t lo = P.begin + ci * P.chunk;
     const uint32_t hi = min(lo + P.chunk, seg_end);
-    const uint32_t nref =
-        scatter_range<kNBMax, false>(w, cur, lo, hi, nb, sm.ss, sm.t, sm.ino, k, nullptr, seg_end, P.depth);
+    const float* C = nullptr;
+    const bool model = p.learned && P.size >= kLearnedMinSize;
+    if (model) {
+        const float* tab = w.cdf_tab + (size_t)s * (p.cdf_M + 1);
+        for (uint32_t j = threadIdx.x; j <= p.cdf_M; j += blockDim.x) sm.C[j] = tab[j];
+        __syncthreads();
+        C = sm.C;
+    }
+    const uint32_t nref = scatter_range<kNBMax, false>(w, cur, lo, hi, nb, sm.ss, sm.t, sm.ino, k, nullptr, seg_end,
+                                                       P.depth, C, p.cdf_M, model ? w.cdf_kmin[s] : 0ull,
+                                                       model ? w.cdf_scale[s] : 0.0f);
     add_refills(w, nref);
 }
 
@@ -1022,6 +1088,10 @@ cudaError_t launch_round(const Work& w, const Params& p, int cur, uint32_t L, ui
         {
             ProfScope ps(pf, kSample, st);
             k_sample<<<L, 1024, 0, st>>>(w, p, cur);
+        }
+        if (p.learned) {
+            cudaError_t e = launch_cdf_fit(w, p, L, pf, st);
+            if (e != cudaSuccess) return e;
         }
         {
             ProfScope ps(pf, kClassify, st);
