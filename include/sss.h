@@ -56,7 +56,7 @@ typedef enum {
 
 /* Tuning knobs.  Defaults: k_max 10, base_threshold 128, medium_threshold
  * 2048, chunk 32768, seed 0x5eed, cdf_segments 4096, cdf_steps 16,
- * cdf_lr 0.05, profile 0. */
+ * cdf_lr 0.05, profile 0, graph 0. */
 typedef struct sss_options {
     int32_t k_max;             /* largest splitter tree depth k: v = 2^k - 1 splitters, 1..10 */
     uint32_t base_threshold;   /* buckets of at most this many strings go to the base case, 16..128 */
@@ -71,7 +71,12 @@ typedef struct sss_options {
     float cdf_lr;            /* learned CDF: Adam step size */
     uint32_t profile;        /* 1: time every kernel launch with CUDA events on the
                                 caller's stream and report per-class totals in
-                                sss_stats (adds one event pair per launch) */
+                                sss_stats (adds one event pair per launch; host-
+                                driven rounds only) */
+    uint32_t graph;          /* 1: run sss_sort / sss_sort_learned as one CUDA graph
+                                whose round loop is a device-side conditional node
+                                (no host round-trip per round; per-round stats not
+                                recorded).  sss_sort_batched always does. */
 } sss_options;
 
 #define SSS_MAX_ROUNDS_LOGGED 64
@@ -157,10 +162,15 @@ int sss_sort_noalloc(const uint8_t* chars, const uint64_t* offsets, uint32_t n,
 int sss_sort_host(const uint8_t* chars, uint64_t chars_bytes, const uint64_t* offsets,
                   uint32_t n, uint32_t* out_perm, uint32_t* out_lcp);
 
-/* Sort num_sets independent sets at once.  set_begin (host, num_sets + 1
+/* Sort num_sets independent sets at once, in one launch of a CUDA graph:
+ * every set is a root segment and all sets advance through the same
+ * distribution rounds together; the round loop is a conditional graph node
+ * decided on the device, so the call makes one graph launch and one final
+ * header readback.  The instantiated graph is cached while the buffers,
+ * sizes and options stay the same.  set_begin (host, num_sets + 1
  * entries, non-decreasing, set_begin[0] = 0, set_begin[num_sets] = n) gives
  * set j the strings with global index in [set_begin[j], set_begin[j+1]).
- * All sets advance through the same distribution rounds together.  Outputs
+ * Outputs
  * are per set: for rank r inside set j (global position set_begin[j] + r),
  * out_perm holds the index relative to set_begin[j], and out_lcp is 0 at
  * each set's first position. */

@@ -42,7 +42,7 @@ class sss_options(ctypes.Structure):
     _fields_ = [("k_max", ctypes.c_int32), ("base_threshold", ctypes.c_uint32),
                 ("medium_threshold", ctypes.c_uint32), ("chunk", ctypes.c_uint32),
                 ("seed", ctypes.c_uint64), ("cdf_segments", ctypes.c_uint32), ("cdf_steps", ctypes.c_uint32),
-                ("cdf_lr", ctypes.c_float), ("profile", ctypes.c_uint32)]
+                ("cdf_lr", ctypes.c_float), ("profile", ctypes.c_uint32), ("graph", ctypes.c_uint32)]
 
 
 class sss_stats(ctypes.Structure):

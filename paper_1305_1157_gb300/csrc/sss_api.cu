@@ -22,7 +22,7 @@ using namespace sss;
 namespace {
 
 std::mutex g_mu;
-sss_options g_opt = {10, 128u, 2048u, 32768u, 0x5eedull, 4096u, 16u, 0.05f, 0u};
+sss_options g_opt = {10, 128u, 2048u, 32768u, 0x5eedull, 4096u, 16u, 0.05f, 0u, 0u};
 sss_stats g_stats;
 Prof g_prof;
 char g_err[512] = "no error";
@@ -211,7 +211,8 @@ int read_hdr(Hdr* hh, const Work& w, cudaStream_t st) {
     return SSS_OK;
 }
 
-// The whole sort on an initialised Work (see the file comment).
+// The whole sort on an initialised Work with the host driving the rounds
+// (see the file comment): one header readback per round.
 int run_sort(const Work& w, const sss_options& o, const Seg* roots_dev, uint32_t num_roots, Hdr* hh,
              cudaStream_t st, sss_stats* stats, bool learned = false) {
     Params p{learned ? 1 : 0, o.cdf_segments, o.cdf_steps, o.cdf_lr, o.k_max, o.base_threshold,
@@ -219,16 +220,15 @@ int run_sort(const Work& w, const sss_options& o, const Seg* roots_dev, uint32_t
     Prof* pf = &g_prof;
     pf->reset(o.profile != 0);
     memset(stats, 0, sizeof(*stats));
+    CK(prepare_kernels(o.cdf_segments), "kernel attributes");
     CK(launch_init(w, pf, st), "init");
     CK(launch_roots(w, p, roots_dev, num_roots, pf, st), "roots");
     CK(launch_plan(w, p, pf, st), "plan");
     int rc = read_hdr(hh, w, st);
     if (rc) return rc;
-    int cur = 0, small_buf = 0, med_in = 0;
     for (uint32_t round = 0;; round++) {
         uint32_t tiles = 0;
-        CK(launch_small(w, p, small_buf, hh->n_small_snap, hh->n_bigrun_snap, hh->small_elems_snap, &tiles, pf, st),
-           "base case");
+        CK(launch_small(w, p, hh, &tiles, pf, st), "base case");
         stats->base_tiles += tiles;
         stats->base_strings += hh->small_elems_snap;
         if (hh->L == 0 && hh->n_med_snap == 0) break;
@@ -240,14 +240,11 @@ int run_sort(const Work& w, const sss_options& o, const Seg* roots_dev, uint32_t
         stats->rounds++;
         stats->round_strings += (uint64_t)hh->large_elems_snap + hh->med_elems_snap;
         stats->medium_strings += hh->med_elems_snap;
-        CK(launch_round(w, p, cur, hh->L, hh->total_chunks, hh->total_counts, hh->n_med_snap, med_in, pf, st),
-           "round");
+        CK(launch_round(w, p, hh, pf, st), "round");
         CK(launch_plan(w, p, pf, st), "plan");
+        CK(launch_advance(w, pf, st), "advance");
         rc = read_hdr(hh, w, st);
         if (rc) return rc;
-        small_buf = cur ^ 1;
-        cur ^= 1;
-        med_in ^= 1;
     }
     CK(launch_fixup(w, pf, st), "lcp fixup");
     if (roots_dev) CK(launch_localize(w.out_perm, roots_dev, num_roots, pf, st), "localize");
@@ -262,6 +259,157 @@ int run_sort(const Work& w, const sss_options& o, const Seg* roots_dev, uint32_t
     stats->profiled = pf->enabled ? 1u : 0u;
     for (int i = 0; i < kClasses; i++) stats->prof_launches[i] = pf->cls_launches[i];
     pf->collect(stats->prof_ms);
+    return SSS_OK;
+}
+
+// ------------------------------------------------------------ graph form
+//
+// The same sort as one CUDA graph: prologue (init, roots, plan, base case),
+// a conditional WHILE node whose body is one round (round kernels, plan,
+// advance, base case) and whose last kernel decides on the device whether
+// another round is needed, then the epilogue (LCP fixup, index rebasing).
+// Kernels take their work counts from the device header, so one launch runs
+// the whole sort without host round-trips.  Instantiated graphs are cached
+// per device and reused while the call's buffers and options are unchanged.
+
+struct GraphKey {
+    const void *chars, *offsets, *perm, *lcp, *ws, *roots;
+    uint32_t n, num_roots;
+    sss_options opt;
+    int learned;
+    bool operator==(const GraphKey& o) const { return memcmp(this, &o, sizeof(GraphKey)) == 0; }
+};
+
+struct GraphCache {
+    bool valid = false;
+    GraphKey key;
+    cudaGraphExec_t exec = nullptr;
+    uint32_t launches_prologue = 0, launches_body = 0, launches_epilogue = 0;
+};
+GraphCache g_graph[kMaxDevices];
+
+int build_graph(const Work& w, const Params& p, const Seg* roots_dev, uint32_t num_roots, GraphCache& gc) {
+    // captured on streams of our own (the caller's may be the legacy default
+    // stream, which cannot be captured); the graph is launched on the caller's
+    cudaStream_t st = nullptr, body_st = nullptr;
+    CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "capture stream");
+    if (cudaStreamCreateWithFlags(&body_st, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaStreamDestroy(st);
+        return cuda_fail(cudaGetLastError(), "stream for the round body");
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t err = cudaSuccess;
+    auto done = [&](cudaError_t e, const char* where) -> int {
+        cudaStreamCaptureStatus cs;
+        if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+            cudaGraph_t g2 = nullptr;
+            cudaStreamEndCapture(st, &g2);
+            if (g2) cudaGraphDestroy(g2);
+        }
+        cudaStreamDestroy(body_st);
+        cudaStreamDestroy(st);
+        cudaGetLastError();
+        return cuda_fail(e, where);
+    };
+    Prof counter;  // counts kernel launches per part
+    counter.reset(false);
+    if ((err = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return done(err, "begin capture");
+    cudaStreamCaptureStatus cs;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    if ((err = cudaStreamGetCaptureInfo(st, &cs, nullptr, &graph, &deps, nullptr, &ndeps)) != cudaSuccess)
+        return done(err, "capture info");
+    cudaGraphConditionalHandle cond;
+    if ((err = cudaGraphConditionalHandleCreate(&cond, graph, 0, 0)) != cudaSuccess)
+        return done(err, "conditional handle");
+    // prologue
+    if ((err = launch_init(w, &counter, st)) != cudaSuccess ||
+        (err = launch_roots(w, p, roots_dev, num_roots, &counter, st)) != cudaSuccess ||
+        (err = launch_plan(w, p, &counter, st)) != cudaSuccess ||
+        (err = launch_small(w, p, nullptr, nullptr, &counter, st)) != cudaSuccess ||
+        (err = launch_set_cond(w, cond, st)) != cudaSuccess)
+        return done(err, "graph prologue");
+    gc.launches_prologue = counter.launches + 1;
+    // the round loop
+    if ((err = cudaStreamGetCaptureInfo(st, &cs, nullptr, &graph, &deps, nullptr, &ndeps)) != cudaSuccess)
+        return done(err, "capture info");
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t loop;
+    if ((err = cudaGraphAddNode(&loop, graph, deps, nullptr, ndeps, &cp)) != cudaSuccess)
+        return done(err, "conditional node");
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if ((err = cudaStreamUpdateCaptureDependencies(st, &loop, nullptr, 1, cudaStreamSetCaptureDependencies)) !=
+        cudaSuccess)
+        return done(err, "capture dependencies");
+    if ((err = cudaStreamBeginCaptureToGraph(body_st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+        cudaSuccess)
+        return done(err, "begin body capture");
+    counter.reset(false);
+    if ((err = launch_round(w, p, nullptr, &counter, body_st)) != cudaSuccess ||
+        (err = launch_plan(w, p, &counter, body_st)) != cudaSuccess ||
+        (err = launch_advance(w, &counter, body_st)) != cudaSuccess ||
+        (err = launch_small(w, p, nullptr, nullptr, &counter, body_st)) != cudaSuccess ||
+        (err = launch_set_cond(w, cond, body_st)) != cudaSuccess) {
+        cudaGraph_t b2 = nullptr;
+        cudaStreamEndCapture(body_st, &b2);
+        return done(err, "graph body");
+    }
+    gc.launches_body = counter.launches + 1;
+    cudaGraph_t body_out = nullptr;
+    if ((err = cudaStreamEndCapture(body_st, &body_out)) != cudaSuccess) return done(err, "end body capture");
+    // epilogue
+    counter.reset(false);
+    if ((err = launch_fixup(w, &counter, st)) != cudaSuccess ||
+        (roots_dev && (err = launch_localize(w.out_perm, roots_dev, num_roots, &counter, st)) != cudaSuccess))
+        return done(err, "graph epilogue");
+    gc.launches_epilogue = counter.launches;
+    cudaGraph_t full = nullptr;
+    if ((err = cudaStreamEndCapture(st, &full)) != cudaSuccess) return done(err, "end capture");
+    cudaStreamDestroy(body_st);
+    cudaStreamDestroy(st);
+    cudaGraphExec_t exec = nullptr;
+    err = cudaGraphInstantiate(&exec, full, 0);
+    cudaGraphDestroy(full);
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_fail(err, "graph instantiate");
+    }
+    gc.exec = exec;
+    return SSS_OK;
+}
+
+int run_sort_graph(const Work& w, const sss_options& o, const Seg* roots_dev, uint32_t num_roots, Hdr* hh,
+                   cudaStream_t st, sss_stats* stats, bool learned, const GraphKey& key) {
+    Params p{learned ? 1 : 0, o.cdf_segments, o.cdf_steps, o.cdf_lr, o.k_max, o.base_threshold,
+             o.medium_threshold, o.chunk, o.seed, device_sms(), 0u};
+    memset(stats, 0, sizeof(*stats));
+    int dev = 0;
+    CK(cudaGetDevice(&dev), "cudaGetDevice");
+    GraphCache& gc = g_graph[dev];
+    if (!gc.valid || !(gc.key == key)) {
+        if (gc.exec) cudaGraphExecDestroy(gc.exec);
+        gc = GraphCache();
+        CK(prepare_kernels(o.cdf_segments), "kernel attributes");
+        const int rc = build_graph(w, p, roots_dev, num_roots, gc);
+        if (rc) return rc;
+        gc.key = key;
+        gc.valid = true;
+    }
+    CK(cudaGraphLaunch(gc.exec, st), "graph launch");
+    const int rc = read_hdr(hh, w, st);
+    if (rc) return rc;
+    stats->rounds = hh->round;
+    stats->refilled_strings = hh->refills;
+    stats->base_iterations = hh->base_iters;
+    stats->learned_keys = hh->learned_keys;
+    stats->learned_misses = hh->learned_misses;
+    for (int i = 0; i < 8; i++) stats->base_segment_hist[i] = hh->small_hist[i];
+    stats->launches = gc.launches_prologue + hh->round * gc.launches_body + gc.launches_epilogue;
     return SSS_OK;
 }
 
@@ -303,7 +451,16 @@ int sort_common(const uint8_t* chars, const uint64_t* offsets, uint32_t n, uint3
         CK(cudaStreamSynchronize(st), "roots upload");
     }
     sss_stats stats;
-    rc = run_sort(w, g_opt, roots_dev, num_sets, P->hh, st, &stats, learned);
+    if (g_opt.graph || set_begin) {
+        GraphKey key;
+        memset(&key, 0, sizeof(key));
+        key.chars = chars; key.offsets = offsets; key.perm = perm; key.lcp = lcp; key.ws = ws;
+        key.roots = roots_dev; key.n = n; key.num_roots = num_sets; key.opt = g_opt; key.learned = learned;
+        key.opt.profile = 0;
+        rc = run_sort_graph(w, g_opt, roots_dev, num_sets, P->hh, st, &stats, learned, key);
+    } else {
+        rc = run_sort(w, g_opt, roots_dev, num_sets, P->hh, st, &stats, learned);
+    }
     if (rc) return rc;
     g_stats = stats;
     return SSS_OK;
@@ -456,6 +613,11 @@ int sss_release(void) {
     cudaGetDevice(&cur);
     for (int d = 0; d < kMaxDevices; d++) {
         DevPool& P = g_pool[d];
+        if (g_graph[d].exec) {
+            cudaSetDevice(d);
+            cudaGraphExecDestroy(g_graph[d].exec);
+            g_graph[d] = GraphCache();
+        }
         if (!P.ws && !P.io && !P.hh) continue;
         cudaSetDevice(d);
         if (P.ws) cudaFree(P.ws);

@@ -81,10 +81,12 @@ struct Hdr {
     // snapshot for the host, written by k_plan
     uint32_t L, total_chunks, total_counts, total_tree;
     uint32_t n_med_snap, n_small_snap, n_bigrun_snap, small_elems_snap;
-    uint32_t large_elems_snap, med_elems_snap, chunk, pad1;
+    uint32_t large_elems_snap, med_elems_snap, chunk, round;  // round: rounds done (buffer parity)
     unsigned long long refills;   // key words gathered in rounds
     unsigned long long base_iters;  // base-case refill iterations summed over tiles
     unsigned long long learned_keys, learned_misses;  // proposals made / rejected by the exact check
+    // work queues of the persistent kernels (reset by k_plan)
+    uint32_t q_sample, q_fit, q_classify, q_scatter, q_med, q_base, q_bigrun, q_pad;
     uint32_t small_hist[8];         // base-case segments by floor(log2(size))
 };
 
@@ -292,6 +294,15 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
     return z ^ (z >> 31);
 }
 
+// Next work item of a persistent CTA from the queue counter q (items are
+// taken in order; the caller stops at its item count).  Contains barriers.
+__device__ __forceinline__ uint32_t next_item(uint32_t* q, uint32_t* s_item) {
+    __syncthreads();  // everyone is done with the previous item
+    if (threadIdx.x == 0) *s_item = atomicAdd(q, 1u);
+    __syncthreads();
+    return *s_item;
+}
+
 // ------------------------------------------------------------ learned proposal
 
 // Segments smaller than this are classified by the tree alone (a model's fit
@@ -398,16 +409,24 @@ cudaError_t launch_init(const Work& w, Prof* pf, cudaStream_t st);
 cudaError_t launch_roots(const Work& w, const Params& p, const Seg* roots, uint32_t num_roots, Prof* pf,
                          cudaStream_t st);
 cudaError_t launch_plan(const Work& w, const Params& p, Prof* pf, cudaStream_t st);
-// device-wide kernels for the L planned segments and one CTA per segment of
-// med list med_in; children go to lists (med list med_in ^ 1)
-cudaError_t launch_round(const Work& w, const Params& p, int cur, uint32_t L, uint32_t total_chunks,
-                         uint32_t total_counts, uint32_t n_med, int med_in, Prof* pf, cudaStream_t st);
-cudaError_t launch_small(const Work& w, const Params& p, int buf, uint32_t n_small, uint32_t n_bigrun,
-                         uint32_t small_total, uint32_t* out_tiles, Prof* pf, cudaStream_t st);
+// One distribution round: device-wide kernels for the planned large segments
+// and one CTA per medium segment, reading counts and the buffer parity
+// (hdr->round) from device memory.  hc: host copy of the header when known
+// (exact grids, empty launches skipped), nullptr for persistent grids (graph
+// capture).
+cudaError_t launch_round(const Work& w, const Params& p, const Hdr* hc, Prof* pf, cudaStream_t st);
+cudaError_t launch_set_cond(const Work& w, cudaGraphConditionalHandle cond, cudaStream_t st);
+cudaError_t prepare_kernels(uint32_t cdf_M);
+cudaError_t prepare_cdf_kernels(uint32_t M);
+// hdr->round += 1 (flips the working buffers and medium lists)
+cudaError_t launch_advance(const Work& w, Prof* pf, cudaStream_t st);
+// base case and large runs of the buckets listed by the last k_plan
+cudaError_t launch_small(const Work& w, const Params& p, const Hdr* hc, uint32_t* out_tiles, Prof* pf,
+                         cudaStream_t st);
 cudaError_t launch_fixup(const Work& w, Prof* pf, cudaStream_t st);
 cudaError_t launch_localize(uint32_t* perm, const Seg* roots, uint32_t num_roots, Prof* pf, cudaStream_t st);
-cudaError_t launch_scan_u32(const uint32_t* in, uint32_t* out, uint32_t n, uint32_t* tmp, Prof* pf,
-                            cudaStream_t st);
+cudaError_t launch_scan_u32(const uint32_t* in, uint32_t* out, const uint32_t* n_ptr, const uint32_t* n_host,
+                            uint32_t* tmp, Prof* pf, cudaStream_t st);
 size_t scan_tmp_elems(uint32_t n);
 uint32_t device_sms();
 
@@ -419,7 +438,7 @@ cudaError_t launch_classify(const uint64_t* keys, uint32_t n, const uint64_t* lv
                             int k, uint16_t* out, cudaStream_t st);
 // learned CDF (sss_learned.cu)
 size_t cdf_fit_smem(uint32_t M);
-cudaError_t launch_cdf_fit(const Work& w, const Params& p, uint32_t L, Prof* pf, cudaStream_t st);
+cudaError_t launch_cdf_fit(const Work& w, const Params& p, uint32_t grid, Prof* pf, cudaStream_t st);
 cudaError_t launch_cdf_loss_grad(const float* theta, uint32_t M, const float* u, const float* y, uint32_t S,
                                  float* loss, float* grad, cudaStream_t st);
 

@@ -160,6 +160,9 @@ __global__ void k_hdr_reset(Work w) {
     h->base_iters = 0ull;
     h->learned_keys = 0ull;
     h->learned_misses = 0ull;
+    h->round = 0;
+    h->q_sample = 0; h->q_fit = 0; h->q_classify = 0; h->q_scatter = 0;
+    h->q_med = 0; h->q_base = 0; h->q_bigrun = 0;
     for (int i = 0; i < 8; i++) h->small_hist[i] = 0;
 }
 
@@ -237,6 +240,8 @@ __global__ void __launch_bounds__(1024) k_plan(Work w, Params p) {
         h->n_bigrun = 0;
         h->small_elems = 0;
         h->med_elems = 0;
+        h->q_sample = 0; h->q_fit = 0; h->q_classify = 0; h->q_scatter = 0;
+        h->q_med = 0; h->q_base = 0; h->q_bigrun = 0;
     }
 }
 
@@ -335,25 +340,29 @@ __device__ __forceinline__ uint32_t sample_pos(uint64_t seed, uint32_t begin, ui
     return (uint32_t)(((uint64_t)r * size) >> 32);
 }
 
-__global__ void __launch_bounds__(1024) k_sample(Work w, Params p, int cur) {
+__global__ void __launch_bounds__(1024) k_sample(Work w, Params p) {
     __shared__ uint64_t samp[kSampleMax];
     __shared__ uint64_t lvl[kVMax + 1];
     __shared__ int32_t ra[kVMax + 1], rb[kVMax + 1];
-    const SegPlan P = w.plans[blockIdx.x];
-    const int k = (int)P.k;
-    const uint32_t pw = 2u << k;
-    const uint32_t cnt = pw - 1u;  // alpha (v + 1) - 1 with alpha = 2
-    const Rec* recs = w.rec[cur];
-    for (uint32_t j = threadIdx.x; j < pw; j += blockDim.x)
-        samp[j] = j < cnt ? recs[P.begin + sample_pos(p.seed, P.begin, P.size, j)].key : ~0ull;
-    __syncthreads();
-    bitonic_sort_u64(samp, pw);
-    if (p.learned) {
-        uint64_t* out = w.cdf_samp + (size_t)blockIdx.x * kSampleMax;
-        for (uint32_t j = threadIdx.x; j < cnt; j += blockDim.x) out[j] = samp[j];
+    __shared__ uint32_t s_item;
+    const Rec* recs = w.rec[w.hdr->round & 1u];
+    const uint32_t L = w.hdr->L;
+    for (uint32_t seg = next_item(&w.hdr->q_sample, &s_item); seg < L; seg = next_item(&w.hdr->q_sample, &s_item)) {
+        const SegPlan P = w.plans[seg];
+        const int k = (int)P.k;
+        const uint32_t pw = 2u << k;
+        const uint32_t cnt = pw - 1u;  // alpha (v + 1) - 1 with alpha = 2
+        for (uint32_t j = threadIdx.x; j < pw; j += blockDim.x)
+            samp[j] = j < cnt ? recs[P.begin + sample_pos(p.seed, P.begin, P.size, j)].key : ~0ull;
+        __syncthreads();
+        bitonic_sort_u64(samp, pw);
+        if (p.learned) {
+            uint64_t* out = w.cdf_samp + (size_t)seg * kSampleMax;
+            for (uint32_t j = threadIdx.x; j < cnt; j += blockDim.x) out[j] = samp[j];
+        }
+        select_splitters(samp, cnt, k, lvl, ra, rb);
+        emit_tree(lvl, k, w.tree_lvl + P.tree_base, w.tree_ino + P.tree_base);
     }
-    select_splitters(samp, cnt, k, lvl, ra, rb);
-    emit_tree(lvl, k, w.tree_lvl + P.tree_base, w.tree_ino + P.tree_base);
 }
 
 // Stand-alone splitter construction for a caller's sample (sss_build_splitters).
@@ -432,43 +441,47 @@ __device__ __forceinline__ void classify_range_learned(const Rec* __restrict__ r
 
 constexpr uint32_t kCdfMMax = 4096;
 
-__global__ void __launch_bounds__(kClassifyThreads) k_classify(Work w, Params p, int cur) {
+__global__ void __launch_bounds__(kClassifyThreads) k_classify(Work w, Params p) {
     __shared__ uint64_t t[kVMax + 1];
     __shared__ uint64_t ino[kVMax];
     __shared__ uint32_t hist[kNBMax + 1];
     __shared__ float C[kCdfMMax + 1];
-    const uint32_t c = blockIdx.x;
-    const uint32_t s = w.chunk_seg[c];
-    const SegPlan P = w.plans[s];
-    const uint32_t ci = c - P.chunk_base;
-    const int k = (int)P.k;
-    const uint32_t v = (1u << k) - 1u, nb = 2u * v + 1u;
-    for (uint32_t i = threadIdx.x; i < v; i += blockDim.x) {
-        t[i + 1] = w.tree_lvl[P.tree_base + i];
-        ino[i] = w.tree_ino[P.tree_base + i];
-    }
-    for (uint32_t b = threadIdx.x; b <= nb; b += blockDim.x) hist[b] = 0;
-    __syncthreads();
-    const uint32_t lo = P.begin + ci * P.chunk;
-    const uint32_t hi = min(lo + P.chunk, P.begin + P.size);
-    if (p.learned && P.size >= kLearnedMinSize) {
-        const float* tab = w.cdf_tab + (size_t)s * (p.cdf_M + 1);
-        for (uint32_t j = threadIdx.x; j <= p.cdf_M; j += blockDim.x) C[j] = tab[j];
-        __syncthreads();
-        uint32_t misses = 0;
-        classify_range_learned(w.rec[cur], lo, hi, t, ino, k, nb, hist, C, p.cdf_M, w.cdf_kmin[s], w.cdf_scale[s],
-                               misses);
-        misses = __reduce_add_sync(FULL_MASK, misses);
-        if ((threadIdx.x & 31u) == 0) {
-            if (misses) atomicAdd(&w.hdr->learned_misses, (unsigned long long)misses);
+    __shared__ uint32_t s_item;
+    const int cur = w.hdr->round & 1u;
+    const uint32_t total_chunks = w.hdr->total_chunks;
+    for (uint32_t c = next_item(&w.hdr->q_classify, &s_item); c < total_chunks;
+         c = next_item(&w.hdr->q_classify, &s_item)) {
+        const uint32_t s = w.chunk_seg[c];
+        const SegPlan P = w.plans[s];
+        const uint32_t ci = c - P.chunk_base;
+        const int k = (int)P.k;
+        const uint32_t v = (1u << k) - 1u, nb = 2u * v + 1u;
+        for (uint32_t i = threadIdx.x; i < v; i += blockDim.x) {
+            t[i + 1] = w.tree_lvl[P.tree_base + i];
+            ino[i] = w.tree_ino[P.tree_base + i];
         }
-        if (threadIdx.x == 0) atomicAdd(&w.hdr->learned_keys, (unsigned long long)(hi - lo));
-    } else {
-        classify_range(w.rec[cur], lo, hi, t, ino, k, nb, hist, nullptr);
+        for (uint32_t b = threadIdx.x; b <= nb; b += blockDim.x) hist[b] = 0;
+        __syncthreads();
+        const uint32_t lo = P.begin + ci * P.chunk;
+        const uint32_t hi = min(lo + P.chunk, P.begin + P.size);
+        if (p.learned && P.size >= kLearnedMinSize) {
+            const float* tab = w.cdf_tab + (size_t)s * (p.cdf_M + 1);
+            for (uint32_t j = threadIdx.x; j <= p.cdf_M; j += blockDim.x) C[j] = tab[j];
+            __syncthreads();
+            uint32_t misses = 0;
+            classify_range_learned(w.rec[cur], lo, hi, t, ino, k, nb, hist, C, p.cdf_M, w.cdf_kmin[s],
+                                   w.cdf_scale[s], misses);
+            misses = __reduce_add_sync(FULL_MASK, misses);
+            if ((threadIdx.x & 31u) == 0 && misses) atomicAdd(&w.hdr->learned_misses, (unsigned long long)misses);
+            if (threadIdx.x == 0) atomicAdd(&w.hdr->learned_keys, (unsigned long long)(hi - lo));
+        } else {
+            classify_range(w.rec[cur], lo, hi, t, ino, k, nb, hist, nullptr);
+        }
+        __syncthreads();
+        for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x)
+            w.counts[P.count_base + b * P.chunks + ci] = hist[b];
+        __syncthreads();
     }
-    __syncthreads();
-    for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x)
-        w.counts[P.count_base + b * P.chunks + ci] = hist[b];
 }
 
 // ------------------------------------------------------------ stable scatter
@@ -608,68 +621,75 @@ struct ScatterSmem {
     float C[kCdfMMax + 1];  // learned model knots (learned mode only)
 };
 
-__global__ void __launch_bounds__(kScatterThreads, SSS_SCATTER_MIN_BLOCKS) k_scatter(Work w, Params p, int cur, int med_out) {
+__global__ void __launch_bounds__(kScatterThreads, SSS_SCATTER_MIN_BLOCKS) k_scatter(Work w, Params p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ScatterSmem& sm = *reinterpret_cast<ScatterSmem*>(smem_raw);
-    const uint32_t c = blockIdx.x;
-    const uint32_t s = w.chunk_seg[c];
-    const SegPlan P = w.plans[s];
-    const uint32_t ci = c - P.chunk_base;
-    const int k = (int)P.k;
-    const uint32_t v = (1u << k) - 1u, nb = 2u * v + 1u;
-    for (uint32_t i = threadIdx.x; i < v; i += blockDim.x) {
-        sm.t[i + 1] = w.tree_lvl[P.tree_base + i];
-        sm.ino[i] = w.tree_ino[P.tree_base + i];
-    }
-    __syncthreads();
-    const uint32_t* S = w.counts_scan + P.count_base;
-    const uint32_t seg_end = P.begin + P.size;
-    // bucket b starts at S[b * chunks] and this chunk's part of it at
-    // S[b * chunks + ci] (relative to S[0]): issue every load first
-    constexpr int kBPT = (kNBMax + kScatterThreads) / kScatterThreads;
-    uint32_t s_first[kBPT], s_next[kBPT], s_mine[kBPT];
-    const uint32_t S0 = S[0];
-#pragma unroll
-    for (int q = 0; q < kBPT; q++) {
-        const uint32_t b = threadIdx.x + q * kScatterThreads;
-        s_first[q] = b < nb ? S[b * P.chunks] : 0u;
-        s_mine[q] = b < nb ? S[b * P.chunks + ci] : 0u;
-        s_next[q] = b + 1 < nb ? S[(b + 1) * P.chunks] : 0u;
-    }
-#pragma unroll
-    for (int q = 0; q < kBPT; q++) {
-        const uint32_t b = threadIdx.x + q * kScatterThreads;
-        if (b <= nb) {
-            for (int ww = 0; ww < kScatterWarps; ww++) sm.ss.whist[ww][b] = 0;
+    const int cur = w.hdr->round & 1u;
+    const int med_out = cur ^ 1;
+    const uint32_t total_chunks = w.hdr->total_chunks;
+    __shared__ uint32_t s_item;
+    for (uint32_t c = next_item(&w.hdr->q_scatter, &s_item); c < total_chunks;
+         c = next_item(&w.hdr->q_scatter, &s_item)) {
+        const uint32_t s = w.chunk_seg[c];
+        const SegPlan P = w.plans[s];
+        const uint32_t ci = c - P.chunk_base;
+        const int k = (int)P.k;
+        const uint32_t v = (1u << k) - 1u, nb = 2u * v + 1u;
+        for (uint32_t i = threadIdx.x; i < v; i += blockDim.x) {
+            sm.t[i + 1] = w.tree_lvl[P.tree_base + i];
+            sm.ino[i] = w.tree_ino[P.tree_base + i];
         }
-        if (b < nb) {
-            const uint32_t start = P.begin + (s_first[q] - S0);
-            const uint32_t end = (b + 1 < nb) ? P.begin + (s_next[q] - S0) : seg_end;
-            const uint32_t size = end - start;
-            sm.ss.run_pos[b] = P.begin + (s_mine[q] - S0);
-            const BucketInfo bi = bucket_info(b, nb, P.depth, sm.ino, size);
-            sm.ss.rdep[b] = refill_code(bi, size, P.depth);
-            if (ci == 0 && size > 0) {
-                if (start > P.begin) w.out_lcp[start] = kLcpFlag | P.depth;
-                append_child(w, p, med_out, start, size, bi.cdepth, bi.isrun, bi.runlcp);
+        __syncthreads();
+        const uint32_t* S = w.counts_scan + P.count_base;
+        const uint32_t seg_end = P.begin + P.size;
+        // bucket b starts at S[b * chunks] and this chunk's part of it at
+        // S[b * chunks + ci] (relative to S[0]): issue every load first
+        constexpr int kBPT = (kNBMax + kScatterThreads) / kScatterThreads;
+        uint32_t s_first[kBPT], s_next[kBPT], s_mine[kBPT];
+        const uint32_t S0 = S[0];
+#pragma unroll
+        for (int q = 0; q < kBPT; q++) {
+            const uint32_t b = threadIdx.x + q * kScatterThreads;
+            s_first[q] = b < nb ? S[b * P.chunks] : 0u;
+            s_mine[q] = b < nb ? S[b * P.chunks + ci] : 0u;
+            s_next[q] = b + 1 < nb ? S[(b + 1) * P.chunks] : 0u;
+        }
+#pragma unroll
+        for (int q = 0; q < kBPT; q++) {
+            const uint32_t b = threadIdx.x + q * kScatterThreads;
+            if (b <= nb) {
+                for (int ww = 0; ww < kScatterWarps; ww++) sm.ss.whist[ww][b] = 0;
+            }
+            if (b < nb) {
+                const uint32_t start = P.begin + (s_first[q] - S0);
+                const uint32_t end = (b + 1 < nb) ? P.begin + (s_next[q] - S0) : seg_end;
+                const uint32_t size = end - start;
+                sm.ss.run_pos[b] = P.begin + (s_mine[q] - S0);
+                const BucketInfo bi = bucket_info(b, nb, P.depth, sm.ino, size);
+                sm.ss.rdep[b] = refill_code(bi, size, P.depth);
+                if (ci == 0 && size > 0) {
+                    if (start > P.begin) w.out_lcp[start] = kLcpFlag | P.depth;
+                    append_child(w, p, med_out, start, size, bi.cdepth, bi.isrun, bi.runlcp);
+                }
             }
         }
-    }
-    __syncthreads();
-    const uint32_t lo = P.begin + ci * P.chunk;
-    const uint32_t hi = min(lo + P.chunk, seg_end);
-    const float* C = nullptr;
-    const bool model = p.learned && P.size >= kLearnedMinSize;
-    if (model) {
-        const float* tab = w.cdf_tab + (size_t)s * (p.cdf_M + 1);
-        for (uint32_t j = threadIdx.x; j <= p.cdf_M; j += blockDim.x) sm.C[j] = tab[j];
         __syncthreads();
-        C = sm.C;
+        const uint32_t lo = P.begin + ci * P.chunk;
+        const uint32_t hi = min(lo + P.chunk, seg_end);
+        const float* C = nullptr;
+        const bool model = p.learned && P.size >= kLearnedMinSize;
+        if (model) {
+            const float* tab = w.cdf_tab + (size_t)s * (p.cdf_M + 1);
+            for (uint32_t j = threadIdx.x; j <= p.cdf_M; j += blockDim.x) sm.C[j] = tab[j];
+            __syncthreads();
+            C = sm.C;
+        }
+        const uint32_t nref = scatter_range<kNBMax, false>(w, cur, lo, hi, nb, sm.ss, sm.t, sm.ino, k, nullptr, seg_end,
+                                                           P.depth, C, p.cdf_M, model ? w.cdf_kmin[s] : 0ull,
+                                                           model ? w.cdf_scale[s] : 0.0f);
+        add_refills(w, nref);
+        __syncthreads();
     }
-    const uint32_t nref = scatter_range<kNBMax, false>(w, cur, lo, hi, nb, sm.ss, sm.t, sm.ino, k, nullptr, seg_end,
-                                                       P.depth, C, p.cdf_M, model ? w.cdf_kmin[s] : 0ull,
-                                                       model ? w.cdf_scale[s] : 0.0f);
-    add_refills(w, nref);
 }
 
 // ------------------------------------------------------------ medium round
@@ -689,57 +709,64 @@ struct MedSmem {
 // One CTA runs one whole distribution round for one medium segment (the
 // sequential S^5 of the paper, here on one SM): sample, tree, classify into a
 // shared bucket array, local prefix sum, stable move, child segments.
-__global__ void __launch_bounds__(kScatterThreads, SSS_SCATTER_MIN_BLOCKS) k_med_round(Work w, Params p, int cur, int med_in, int med_out) {
+__global__ void __launch_bounds__(kScatterThreads, SSS_SCATTER_MIN_BLOCKS) k_med_round(Work w, Params p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     MedSmem& sm = *reinterpret_cast<MedSmem*>(smem_raw);
-    const Seg g = w.med[med_in][blockIdx.x];
-    const uint32_t m = g.size;
-    const int k = choose_k(m, min(p.k_max, kMedKMax));
-    const uint32_t v = (1u << k) - 1u, nb = 2u * v + 1u;
-    const uint32_t pw = 2u << k, cnt = pw - 1u;
-    const Rec* recs = w.rec[cur];
-    for (uint32_t j = threadIdx.x; j < pw; j += blockDim.x)
-        sm.samp[j] = j < cnt ? recs[g.begin + sample_pos(p.seed, g.begin, m, j)].key : ~0ull;
-    for (uint32_t b = threadIdx.x; b <= nb; b += blockDim.x) {
-        sm.hist[b] = 0;
-        for (int q = 0; q < kScatterWarps; q++) sm.ss.whist[q][b] = 0;
-    }
-    __syncthreads();
-    bitonic_sort_u64(sm.samp, pw);
-    select_splitters(sm.samp, cnt, k, sm.lvl, sm.ra, sm.rb);
-    emit_tree(sm.lvl, k, sm.t + 1, sm.ino);
-    classify_range(recs, g.begin, g.begin + m, sm.t, sm.ino, k, nb, sm.hist, sm.bid);
-    __syncthreads();
-    // bucket starts: consecutive buckets per thread
-    constexpr int kPer = (kMedNB + 1) / kScatterThreads;
-    uint32_t cnts[kPer], sum = 0;
-#pragma unroll
-    for (int q = 0; q < kPer; q++) {
-        const uint32_t b = threadIdx.x * kPer + q;
-        cnts[q] = b < nb ? sm.hist[b] : 0u;
-        sum += cnts[q];
-    }
-    uint32_t start = g.begin + block_excl_sum(sum, sm.wsum, nullptr);
-#pragma unroll
-    for (int q = 0; q < kPer; q++) {
-        const uint32_t b = threadIdx.x * kPer + q;
-        if (b < nb) {
-            const uint32_t size = cnts[q];
-            const BucketInfo bi = bucket_info(b, nb, g.depth, sm.ino, size);
-            sm.ss.run_pos[b] = start;
-            sm.ss.rdep[b] = refill_code(bi, size, g.depth);
-            if (size > 0) {
-                if (start > g.begin) w.out_lcp[start] = kLcpFlag | g.depth;
-                append_child(w, p, med_out, start, size, bi.cdepth, bi.isrun, bi.runlcp);
-            }
+    const int cur = w.hdr->round & 1u;
+    const int med_in = cur, med_out = cur ^ 1;
+    const uint32_t n_med = w.hdr->n_med_snap;
+    __shared__ uint32_t s_item;
+    for (uint32_t mi = next_item(&w.hdr->q_med, &s_item); mi < n_med; mi = next_item(&w.hdr->q_med, &s_item)) {
+        const Seg g = w.med[med_in][mi];
+        const uint32_t m = g.size;
+        const int k = choose_k(m, min(p.k_max, kMedKMax));
+        const uint32_t v = (1u << k) - 1u, nb = 2u * v + 1u;
+        const uint32_t pw = 2u << k, cnt = pw - 1u;
+        const Rec* recs = w.rec[cur];
+        for (uint32_t j = threadIdx.x; j < pw; j += blockDim.x)
+            sm.samp[j] = j < cnt ? recs[g.begin + sample_pos(p.seed, g.begin, m, j)].key : ~0ull;
+        for (uint32_t b = threadIdx.x; b <= nb; b += blockDim.x) {
+            sm.hist[b] = 0;
+            for (int q = 0; q < kScatterWarps; q++) sm.ss.whist[q][b] = 0;
         }
-        start += cnts[q];
+        __syncthreads();
+        bitonic_sort_u64(sm.samp, pw);
+        select_splitters(sm.samp, cnt, k, sm.lvl, sm.ra, sm.rb);
+        emit_tree(sm.lvl, k, sm.t + 1, sm.ino);
+        classify_range(recs, g.begin, g.begin + m, sm.t, sm.ino, k, nb, sm.hist, sm.bid);
+        __syncthreads();
+        // bucket starts: consecutive buckets per thread
+        constexpr int kPer = (kMedNB + 1) / kScatterThreads;
+        uint32_t cnts[kPer], sum = 0;
+#pragma unroll
+        for (int q = 0; q < kPer; q++) {
+            const uint32_t b = threadIdx.x * kPer + q;
+            cnts[q] = b < nb ? sm.hist[b] : 0u;
+            sum += cnts[q];
+        }
+        uint32_t start = g.begin + block_excl_sum(sum, sm.wsum, nullptr);
+#pragma unroll
+        for (int q = 0; q < kPer; q++) {
+            const uint32_t b = threadIdx.x * kPer + q;
+            if (b < nb) {
+                const uint32_t size = cnts[q];
+                const BucketInfo bi = bucket_info(b, nb, g.depth, sm.ino, size);
+                sm.ss.run_pos[b] = start;
+                sm.ss.rdep[b] = refill_code(bi, size, g.depth);
+                if (size > 0) {
+                    if (start > g.begin) w.out_lcp[start] = kLcpFlag | g.depth;
+                    append_child(w, p, med_out, start, size, bi.cdepth, bi.isrun, bi.runlcp);
+                }
+            }
+            start += cnts[q];
+        }
+        __syncthreads();
+        const uint32_t nref =
+            scatter_range<kMedNB, true>(w, cur, g.begin, g.begin + m, nb, sm.ss, sm.t, sm.ino, k, sm.bid, g.begin + m,
+                                        g.depth);
+        add_refills(w, nref);
+        __syncthreads();
     }
-    __syncthreads();
-    const uint32_t nref =
-        scatter_range<kMedNB, true>(w, cur, g.begin, g.begin + m, nb, sm.ss, sm.t, sm.ino, k, sm.bid, g.begin + m,
-                                    g.depth);
-    add_refills(w, nref);
 }
 
 // ------------------------------------------------------------ base case
@@ -789,12 +816,17 @@ __device__ __forceinline__ uint32_t warp_lower_bound(const uint32_t* __restrict_
 // words holding the terminator are equal strings, and groups of equal key
 // words without it become runs 8 bytes deeper (new words gathered) for the
 // next pass.
-__global__ void __launch_bounds__(kBaseThreads) k_base(Work w, uint32_t T, int buf, uint32_t ns, uint32_t total) {
+__global__ void __launch_bounds__(kBaseThreads) k_base(Work w, Params p) {
     __shared__ BaseSmem sm;
     const uint32_t s = threadIdx.x;
     const uint32_t lane = s & 31u, warp = s >> 5;
-    const uint32_t t0 = blockIdx.x * T;
-    if (t0 >= total) return;
+    const int buf = w.hdr->round & 1u;
+    const uint32_t ns = w.hdr->n_small_snap, total = w.hdr->small_elems_snap;
+    const uint32_t T = p.base_threshold;
+    const uint32_t tiles = (total + T - 1) / T;
+    __shared__ uint32_t s_item;
+    for (uint32_t tile = next_item(&w.hdr->q_base, &s_item); tile < tiles; tile = next_item(&w.hdr->q_base, &s_item)) {
+    const uint32_t t0 = tile * T;
     const uint32_t t1 = min(t0 + T, total);
     if (warp == 0) {
         const uint32_t lo = warp_lower_bound(w.small_off, ns, t0);
@@ -803,7 +835,10 @@ __global__ void __launch_bounds__(kBaseThreads) k_base(Work w, uint32_t T, int b
     }
     __syncthreads();
     const uint32_t lo = sm.lohi[0], hi = sm.lohi[1];
-    if (lo >= hi) return;
+    if (lo >= hi) {
+        __syncthreads();  // lohi is rewritten by the next tile
+        continue;
+    }
     const uint32_t slot0 = w.small_off[lo];
     const uint32_t cnt = (hi < ns ? w.small_off[hi] : total) - slot0;
     const uint32_t nseg = hi - lo;
@@ -837,7 +872,7 @@ __global__ void __launch_bounds__(kBaseThreads) k_base(Work w, uint32_t T, int b
     for (;; iter++) {
         if (iter >= kBaseMaxIters) {  // never expected: strings end, so runs end
             if (s == 0) atomicOr(&w.hdr->err, kErrBaseIters);
-            return;
+            break;
         }
         // ---- rank inside the run: (key, slot) order keeps index order for ties
         uint32_t np = s;
@@ -922,11 +957,16 @@ __global__ void __launch_bounds__(kBaseThreads) k_base(Work w, uint32_t T, int b
     }
     if (s < cnt) w.out_perm[G] = id;
     if (s == 0) atomicAdd(&w.hdr->base_iters, (unsigned long long)(iter + 1));
+    __syncthreads();  // shared arrays are rewritten by the next tile
+    }
 }
 
 // Buckets too large for the base case whose strings are all equal.
-__global__ void k_bigrun(Work w, int buf, uint32_t nrun) {
-    for (uint32_t r = blockIdx.x; r < nrun; r += gridDim.x) {
+__global__ void k_bigrun(Work w) {
+    const int buf = w.hdr->round & 1u;
+    const uint32_t nrun = w.hdr->n_bigrun_snap;
+    __shared__ uint32_t s_item;
+    for (uint32_t r = next_item(&w.hdr->q_bigrun, &s_item); r < nrun; r = next_item(&w.hdr->q_bigrun, &s_item)) {
         const Seg g = w.bigrun[r];
         for (uint32_t i = threadIdx.x; i < g.size; i += blockDim.x) {
             const uint32_t q = g.begin + i;
@@ -967,22 +1007,29 @@ constexpr uint32_t kScanTile = kScanThreads * kScanPer;
 
 size_t scan_tmp_elems(uint32_t n) { return (size_t)(n + kScanTile - 1) / kScanTile + 1; }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* in, uint32_t n, uint32_t* sums) {
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* in, const uint32_t* n_ptr,
+                                                              uint32_t* sums) {
     __shared__ uint32_t wsum[33];
-    const uint32_t base = blockIdx.x * kScanTile;
-    uint32_t s = 0;
+    const uint32_t n = *n_ptr;
+    const uint32_t tiles = (n + kScanTile - 1) / kScanTile;
+    for (uint32_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const uint32_t base = tile * kScanTile;
+        uint32_t s = 0;
 #pragma unroll
-    for (int j = 0; j < kScanPer; j++) {
-        uint32_t i = base + j * kScanThreads + threadIdx.x;
-        if (i < n) s += in[i];
+        for (int j = 0; j < kScanPer; j++) {
+            const uint32_t i = base + j * kScanThreads + threadIdx.x;
+            if (i < n) s += in[i];
+        }
+        uint32_t tot;
+        block_excl_sum(s, wsum, &tot);
+        if (threadIdx.x == 0) sums[tile] = tot;
     }
-    uint32_t tot;
-    block_excl_sum(s, wsum, &tot);
-    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
 }
 
-__global__ void __launch_bounds__(1024) k_scan_tiles(uint32_t* sums, uint32_t ntiles, uint32_t* total_out) {
+__global__ void __launch_bounds__(1024) k_scan_tiles(uint32_t* sums, const uint32_t* n_ptr, uint32_t* out) {
     __shared__ uint32_t wsum[33];
+    const uint32_t n = *n_ptr;
+    const uint32_t ntiles = (n + kScanTile - 1) / kScanTile;
     const uint32_t per = (ntiles + blockDim.x - 1) / blockDim.x;
     const uint32_t lo = min(ntiles, threadIdx.x * per), hi = min(ntiles, lo + per);
     uint32_t s = 0;
@@ -990,44 +1037,52 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(uint32_t* sums, uint32_t nt
     uint32_t tot;
     uint32_t ex = block_excl_sum(s, wsum, &tot);
     for (uint32_t i = lo; i < hi; i++) {
-        uint32_t x = sums[i];
+        const uint32_t x = sums[i];
         sums[i] = ex;
         ex += x;
     }
-    if (threadIdx.x == 0) *total_out = tot;
+    if (threadIdx.x == 0) out[n] = tot;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* in, uint32_t* out, uint32_t n,
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* in, uint32_t* out, const uint32_t* n_ptr,
                                                             const uint32_t* sums) {
     __shared__ uint32_t wsum[33];
-    const uint32_t base = blockIdx.x * kScanTile + threadIdx.x * kScanPer;
-    uint32_t v[kScanPer];
-    uint32_t s = 0;
+    const uint32_t n = *n_ptr;
+    const uint32_t tiles = (n + kScanTile - 1) / kScanTile;
+    for (uint32_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const uint32_t base = tile * kScanTile + threadIdx.x * kScanPer;
+        uint32_t v[kScanPer];
+        uint32_t s = 0;
 #pragma unroll
-    for (int j = 0; j < kScanPer; j++) {
-        uint32_t i = base + j;
-        v[j] = i < n ? in[i] : 0u;
-        s += v[j];
-    }
-    uint32_t ex = block_excl_sum(s, wsum, nullptr) + sums[blockIdx.x];
+        for (int j = 0; j < kScanPer; j++) {
+            const uint32_t i = base + j;
+            v[j] = i < n ? in[i] : 0u;
+            s += v[j];
+        }
+        uint32_t ex = block_excl_sum(s, wsum, nullptr) + sums[tile];
 #pragma unroll
-    for (int j = 0; j < kScanPer; j++) {
-        uint32_t i = base + j;
-        if (i < n) out[i] = ex;
-        ex += v[j];
+        for (int j = 0; j < kScanPer; j++) {
+            const uint32_t i = base + j;
+            if (i < n) out[i] = ex;
+            ex += v[j];
+        }
     }
 }
 
-// out[0..n) = exclusive prefix sums of in, out[n] = total.  tmp holds
+// out[0..n) = exclusive prefix sums of in, out[n] = total, with n read from
+// device memory (*n_ptr); n_host (if known) only sizes the grid.  tmp holds
 // scan_tmp_elems(n) entries.
-cudaError_t launch_scan_u32(const uint32_t* in, uint32_t* out, uint32_t n, uint32_t* tmp, Prof* pf,
-                            cudaStream_t st) {
-    if (n == 0) return cudaMemsetAsync(out, 0, sizeof(uint32_t), st);
-    const uint32_t tiles = (n + kScanTile - 1) / kScanTile;
+cudaError_t launch_scan_u32(const uint32_t* in, uint32_t* out, const uint32_t* n_ptr, const uint32_t* n_host,
+                            uint32_t* tmp, Prof* pf, cudaStream_t st) {
+    uint32_t grid = device_sms() * 8u;
+    if (n_host) {
+        const uint32_t tiles = (*n_host + kScanTile - 1) / kScanTile;
+        grid = max(1u, min(grid, tiles));
+    }
     ProfScope ps(pf, kScan, st);
-    k_scan_reduce<<<tiles, kScanThreads, 0, st>>>(in, n, tmp);
-    k_scan_tiles<<<1, 1024, 0, st>>>(tmp, tiles, out + n);
-    k_scan_down<<<tiles, kScanThreads, 0, st>>>(in, out, n, tmp);
+    k_scan_reduce<<<grid, kScanThreads, 0, st>>>(in, n_ptr, tmp);
+    k_scan_tiles<<<1, 1024, 0, st>>>(tmp, n_ptr, out);
+    k_scan_down<<<grid, kScanThreads, 0, st>>>(in, out, n_ptr, tmp);
     if (pf) { pf->launches += 2; pf->cls_launches[kScan] += 2; }
     return cudaGetLastError();
 }
@@ -1081,50 +1136,88 @@ cudaError_t launch_plan(const Work& w, const Params& p, Prof* pf, cudaStream_t s
     return cudaGetLastError();
 }
 
-cudaError_t launch_round(const Work& w, const Params& p, int cur, uint32_t L, uint32_t total_chunks,
-                         uint32_t total_counts, uint32_t n_med, int med_in, Prof* pf, cudaStream_t st) {
-    if (L) {
-        cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ScatterSmem));
+// Grid of a queue-driven kernel: one CTA per work item when the host knows
+// the count (0 = nothing to launch), else `fixed` persistent CTAs.
+static uint32_t grid_of(uint32_t fixed, const Hdr* hc, uint32_t known) { return hc ? known : fixed; }
+
+__global__ void k_advance(Work w) { w.hdr->round += 1u; }
+
+cudaError_t launch_round(const Work& w, const Params& p, const Hdr* hc, Prof* pf, cudaStream_t st) {
+    const uint32_t sms = p.num_sms;
+    const uint32_t gL = grid_of(sms * 2u, hc, hc ? hc->L : 0u);
+    if (gL) {
         {
             ProfScope ps(pf, kSample, st);
-            k_sample<<<L, 1024, 0, st>>>(w, p, cur);
+            k_sample<<<gL, 1024, 0, st>>>(w, p);
         }
         if (p.learned) {
-            cudaError_t e = launch_cdf_fit(w, p, L, pf, st);
+            cudaError_t e = launch_cdf_fit(w, p, grid_of(sms, hc, hc ? hc->L : 0u), pf, st);
             if (e != cudaSuccess) return e;
         }
+        const uint32_t gc = grid_of(sms * 4u, hc, hc ? hc->total_chunks : 0u);
         {
             ProfScope ps(pf, kClassify, st);
-            k_classify<<<total_chunks, kClassifyThreads, 0, st>>>(w, p, cur);
+            k_classify<<<gc, kClassifyThreads, 0, st>>>(w, p);
         }
-        cudaError_t e = launch_scan_u32(w.counts, w.counts_scan, total_counts, w.scan_tmp, pf, st);
+        cudaError_t e = launch_scan_u32(w.counts, w.counts_scan, &w.hdr->total_counts, hc ? &hc->total_counts : nullptr,
+                                        w.scan_tmp, pf, st);
         if (e != cudaSuccess) return e;
         {
             ProfScope ps(pf, kScatter, st);
-            k_scatter<<<total_chunks, kScatterThreads, sizeof(ScatterSmem), st>>>(w, p, cur, med_in ^ 1);
+            k_scatter<<<grid_of(sms * 2u, hc, hc ? hc->total_chunks : 0u), kScatterThreads, sizeof(ScatterSmem),
+                        st>>>(w, p);
         }
     }
-    if (n_med) {
-        cudaFuncSetAttribute(k_med_round, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MedSmem));
+    const uint32_t gm = grid_of(sms * 2u, hc, hc ? hc->n_med_snap : 0u);
+    if (gm) {
         ProfScope ps(pf, kMedium, st);
-        k_med_round<<<n_med, kScatterThreads, sizeof(MedSmem), st>>>(w, p, cur, med_in, med_in ^ 1);
+        k_med_round<<<gm, kScatterThreads, sizeof(MedSmem), st>>>(w, p);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_small(const Work& w, const Params& p, int buf, uint32_t n_small, uint32_t n_bigrun,
-                         uint32_t small_total, uint32_t* out_tiles, Prof* pf, cudaStream_t st) {
-    uint32_t tiles = 0;
-    if (n_small) {
-        cudaError_t e = launch_scan_u32(w.small_size, w.small_off, n_small, w.scan_tmp, pf, st);
+// Loop condition of the graph form: another round is needed while the last
+// plan left large or medium segments.
+__global__ void k_set_cond(Work w, cudaGraphConditionalHandle cond) {
+    cudaGraphSetConditional(cond, (w.hdr->L > 0u || w.hdr->n_med_snap > 0u) ? 1u : 0u);
+}
+
+cudaError_t launch_set_cond(const Work& w, cudaGraphConditionalHandle cond, cudaStream_t st) {
+    k_set_cond<<<1, 1, 0, st>>>(w, cond);
+    return cudaGetLastError();
+}
+
+// Shared-memory limits of the kernels that need more than 48 KB (set once,
+// outside any stream capture).
+cudaError_t prepare_kernels(uint32_t cdf_M) {
+    cudaError_t e = cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ScatterSmem));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_med_round, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MedSmem));
+    if (e == cudaSuccess) e = prepare_cdf_kernels(cdf_M);
+    return e;
+}
+
+cudaError_t launch_advance(const Work& w, Prof* pf, cudaStream_t st) {
+    ProfScope ps(pf, kPlan, st);
+    k_advance<<<1, 1, 0, st>>>(w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_small(const Work& w, const Params& p, const Hdr* hc, uint32_t* out_tiles, Prof* pf,
+                         cudaStream_t st) {
+    const uint32_t sms = p.num_sms;
+    uint32_t tiles = hc ? (hc->small_elems_snap + p.base_threshold - 1) / p.base_threshold : 0u;
+    if (!hc || hc->n_small_snap) {
+        cudaError_t e = launch_scan_u32(w.small_size, w.small_off, &w.hdr->n_small_snap,
+                                        hc ? &hc->n_small_snap : nullptr, w.scan_tmp, pf, st);
         if (e != cudaSuccess) return e;
-        tiles = (small_total + p.base_threshold - 1) / p.base_threshold;
         ProfScope ps(pf, kBase, st);
-        k_base<<<tiles, kBaseThreads, 0, st>>>(w, p.base_threshold, buf, n_small, small_total);
+        k_base<<<grid_of(sms * 8u, hc, tiles), kBaseThreads, 0, st>>>(w, p);
     }
-    if (n_bigrun) {
+    const uint32_t gr = grid_of(sms * 4u, hc, hc ? hc->n_bigrun_snap : 0u);
+    if (gr) {
         ProfScope ps(pf, kRuns, st);
-        k_bigrun<<<grid_for((uint64_t)n_bigrun * 256, 256, 4, p.num_sms), 256, 0, st>>>(w, buf, n_bigrun);
+        k_bigrun<<<gr, 256, 0, st>>>(w);
     }
     if (out_tiles) *out_tiles = tiles;
     return cudaGetLastError();

@@ -177,11 +177,14 @@ __device__ __forceinline__ void cdf_place(float u, uint32_t M, int& m, float& f)
 __global__ void __launch_bounds__(kFitThreads) k_cdf_fit(Work w, Params p) {
     extern __shared__ __align__(16) float fit_smem[];
     const uint32_t M = p.cdf_M;
-    const SegPlan P = w.plans[blockIdx.x];
-    if (P.size < kLearnedMinSize) return;
+    const uint32_t L = w.hdr->L;
+    __shared__ uint32_t s_item;
+    for (uint32_t seg = next_item(&w.hdr->q_fit, &s_item); seg < L; seg = next_item(&w.hdr->q_fit, &s_item)) {
+    const SegPlan P = w.plans[seg];
+    if (P.size < kLearnedMinSize) continue;
     const uint32_t S = (2u << P.k) - 1u;
     const CdfShared c = carve(fit_smem, M, kSampleMax);
-    const uint64_t* samp = w.cdf_samp + (size_t)blockIdx.x * kSampleMax;
+    const uint64_t* samp = w.cdf_samp + (size_t)seg * kSampleMax;
     const uint64_t kmin = samp[0], kmax = samp[S - 1];
     const float scale = kmax > kmin ? 1.0f / __ull2float_rn(kmax - kmin) : 0.0f;
     const uint64_t* ino = w.tree_ino + P.tree_base;
@@ -237,21 +240,27 @@ __global__ void __launch_bounds__(kFitThreads) k_cdf_fit(Work w, Params p) {
     for (uint32_t j = threadIdx.x; j < M; j += blockDim.x) c.P[j] = softplus_f(c.theta[j]);
     __syncthreads();
     const float T = block_excl_scan_f(c.P, M, c.wsum);
-    float* tab = w.cdf_tab + (size_t)blockIdx.x * (M + 1);
+    float* tab = w.cdf_tab + (size_t)seg * (M + 1);
     for (uint32_t j = threadIdx.x; j < M; j += blockDim.x) tab[j] = c.P[j] / T;
     if (threadIdx.x == 0) {
         tab[M] = 1.0f;
-        w.cdf_kmin[blockIdx.x] = kmin;
-        w.cdf_scale[blockIdx.x] = scale;
+        w.cdf_kmin[seg] = kmin;
+        w.cdf_scale[seg] = scale;
+    }
+    __syncthreads();  // shared arrays are rewritten by the next segment
     }
 }
 
-cudaError_t launch_cdf_fit(const Work& w, const Params& p, uint32_t L, Prof* pf, cudaStream_t st) {
-    const size_t smem = cdf_fit_smem(p.cdf_M);
+cudaError_t prepare_cdf_kernels(uint32_t M) {
+    const size_t smem = cdf_fit_smem(M);
     cudaError_t e = cudaFuncSetAttribute(k_cdf_fit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    return e;
+}
+
+cudaError_t launch_cdf_fit(const Work& w, const Params& p, uint32_t grid, Prof* pf, cudaStream_t st) {
+    const size_t smem = cdf_fit_smem(p.cdf_M);
     ProfScope ps(pf, kLearned, st);
-    k_cdf_fit<<<L, kFitThreads, smem, st>>>(w, p);
+    k_cdf_fit<<<grid, kFitThreads, smem, st>>>(w, p);
     return cudaGetLastError();
 }
 

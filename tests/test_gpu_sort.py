@@ -281,3 +281,51 @@ def test_full_size_workloads_verified(name):
     perm, lcp = gpu_sort(s)
     code, bad = oracle.verify(s.chars, s.offsets, perm, lcp)
     assert code == 0, (oracle.VERIFY_CODES[code], bad)
+
+
+# ------------------------------------------------------------------ graph form
+
+@pytest.mark.parametrize("opts", [SMALL_OPTS[0], SMALL_OPTS[1], SMALL_OPTS[3]])
+@pytest.mark.parametrize("kind,n,seed", [(2, 200_000, 61), (3, 100_000, 62), (1, 100_000, 63)])
+def test_graph_form_matches_oracle(opts, kind, n, seed):
+    sss.sss_set_options(graph=1, **opts)
+    s = gen.generate(kind, n, seed)
+    perm, lcp = gpu_sort(s)
+    assert_same(s, perm, lcp)
+    # the cached graph is relaunched on the same buffers
+    chars, offsets = to_dev(s)
+    st = sss.sss_get_last_stats()
+    assert st.rounds >= 1 and st.launches > 0
+
+
+@pytest.mark.parametrize("name", ["all_equal", "long_prefix_1k", "two_empty", "one", "high_bytes"])
+def test_graph_form_edge_cases(name):
+    sss.sss_set_options(graph=1, base_threshold=16, medium_threshold=64, k_max=3, chunk=2048)
+    items = list(EDGE_CASES[name])
+    random.Random(len(items)).shuffle(items)
+    s = gen.from_list(items)
+    perm, lcp = gpu_sort(s)
+    assert_same(s, perm, lcp)
+
+
+def test_graph_relaunch_is_repeatable():
+    sss.sss_set_options(graph=1)
+    s = gen.generate(2, 300_000, 64)
+    chars, offsets = to_dev(s)
+    perm = torch.empty(s.n, dtype=torch.int32, device="cuda")
+    lcp = torch.empty(s.n, dtype=torch.int32, device="cuda")
+    ref_perm, ref_lcp = oracle.sort(s.chars, s.offsets)
+    for _ in range(3):
+        perm.fill_(-1)
+        lcp.fill_(-1)
+        sss.sss_sort(chars, offsets, s.n, perm, lcp)
+        torch.cuda.synchronize()
+        assert np.array_equal(u32(perm), ref_perm)
+        assert np.array_equal(u32(lcp), ref_lcp)
+
+
+def test_graph_form_learned():
+    sss.sss_set_options(graph=1)
+    s = gen.generate(2, 300_000, 65)
+    perm, lcp = gpu_sort(s, learned=True)
+    assert_same(s, perm, lcp)
