@@ -37,6 +37,12 @@ WORKLOADS = {
     "url-64m": dict(kind=2, n=64_000_000, seed=4),
 }
 
+# batched workload: 10,000 sets, sizes log-uniform in [100, 4000] (about 500M
+# characters in total), kinds uniform, seed 5
+BATCH_WORKLOADS = {
+    "sets-10k": dict(num_sets=10_000, lo=100, hi=4000, seed=5),
+}
+
 SLACK = 16
 
 
@@ -65,7 +71,13 @@ def _load():
                                         ctypes.c_uint64, u64p]
         lib.gen_uniform_f64.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
                                         ctypes.POINTER(ctypes.c_double)]
-        for f in (lib.gen_lengths, lib.gen_fill, lib.gen_uniform_u64, lib.gen_uniform_f64):
+        ip = ctypes.POINTER(ctypes.c_int)
+        lib.gen_batch_lengths.argtypes = [ctypes.c_uint32, ip, u64p, u64p, ctypes.c_uint64,
+                                          ctypes.POINTER(ctypes.c_uint32), ctypes.c_int]
+        lib.gen_batch_fill.argtypes = [ctypes.c_uint32, ip, u64p, u64p, ctypes.c_uint64, u64p,
+                                       ctypes.POINTER(ctypes.c_uint8), ctypes.c_int]
+        for f in (lib.gen_lengths, lib.gen_fill, lib.gen_uniform_u64, lib.gen_uniform_f64,
+                  lib.gen_batch_lengths, lib.gen_batch_fill):
             f.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -161,21 +173,39 @@ def batch_sizes(num_sets: int, lo: int, hi: int, seed: int):
 
 
 def generate_batch(num_sets: int, lo: int, hi: int, seed: int, threads: int | None = None) -> Batch:
+    """num_sets independent sets, sizes log-uniform in [lo, hi], kinds uniform
+    in {1,2,3}; set j draws its strings from its own streams (seed
+    seed * 1000003 + j); the url pools and dna model come from `seed` and are
+    shared by the sets of a kind."""
+    lib = _load()
     sizes, kinds = batch_sizes(num_sets, lo, hi, seed)
-    parts = [generate(int(kinds[j]), int(sizes[j]), seed * 1_000_003 + j, threads)
-             for j in range(num_sets)]
-    total = sum(p.total for p in parts)
+    sizes = np.ascontiguousarray(sizes.astype(np.uint64))
+    kinds = np.ascontiguousarray(kinds.astype(np.int32))
+    seeds = np.ascontiguousarray((np.uint64(seed) * np.uint64(1_000_003) + np.arange(num_sets, dtype=np.uint64)))
     n = int(sizes.sum())
+    t = _threads(threads)
+    lens = np.zeros(max(n, 1), dtype=np.uint32)
+    if lib.gen_batch_lengths(num_sets, _ptr(kinds, ctypes.c_int), _ptr(sizes, ctypes.c_uint64),
+                             _ptr(seeds, ctypes.c_uint64), seed, _ptr(lens, ctypes.c_uint32), t) != 0:
+        raise RuntimeError("gen_batch_lengths failed")
+    lens = lens[:n]
+    offsets = np.zeros(max(n, 1), dtype=np.uint64)
+    if n > 1:
+        np.cumsum(lens[:-1], dtype=np.uint64, out=offsets[1:n])
+    offsets = offsets[:n]
+    total = int(lens.sum(dtype=np.uint64))
     chars = np.zeros(total + SLACK, dtype=np.uint8)
-    offsets = np.zeros(n, dtype=np.uint64)
+    if n and lib.gen_batch_fill(num_sets, _ptr(kinds, ctypes.c_int), _ptr(sizes, ctypes.c_uint64),
+                                _ptr(seeds, ctypes.c_uint64), seed, _ptr(offsets, ctypes.c_uint64),
+                                _ptr(chars, ctypes.c_uint8), t) != 0:
+        raise RuntimeError("gen_batch_fill failed")
     set_begin = np.zeros(num_sets + 1, dtype=np.uint64)
-    cpos = 0
-    spos = 0
-    for j, p in enumerate(parts):
-        chars[cpos:cpos + p.total] = p.chars[:p.total]
-        offsets[spos:spos + p.n] = p.offsets + np.uint64(cpos)
-        cpos += p.total
-        spos += p.n
-        set_begin[j + 1] = spos
+    set_begin[1:] = np.cumsum(sizes)
     return Batch(strings=Strings(chars=chars, offsets=offsets, n=n, total=total),
                  set_begin=set_begin, kinds=kinds)
+
+
+def set_strings(b: Batch, j: int) -> Strings:
+    """Set j of a batch as its own Strings (offsets rebased, shared chars)."""
+    lo, hi = int(b.set_begin[j]), int(b.set_begin[j + 1])
+    return Strings(chars=b.strings.chars, offsets=b.strings.offsets[lo:hi], n=hi - lo, total=0)

@@ -354,6 +354,96 @@ int gen_fill(int kind, uint64_t n, uint64_t seed, const uint64_t *offsets, uint8
     return rc;
 }
 
+/* ------------------------------------------------------------- batches
+ *
+ * Many independent sets in one call: set j has kind kinds[j], sizes[j]
+ * strings and its own per-string streams (seed seeds[j]); the url pools and
+ * the dna Markov model are built once from pool_seed and shared by all sets
+ * of that kind.  Sets are laid out back to back; lens / offsets are indexed
+ * globally.  Parallel over sets. */
+
+typedef struct {
+    uint32_t lo, hi; /* sets */
+    const int *kinds; const uint64_t *sizes, *seeds, *first;
+    uint32_t *lens; const uint64_t *offsets; uint8_t *chars;
+    const url_pools_t *pools; const dna_model_t *dna;
+} batch_job_t;
+
+static void *batch_run(void *arg) {
+    batch_job_t *b = (batch_job_t *)arg;
+    for (uint32_t j = b->lo; j < b->hi; j++) {
+        job_t jj;
+        memset(&jj, 0, sizeof(jj));
+        jj.kind = b->kinds[j];
+        jj.seed = b->seeds[j];
+        jj.pools = b->pools;
+        jj.dna = b->dna;
+        jj.lo = 0;
+        jj.hi = b->sizes[j];
+        uint32_t *src = NULL;
+        if (b->lens) {
+            jj.lens = b->lens + b->first[j];
+        } else {
+            jj.offsets = b->offsets + b->first[j];
+            jj.chars = b->chars;
+            if (jj.kind == 3) {
+                src = dna_sources(b->sizes[j], jj.seed);
+                if (!src) continue;
+                jj.src = src;
+            }
+        }
+        job_run(&jj);
+        free(src);
+    }
+    return NULL;
+}
+
+static int batch_common(uint32_t num_sets, const int *kinds, const uint64_t *sizes, const uint64_t *seeds,
+                        uint64_t pool_seed, uint32_t *lens, const uint64_t *offsets, uint8_t *chars, int nthreads) {
+    for (uint32_t j = 0; j < num_sets; j++)
+        if (kinds[j] < 1 || kinds[j] > 3) return -1;
+    uint64_t *first = (uint64_t *)malloc(sizeof(uint64_t) * (num_sets + 1));
+    if (!first) return -2;
+    first[0] = 0;
+    for (uint32_t j = 0; j < num_sets; j++) first[j + 1] = first[j] + sizes[j];
+    url_pools_t pools;
+    dna_model_t dna;
+    if (url_pools_init(&pools, pool_seed)) { free(first); return -2; }
+    dna_model_init(&dna, pool_seed);
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 64) nthreads = 64;
+    pthread_t th[64];
+    int spawned[64];
+    batch_job_t jobs[64];
+    for (int t = 0; t < nthreads; t++) {
+        batch_job_t bj = {0};
+        bj.lo = (uint32_t)((uint64_t)num_sets * t / nthreads);
+        bj.hi = (uint32_t)((uint64_t)num_sets * (t + 1) / nthreads);
+        bj.kinds = kinds; bj.sizes = sizes; bj.seeds = seeds; bj.first = first;
+        bj.lens = lens; bj.offsets = offsets; bj.chars = chars; bj.pools = &pools; bj.dna = &dna;
+        jobs[t] = bj;
+        spawned[t] = 0;
+        if (t == nthreads - 1) batch_run(&jobs[t]);
+        else if (pthread_create(&th[t], NULL, batch_run, &jobs[t]) == 0) spawned[t] = 1;
+        else batch_run(&jobs[t]);
+    }
+    for (int t = 0; t < nthreads - 1; t++)
+        if (spawned[t]) pthread_join(th[t], NULL);
+    url_pools_free(&pools);
+    free(first);
+    return 0;
+}
+
+int gen_batch_lengths(uint32_t num_sets, const int *kinds, const uint64_t *sizes, const uint64_t *seeds,
+                      uint64_t pool_seed, uint32_t *lens, int nthreads) {
+    return batch_common(num_sets, kinds, sizes, seeds, pool_seed, lens, NULL, NULL, nthreads);
+}
+
+int gen_batch_fill(uint32_t num_sets, const int *kinds, const uint64_t *sizes, const uint64_t *seeds,
+                   uint64_t pool_seed, const uint64_t *offsets, uint8_t *chars, int nthreads) {
+    return batch_common(num_sets, kinds, sizes, seeds, pool_seed, NULL, offsets, chars, nthreads);
+}
+
 /* uniform integers in [0, bound) from stream (seed, stream): used for set
  * sizes and kind choices of the batched workload */
 int gen_uniform_u64(uint64_t seed, uint64_t stream, uint64_t count, uint64_t bound, uint64_t *out) {

@@ -178,6 +178,24 @@ int sss_sort_batched(const uint8_t* chars, const uint64_t* offsets, uint32_t n,
                      const uint64_t* set_begin, uint32_t num_sets,
                      uint32_t* out_perm, uint32_t* out_lcp, void* stream);
 
+/* Autotuner for the batched sort (an addition to the paper): picks the tree
+ * depth (v = 2^k - 1 splitters, k = 5..10), the base-case threshold, the
+ * medium threshold and the device-wide work-item size ("tile") by coordinate
+ * descent, timing graph-form sss_sort_batched runs (median of three, CUDA
+ * events on stream) of the caller's tuning batch -- use a batch of the same
+ * shape as the real work but different data.  Arguments as for
+ * sss_sort_batched; out_perm/out_lcp (device) receive the last run's output.
+ * cache_path (host string, nullable): JSON-lines file; an entry whose key
+ * (device name, SM count, n and num_sets rounded to two significant digits)
+ * matches is used without timing anything, otherwise the winner is appended.
+ * The chosen options become the current options (sss_set_options) and are
+ * written to *out_best (host); *out_ms (host, nullable) gets the winner's
+ * time in milliseconds. */
+int sss_autotune_batched(const uint8_t* chars, const uint64_t* offsets, uint32_t n,
+                         const uint64_t* set_begin, uint32_t num_sets,
+                         uint32_t* out_perm, uint32_t* out_lcp, const char* cache_path,
+                         sss_options* out_best, double* out_ms, void* stream);
+
 /* Learned bucket proposal (an addition to the paper, closest to the jump
  * tables of App. A.2): as sss_sort, but in every device-wide distribution
  * round each segment of at least 65,536 strings fits a monotone

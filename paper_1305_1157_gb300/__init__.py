@@ -22,7 +22,7 @@ __all__ = [
     "SSSError", "sss_sort", "sss_sort_ws", "sss_sort_noalloc", "sss_sort_host", "sss_sort_batched", "sss_sort_learned",
     "sss_workspace_size", "sss_gather_keys", "sss_build_splitters", "sss_classify", "sss_cdf_loss_grad",
     "sss_set_options", "sss_get_options", "sss_get_last_stats", "sss_last_error", "sss_release",
-    "sss_version", "sss_options", "sss_stats", "load", "lib_path", "sort",
+    "sss_version", "sss_options", "sss_stats", "load", "lib_path", "sort", "sss_autotune_batched",
 ]
 
 STATUS = {0: "SSS_OK", -1: "SSS_ERR_INVALID", -2: "SSS_ERR_NOMEM", -3: "SSS_ERR_CUDA",
@@ -84,6 +84,8 @@ _SIG = {
     "sss_sort_noalloc": ([_P, _P, ctypes.c_uint32, _P, _P, _P], ctypes.c_int),
     "sss_sort_batched": ([_P, _P, ctypes.c_uint32, _P, ctypes.c_uint32, _P, _P, _P], ctypes.c_int),
     "sss_sort_learned": ([_P, _P, ctypes.c_uint32, _P, _P, _P], ctypes.c_int),
+    "sss_autotune_batched": ([_P, _P, ctypes.c_uint32, _P, ctypes.c_uint32, _P, _P, ctypes.c_char_p,
+                              ctypes.POINTER(sss_options), ctypes.POINTER(ctypes.c_double), _P], ctypes.c_int),
     "sss_gather_keys": ([_P, _P, _P, _P, ctypes.c_uint32, _P, _P], ctypes.c_int),
     "sss_build_splitters": ([_P, ctypes.c_uint32, ctypes.c_int32, _P, _P, _P], ctypes.c_int),
     "sss_classify": ([_P, ctypes.c_uint32, _P, _P, ctypes.c_int32, _P, _P], ctypes.c_int),
@@ -171,6 +173,16 @@ def sss_sort_host(chars, chars_bytes, offsets, n, out_perm, out_lcp):
 def sss_sort_batched(chars, offsets, n, set_begin, num_sets, out_perm, out_lcp, stream=None):
     _check(load().sss_sort_batched(_addr(chars), _addr(offsets), n, _addr(set_begin), num_sets,
                                    _addr(out_perm), _addr(out_lcp), _stream(stream)))
+
+
+def sss_autotune_batched(chars, offsets, n, set_begin, num_sets, out_perm, out_lcp, cache_path=None, stream=None):
+    """Returns (sss_options chosen, milliseconds of the chosen setting)."""
+    best = sss_options()
+    ms = ctypes.c_double(0.0)
+    path = cache_path.encode() if isinstance(cache_path, str) else cache_path
+    _check(load().sss_autotune_batched(_addr(chars), _addr(offsets), n, _addr(set_begin), num_sets, _addr(out_perm),
+                                       _addr(out_lcp), path, ctypes.byref(best), ctypes.byref(ms), _stream(stream)))
+    return best, ms.value
 
 
 def sss_sort_learned(chars, offsets, n, out_perm, out_lcp, stream=None):

@@ -11,7 +11,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "../../include/sss.h"
@@ -632,6 +634,150 @@ int sss_release(void) {
 const char* sss_version(void) { return "sss-gb300 0.1"; }
 
 }  // extern "C"
+
+// ------------------------------------------------------------ autotuner
+//
+// Coordinate descent over the knobs that shape the work: tree depth (v =
+// 2^k - 1 splitters, k = 5..10), base-case threshold, medium threshold and
+// the device-wide work-item size.  Each candidate is timed as the median of
+// three graph-form batched sorts of the caller's tuning batch (after one
+// untimed run that also builds its graph).  The winner is appended to a
+// JSON-lines cache keyed by device and batch shape.
+
+namespace {
+
+std::string tune_key(uint32_t n, uint32_t num_sets) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop;
+    memset(&prop, 0, sizeof(prop));
+    cudaGetDeviceProperties(&prop, dev);
+    // batch shape: strings and sets, each rounded to two significant digits
+    auto round2 = [](uint64_t x) {
+        uint64_t m = 1;
+        while (x >= 100) { x /= 10; m *= 10; }
+        return x * m;
+    };
+    char buf[256];
+    snprintf(buf, sizeof(buf), "%s|sm%d|n%llu|sets%llu", prop.name, prop.multiProcessorCount,
+             (unsigned long long)round2(n), (unsigned long long)round2(num_sets));
+    for (char* c = buf; *c; c++)
+        if (*c == '"' || *c == '\\') *c = '_';
+    return std::string(buf);
+}
+
+bool cache_lookup(const char* path, const std::string& key, sss_options& o, double& ms) {
+    if (!path) return false;
+    FILE* f = fopen(path, "r");
+    if (!f) return false;
+    char line[1024];
+    bool found = false;
+    const std::string want = "{\"key\": \"" + key + "\",";
+    while (fgets(line, sizeof(line), f)) {
+        if (strncmp(line, want.c_str(), want.size()) != 0) continue;
+        int k = 0;
+        unsigned b = 0, m = 0, c = 0;
+        double t = 0;
+        if (sscanf(line + want.size(), " \"k_max\": %d, \"base_threshold\": %u, \"medium_threshold\": %u, \"chunk\": %u, \"ms\": %lf",
+                   &k, &b, &m, &c, &t) == 5) {
+            o.k_max = k; o.base_threshold = b; o.medium_threshold = m; o.chunk = c;
+            ms = t;
+            found = true;  // the last entry for a key wins
+        }
+    }
+    fclose(f);
+    return found;
+}
+
+void cache_store(const char* path, const std::string& key, const sss_options& o, double ms) {
+    if (!path) return;
+    FILE* f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "{\"key\": \"%s\", \"k_max\": %d, \"base_threshold\": %u, \"medium_threshold\": %u, \"chunk\": %u, \"ms\": %.4f}\n",
+            key.c_str(), o.k_max, o.base_threshold, o.medium_threshold, o.chunk, ms);
+    fclose(f);
+}
+
+}  // namespace
+
+extern "C" int sss_autotune_batched(const uint8_t* chars, const uint64_t* offsets, uint32_t n,
+                                    const uint64_t* set_begin, uint32_t num_sets, uint32_t* out_perm,
+                                    uint32_t* out_lcp, const char* cache_path, sss_options* out_best,
+                                    double* out_ms, void* stream) {
+    std::lock_guard<std::mutex> g(g_mu);
+    if (!set_begin || !out_best) return fail(SSS_ERR_INVALID, "null pointer argument");
+    if (set_begin[0] != 0 || set_begin[num_sets] != n)
+        return fail(SSS_ERR_INVALID, "set_begin must start at 0 and end at n");
+    const std::string key = tune_key(n, num_sets);
+    sss_options best = g_opt;
+    double best_ms = 0.0;
+    if (cache_lookup(cache_path, key, best, best_ms) && check_options(best) == SSS_OK) {
+        g_opt = best;
+        *out_best = best;
+        if (out_ms) *out_ms = best_ms;
+        return SSS_OK;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0), "event");
+    CK(cudaEventCreate(&e1), "event");
+    const sss_options saved = g_opt;
+    auto time_opts = [&](const sss_options& o, double& ms) -> int {
+        g_opt = o;
+        int rc = sort_common(chars, offsets, n, out_perm, out_lcp, nullptr, 0, set_begin, num_sets, st);
+        if (rc) return rc;
+        double t[3];
+        for (int r = 0; r < 3; r++) {
+            cudaEventRecord(e0, st);
+            rc = sort_common(chars, offsets, n, out_perm, out_lcp, nullptr, 0, set_begin, num_sets, st);
+            if (rc) return rc;
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float f = 0.f;
+            cudaEventElapsedTime(&f, e0, e1);
+            t[r] = f;
+        }
+        std::sort(t, t + 3);
+        ms = t[1];
+        return SSS_OK;
+    };
+    int rc = time_opts(best, best_ms);
+    const int ks[] = {5, 6, 7, 8, 9, 10};
+    const uint32_t bases[] = {32, 64, 96, 128};
+    const uint32_t meds[] = {512, 1024, 2048, 4096, 8192};
+    const uint32_t chunks[] = {8192, 16384, 32768, 65536};
+    for (int pass = 0; pass < 2 && rc == SSS_OK; pass++) {
+        for (int knob = 0; knob < 4 && rc == SSS_OK; knob++) {
+            const int count = knob == 0 ? 6 : knob == 1 ? 4 : knob == 2 ? 5 : 4;
+            for (int c = 0; c < count && rc == SSS_OK; c++) {
+                sss_options o = best;
+                if (knob == 0) o.k_max = ks[c];
+                else if (knob == 1) o.base_threshold = bases[c];
+                else if (knob == 2) o.medium_threshold = meds[c];
+                else o.chunk = chunks[c];
+                if (o.medium_threshold < o.base_threshold) continue;
+                if (memcmp(&o, &best, sizeof(o)) == 0 || check_options(o) != SSS_OK) continue;
+                double ms = 0.0;
+                rc = time_opts(o, ms);
+                if (rc == SSS_OK && ms < best_ms) {
+                    best = o;
+                    best_ms = ms;
+                }
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) {
+        g_opt = saved;
+        return rc;
+    }
+    g_opt = best;
+    cache_store(cache_path, key, best, best_ms);
+    *out_best = best;
+    if (out_ms) *out_ms = best_ms;
+    return SSS_OK;
+}
 
 // ------------------------------------------------------------ allocation-free sort
 //
