@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle child (no D, no cpu_baseline)")
     ap.add_argument("--n", type=int, default=None,
                     help="sort only the first n strings of the workload's generator (profiling runs)")
+    ap.add_argument("--legs", default="graph,keys8,learned,batched",
+                    help="extra measurements beside the headline: graph,keys8,learned,batched (or none)")
     return ap.parse_args()
 
 
@@ -217,6 +219,139 @@ def run_reference(args, rank):
     return 0
 
 
+# ------------------------------------------------------------------ extra legs
+
+def _timed(torch, stream, dev, fn, steps, dist):
+    """Mean ms per call of fn over `steps` calls (CUDA events on stream), max over ranks."""
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = a.elapsed_time(b) / max(1, steps)
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms
+
+
+def leg_graph(sss, torch, chars, offsets, perm, lcp, n, stream, dev, args, world, dist):
+    """The same sort as one CUDA graph (device-side round loop)."""
+    o = sss.sss_get_options()
+    o.graph, o.profile = 1, 0
+    sss.sss_set_options(o)
+    fn = lambda: sss.sss_sort(chars, offsets, n, perm, lcp, stream)
+    for _ in range(max(2, args.warmup)):
+        fn()
+    ms = _timed(torch, stream, dev, fn, args.steps, dist)
+    st = sss.sss_get_last_stats()
+    o.graph = 0
+    sss.sss_set_options(o)
+    return {"value": n * world / (ms * 1e-3), "unit": "strings/s", "ms_per_step": ms, "steps": args.steps,
+            "gpu_launches_per_step": int(st.launches), "rounds": int(st.rounds)}
+
+
+def leg_keys8(sss, torch, chars, offsets, perm, lcp, n, stream, dev, args, world, dist):
+    """Graph form with one-word keys (w = 8 characters, the paper's key)
+    instead of two-word keys."""
+    o = sss.sss_get_options()
+    saved = o.key_bytes
+    o.graph, o.profile, o.key_bytes = 1, 0, 8
+    sss.sss_set_options(o)
+    fn = lambda: sss.sss_sort(chars, offsets, n, perm, lcp, stream)
+    for _ in range(max(2, args.warmup)):
+        fn()
+    steps = max(3, args.steps // 2)
+    ms = _timed(torch, stream, dev, fn, steps, dist)
+    st = sss.sss_get_last_stats()
+    o.graph, o.key_bytes = 0, saved
+    sss.sss_set_options(o)
+    return {"value": n * world / (ms * 1e-3), "unit": "strings/s", "ms_per_step": ms, "steps": steps,
+            "key_bytes": 8, "gpu_launches_per_step": int(st.launches), "rounds": int(st.rounds)}
+
+
+def leg_learned(sss, torch, chars, offsets, perm, lcp, n, stream, dev, args, world, dist):
+    """Learned bucket proposal (fitted CDF, exact verify, tree fallback) on the same workload."""
+    o = sss.sss_get_options()
+    o.graph, o.profile = 0, 0
+    sss.sss_set_options(o)
+    fn = lambda: sss.sss_sort_learned(chars, offsets, n, perm, lcp, stream)
+    for _ in range(max(2, args.warmup)):
+        fn()
+    steps = max(3, args.steps // 4)
+    ms = _timed(torch, stream, dev, fn, steps, dist)
+    st = sss.sss_get_last_stats()
+    # per-kernel split of one profiled run
+    o.profile = 1
+    sss.sss_set_options(o)
+    fn()
+    torch.cuda.synchronize(dev)
+    pst = sss.sss_get_last_stats().as_dict()
+    o.profile = 0
+    sss.sss_set_options(o)
+    prof = pst["profile"] or {}
+    return {"value": n * world / (ms * 1e-3), "unit": "strings/s", "ms_per_step": ms, "steps": steps,
+            "proposals": int(st.learned_keys), "misses": int(st.learned_misses),
+            "miss_rate": (st.learned_misses / st.learned_keys) if st.learned_keys else None,
+            "fit_ms": prof.get("learned", {}).get("ms"), "classify_ms": prof.get("classify", {}).get("ms"),
+            "cdf_segments": int(o.cdf_segments), "cdf_steps": int(o.cdf_steps)}
+
+
+def leg_batched(sss, torch, stream, dev, args, world, dist):
+    """10,000 independent sets: one graph launch (autotuned on a tuning batch
+    of the same shape, other seed) versus one sss_sort launch per set."""
+    import tempfile
+    w = gen.BATCH_WORKLOADS["sets-10k"]
+    tune = gen.generate_batch(w["num_sets"], w["lo"], w["hi"], w["seed"] + 1000)
+    real = gen.generate_batch(w["num_sets"], w["lo"], w["hi"], w["seed"])
+
+    def put(b):
+        s = b.strings
+        return (torch.from_numpy(s.chars).to(dev), torch.from_numpy(s.offsets.view(np.int64)).to(dev),
+                torch.empty(s.n, dtype=torch.int32, device=dev), torch.empty(s.n, dtype=torch.int32, device=dev))
+
+    saved = sss.sss_get_options()
+    t_chars, t_off, t_perm, t_lcp = put(tune)
+    with tempfile.TemporaryDirectory() as d:
+        best, tune_ms = sss.sss_autotune_batched(t_chars, t_off, tune.strings.n, tune.set_begin, w["num_sets"],
+                                                 t_perm, t_lcp, os.path.join(d, "autotune.jsonl"), stream)
+    del t_chars, t_off, t_perm, t_lcp
+    chars, off, perm, lcp = put(real)
+    n = real.strings.n
+    fn = lambda: sss.sss_sort_batched(chars, off, n, real.set_begin, w["num_sets"], perm, lcp, stream)
+    for _ in range(2):
+        fn()
+    steps = max(3, args.steps // 4)
+    ms = _timed(torch, stream, dev, fn, steps, dist)
+    st = sss.sss_get_last_stats()
+    # one launch sequence per set (host-driven rounds), all sets once
+    sss.sss_set_options(saved)
+    sb = real.set_begin.astype(np.int64)
+
+    def per_set():
+        for j in range(w["num_sets"]):
+            lo, hi = int(sb[j]), int(sb[j + 1])
+            sss.sss_sort(chars, off[lo:], hi - lo, perm[lo:], lcp[lo:], stream)
+
+    per_set()
+    ms_ps = _timed(torch, stream, dev, per_set, 1, dist)
+    return {"workload": "sets-10k: 10,000 sets, sizes log-uniform 100-4000, kinds uniform over "
+                        "uniform/url/dna, seed 5", "n": n, "chars_bytes": int(real.strings.total),
+            "value": n * world / (ms * 1e-3), "unit": "strings/s", "ms_per_step": ms, "steps": steps,
+            "graph_launches_per_step": 1, "kernel_launches_per_step": int(st.launches),
+            "per_set_value": n * world / (ms_ps * 1e-3), "per_set_ms": ms_ps,
+            "speedup_vs_per_set": ms_ps / ms,
+            "tuned": {"k_max": int(best.k_max), "base_threshold": int(best.base_threshold),
+                      "medium_threshold": int(best.medium_threshold), "chunk": int(best.chunk),
+                      "key_bytes": int(best.key_bytes), "tuning_ms": tune_ms}}
+
+
 # ------------------------------------------------------------------ gpu arm
 
 def main():
@@ -266,7 +401,7 @@ def main():
     prof_ms = np.zeros(len(sss.K_CLASSES))
     prof_launches = np.zeros(len(sss.K_CLASSES), dtype=np.int64)
     launches = 0
-    round_strings = refills = base_strings = 0
+    large_strings = large_refills = medium_strings = medium_refills = base_strings = 0
     clocks = ClockSampler(visible_gpu(local_rank))
     if dist:
         dist.barrier()
@@ -282,8 +417,10 @@ def main():
         launches += st.launches
         prof_ms += np.array(list(st.prof_ms))
         prof_launches += np.array(list(st.prof_launches))
-        round_strings += st.round_strings
-        refills += st.refilled_strings
+        large_strings += st.round_strings - st.medium_strings
+        large_refills += st.refilled_strings - st.medium_refilled_strings
+        medium_strings += st.medium_strings
+        medium_refills += st.medium_refilled_strings
         base_strings += st.base_strings
         last_stats = st.as_dict()
     t_end.record(stream)
@@ -320,6 +457,18 @@ def main():
         e2e = {"value": n * world / te, "unit": "strings/s", "h2d_bytes_per_step": int(len(s.chars) + 8 * n),
                "d2h_bytes_per_step": int(8 * n), "ms_per_step": te * 1e3}
 
+    legs = set(x for x in args.legs.split(",") if x and x != "none")
+    extra = {}
+    if "graph" in legs:
+        extra["graph_form"] = leg_graph(sss, torch, chars, offsets, perm, lcp, n, stream, dev, args, world, dist)
+    if "keys8" in legs:
+        extra["graph_form_keys8"] = leg_keys8(sss, torch, chars, offsets, perm, lcp, n, stream, dev, args, world,
+                                              dist)
+    if "learned" in legs:
+        extra["learned"] = leg_learned(sss, torch, chars, offsets, perm, lcp, n, stream, dev, args, world, dist)
+    if "batched" in legs:
+        extra["batched"] = leg_batched(sss, torch, stream, dev, args, world, dist)
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -328,16 +477,21 @@ def main():
     # roofline of the dominant kernel
     cls = sss.K_CLASSES
     dom = int(np.argmax(prof_ms))
-    algo = {"scatter": SCATTER_BYTES_PER_STRING * round_strings + REFILL_BYTES * refills,
-            "classify": CLASSIFY_BYTES_PER_STRING * round_strings,
+    # algorithmic bytes per kernel class: device-wide rounds (k_classify,
+    # k_scatter) see the large segments' strings, k_med_round the medium ones
+    algo = {"scatter": SCATTER_BYTES_PER_STRING * large_strings + REFILL_BYTES * large_refills,
+            "classify": CLASSIFY_BYTES_PER_STRING * large_strings,
+            "medium": SCATTER_BYTES_PER_STRING * medium_strings + REFILL_BYTES * medium_refills,
             "base": BASE_BYTES_PER_STRING * base_strings}
-    kname = {"scatter": "k_scatter", "classify": "k_classify", "base": "k_base"}.get(cls[dom], "k_" + cls[dom])
+    units = {"scatter": large_strings, "classify": large_strings, "medium": medium_strings,
+             "base": base_strings}
+    kname = {"scatter": "k_scatter", "classify": "k_classify", "base": "k_base",
+             "medium": "k_med_round"}.get(cls[dom], "k_" + cls[dom])
     peak, peak_kind = measured_hbm_peak()
     roofline = None
     if cls[dom] in algo and prof_ms[dom] > 0:
         achieved = algo[cls[dom]] / (prof_ms[dom] * 1e-3) / 1e9
-        per_launch_units = {"scatter": round_strings, "classify": round_strings,
-                            "base": base_strings}[cls[dom]] / max(1, prof_launches[dom])
+        per_launch_units = units[cls[dom]] / max(1, prof_launches[dom])
         tb = ncu_traffic(kname, args.workload)
         roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
                     "frac": achieved / peak, "peak_kind": f"of {peak_kind}",
@@ -372,7 +526,7 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": args.workload, "description": WORKLOAD_TEXT.get(args.workload, ""),
-                   "mode": args.mode, "n": n, "chars_bytes": int(s.total),
+                   "mode": args.mode, "key_bytes": int(opts.key_bytes), "n": n, "chars_bytes": int(s.total),
                    "D": D, "D_over_N": (D / s.total) if D else None,
                    "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
         "d_bytes_per_s": (D * world / (ms * 1e-3)) if D else None,
@@ -385,9 +539,11 @@ def main():
         "clocks": clk,
         "gpu_launches": int(launches),
         "kernels": kernel_share,
-        "sort_stats": {k: last_stats[k] for k in ("rounds", "base_tiles", "round_strings", "base_strings",
-                                                  "refilled_strings", "learned_keys", "learned_misses")},
+        "sort_stats": {k: last_stats[k] for k in ("rounds", "base_tiles", "round_strings", "medium_strings",
+                                                  "base_strings", "refilled_strings", "medium_refilled_strings",
+                                                  "learned_keys", "learned_misses")},
     }
+    line.update(extra)
     if oracle_info and "error" in oracle_info:
         line["oracle_error"] = oracle_info["error"]
     print(json.dumps(line), flush=True)

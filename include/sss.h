@@ -56,7 +56,7 @@ typedef enum {
 
 /* Tuning knobs.  Defaults: k_max 10, base_threshold 128, medium_threshold
  * 2048, chunk 32768, seed 0x5eed, cdf_segments 4096, cdf_steps 16,
- * cdf_lr 0.05, profile 0, graph 0. */
+ * cdf_lr 0.05, profile 0, graph 0, key_bytes 16. */
 typedef struct sss_options {
     int32_t k_max;             /* largest splitter tree depth k: v = 2^k - 1 splitters, 1..10 */
     uint32_t base_threshold;   /* buckets of at most this many strings go to the base case, 16..128 */
@@ -77,6 +77,11 @@ typedef struct sss_options {
                                 whose round loop is a device-side conditional node
                                 (no host round-trip per round; per-round stats not
                                 recorded).  sss_sort_batched always does. */
+    uint32_t key_bytes;      /* w, characters per classification key: 8 (one 64-bit
+                                key word, as in Sec. 3.1) or 16 (two words compared
+                                as one 128-bit key: a round steps over up to 16
+                                shared characters).  The learned proposal always
+                                uses 8.  The output does not depend on it. */
 } sss_options;
 
 #define SSS_MAX_ROUNDS_LOGGED 64
@@ -110,6 +115,7 @@ typedef struct sss_stats {
     uint64_t learned_keys;           /* keys the learned model proposed a bucket for */
     uint64_t learned_misses;         /* of those, proposals the exact check rejected */
     uint64_t refilled_strings;       /* key words gathered again from chars during rounds */
+    uint64_t medium_refilled_strings; /* of those, gathered in per-CTA (medium) rounds */
     uint32_t launches;               /* kernel launches of the call */
     uint32_t profiled;               /* 1 if the prof_* fields below were measured */
     uint32_t prof_launches[SSS_K_CLASSES]; /* launches per kernel class */

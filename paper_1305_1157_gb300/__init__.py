@@ -42,7 +42,8 @@ class sss_options(ctypes.Structure):
     _fields_ = [("k_max", ctypes.c_int32), ("base_threshold", ctypes.c_uint32),
                 ("medium_threshold", ctypes.c_uint32), ("chunk", ctypes.c_uint32),
                 ("seed", ctypes.c_uint64), ("cdf_segments", ctypes.c_uint32), ("cdf_steps", ctypes.c_uint32),
-                ("cdf_lr", ctypes.c_float), ("profile", ctypes.c_uint32), ("graph", ctypes.c_uint32)]
+                ("cdf_lr", ctypes.c_float), ("profile", ctypes.c_uint32), ("graph", ctypes.c_uint32),
+                ("key_bytes", ctypes.c_uint32)]
 
 
 class sss_stats(ctypes.Structure):
@@ -52,6 +53,7 @@ class sss_stats(ctypes.Structure):
                 ("base_strings", ctypes.c_uint64),
                 ("run_strings", ctypes.c_uint64), ("learned_keys", ctypes.c_uint64),
                 ("learned_misses", ctypes.c_uint64), ("refilled_strings", ctypes.c_uint64),
+                ("medium_refilled_strings", ctypes.c_uint64),
                 ("launches", ctypes.c_uint32), ("profiled", ctypes.c_uint32),
                 ("prof_launches", ctypes.c_uint32 * len(K_CLASSES)),
                 ("prof_ms", ctypes.c_double * len(K_CLASSES)),
@@ -65,7 +67,8 @@ class sss_stats(ctypes.Structure):
                 "base_segment_hist": list(self.base_segment_hist),
                 "base_strings": self.base_strings, "run_strings": self.run_strings,
                 "learned_keys": self.learned_keys, "learned_misses": self.learned_misses,
-                "refilled_strings": self.refilled_strings, "launches": self.launches,
+                "refilled_strings": self.refilled_strings,
+                "medium_refilled_strings": self.medium_refilled_strings, "launches": self.launches,
                 "profile": ({K_CLASSES[i]: {"launches": self.prof_launches[i], "ms": self.prof_ms[i]}
                              for i in range(len(K_CLASSES))} if self.profiled else None),
                 "round_segments": list(self.round_segments)[:min(r, MAX_ROUNDS_LOGGED)],

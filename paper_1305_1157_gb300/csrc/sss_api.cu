@@ -24,7 +24,7 @@ using namespace sss;
 namespace {
 
 std::mutex g_mu;
-sss_options g_opt = {10, 128u, 2048u, 32768u, 0x5eedull, 4096u, 16u, 0.05f, 0u, 0u};
+sss_options g_opt = {10, 128u, 2048u, 32768u, 0x5eedull, 4096u, 16u, 0.05f, 0u, 0u, 16u};
 sss_stats g_stats;
 Prof g_prof;
 char g_err[512] = "no error";
@@ -63,7 +63,7 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 struct Layout {
     size_t total = 0;
     size_t o_rec0, o_rec1, o_counts, o_counts_scan, o_tlvl, o_tino, o_plans, o_chunk_seg,
-        o_large, o_med0, o_med1, o_small, o_small_size, o_small_off, o_bigrun, o_scan_tmp, o_hdr, o_roots,
+        o_large, o_med0, o_med1, o_small, o_small_size, o_small_off, o_tile_first, o_bigrun, o_scan_tmp, o_hdr, o_roots,
         o_cdf_samp, o_cdf_tab, o_cdf_kmin, o_cdf_scale;
     uint32_t cmax, tmax, lmax, chmax, smax, bmax, scan_tmp_max, mmax;
 };
@@ -114,8 +114,8 @@ Layout layout_for(uint32_t n, const sss_options& o, uint32_t num_roots, bool lea
     L.o_rec1 = take(sizeof(Rec) * nn);
     L.o_counts = take(4 * (cmax + 1));
     L.o_counts_scan = take(4 * (cmax + 1));
-    L.o_tlvl = take(8 * tmax);
-    L.o_tino = take(8 * tmax);
+    L.o_tlvl = take(16 * tmax);  // 16 bytes a node: room for wide keys
+    L.o_tino = take(16 * tmax);
     L.o_plans = take(sizeof(SegPlan) * lmax);
     L.o_chunk_seg = take(4 * chmax);
     L.o_large = take(sizeof(Seg) * lmax);
@@ -124,6 +124,7 @@ Layout layout_for(uint32_t n, const sss_options& o, uint32_t num_roots, bool lea
     L.o_small = take(sizeof(Seg) * smax);
     L.o_small_size = take(4 * smax);
     L.o_small_off = take(4 * (smax + 1));
+    L.o_tile_first = take(4 * (nn / T + 2));
     L.o_bigrun = take(sizeof(Seg) * bmax);
     L.o_scan_tmp = take(4 * scan_tmp);
     L.o_hdr = take(sizeof(Hdr));
@@ -158,6 +159,7 @@ Work make_work(const Layout& L, char* ws, const uint8_t* chars, const uint64_t* 
     w.small = (Seg*)(ws + L.o_small);
     w.small_size = (uint32_t*)(ws + L.o_small_size);
     w.small_off = (uint32_t*)(ws + L.o_small_off);
+    w.tile_first = (uint32_t*)(ws + L.o_tile_first);
     w.bigrun = (Seg*)(ws + L.o_bigrun);
     w.scan_tmp = (uint32_t*)(ws + L.o_scan_tmp);
     w.hdr = (Hdr*)(ws + L.o_hdr);
@@ -181,6 +183,7 @@ int check_options(const sss_options& o) {
     if (o.chunk < kSubTile || o.chunk % kSubTile) return fail(SSS_ERR_INVALID, "chunk must be a positive multiple of %u", kSubTile);
     if (o.cdf_segments < 16 || o.cdf_segments > 4096 || (o.cdf_segments & (o.cdf_segments - 1)))
         return fail(SSS_ERR_INVALID, "cdf_segments must be a power of two in 16..4096");
+    if (o.key_bytes != 8 && o.key_bytes != 16) return fail(SSS_ERR_INVALID, "key_bytes must be 8 or 16");
     return SSS_OK;
 }
 
@@ -218,7 +221,7 @@ int read_hdr(Hdr* hh, const Work& w, cudaStream_t st) {
 int run_sort(const Work& w, const sss_options& o, const Seg* roots_dev, uint32_t num_roots, Hdr* hh,
              cudaStream_t st, sss_stats* stats, bool learned = false) {
     Params p{learned ? 1 : 0, o.cdf_segments, o.cdf_steps, o.cdf_lr, o.k_max, o.base_threshold,
-             o.medium_threshold, o.chunk, o.seed, device_sms(), 0u};
+             o.medium_threshold, o.chunk, o.seed, device_sms(), learned ? 8u : o.key_bytes};
     Prof* pf = &g_prof;
     pf->reset(o.profile != 0);
     memset(stats, 0, sizeof(*stats));
@@ -252,7 +255,8 @@ int run_sort(const Work& w, const sss_options& o, const Seg* roots_dev, uint32_t
     if (roots_dev) CK(launch_localize(w.out_perm, roots_dev, num_roots, pf, st), "localize");
     rc = read_hdr(hh, w, st);
     if (rc) return rc;
-    stats->refilled_strings = hh->refills;
+    stats->refilled_strings = hh->refills + hh->med_refills;
+    stats->medium_refilled_strings = hh->med_refills;
     stats->base_iterations = hh->base_iters;
     stats->learned_keys = hh->learned_keys;
     stats->learned_misses = hh->learned_misses;
@@ -388,7 +392,7 @@ int build_graph(const Work& w, const Params& p, const Seg* roots_dev, uint32_t n
 int run_sort_graph(const Work& w, const sss_options& o, const Seg* roots_dev, uint32_t num_roots, Hdr* hh,
                    cudaStream_t st, sss_stats* stats, bool learned, const GraphKey& key) {
     Params p{learned ? 1 : 0, o.cdf_segments, o.cdf_steps, o.cdf_lr, o.k_max, o.base_threshold,
-             o.medium_threshold, o.chunk, o.seed, device_sms(), 0u};
+             o.medium_threshold, o.chunk, o.seed, device_sms(), learned ? 8u : o.key_bytes};
     memset(stats, 0, sizeof(*stats));
     int dev = 0;
     CK(cudaGetDevice(&dev), "cudaGetDevice");
@@ -406,7 +410,8 @@ int run_sort_graph(const Work& w, const sss_options& o, const Seg* roots_dev, ui
     const int rc = read_hdr(hh, w, st);
     if (rc) return rc;
     stats->rounds = hh->round;
-    stats->refilled_strings = hh->refills;
+    stats->refilled_strings = hh->refills + hh->med_refills;
+    stats->medium_refilled_strings = hh->med_refills;
     stats->base_iterations = hh->base_iters;
     stats->learned_keys = hh->learned_keys;
     stats->learned_misses = hh->learned_misses;
@@ -638,8 +643,8 @@ const char* sss_version(void) { return "sss-gb300 0.1"; }
 // ------------------------------------------------------------ autotuner
 //
 // Coordinate descent over the knobs that shape the work: tree depth (v =
-// 2^k - 1 splitters, k = 5..10), base-case threshold, medium threshold and
-// the device-wide work-item size.  Each candidate is timed as the median of
+// 2^k - 1 splitters, k = 5..10), base-case threshold, medium threshold, the
+// device-wide work-item size and the key width (8 or 16 characters).  Each candidate is timed as the median of
 // three graph-form batched sorts of the caller's tuning batch (after one
 // untimed run that also builds its graph).  The winner is appended to a
 // JSON-lines cache keyed by device and batch shape.
@@ -676,11 +681,13 @@ bool cache_lookup(const char* path, const std::string& key, sss_options& o, doub
     while (fgets(line, sizeof(line), f)) {
         if (strncmp(line, want.c_str(), want.size()) != 0) continue;
         int k = 0;
-        unsigned b = 0, m = 0, c = 0;
+        unsigned b = 0, m = 0, c = 0, kb = 0;
         double t = 0;
-        if (sscanf(line + want.size(), " \"k_max\": %d, \"base_threshold\": %u, \"medium_threshold\": %u, \"chunk\": %u, \"ms\": %lf",
-                   &k, &b, &m, &c, &t) == 5) {
-            o.k_max = k; o.base_threshold = b; o.medium_threshold = m; o.chunk = c;
+        if (sscanf(line + want.size(),
+                   " \"k_max\": %d, \"base_threshold\": %u, \"medium_threshold\": %u, \"chunk\": %u, "
+                   "\"key_bytes\": %u, \"ms\": %lf",
+                   &k, &b, &m, &c, &kb, &t) == 6) {
+            o.k_max = k; o.base_threshold = b; o.medium_threshold = m; o.chunk = c; o.key_bytes = kb;
             ms = t;
             found = true;  // the last entry for a key wins
         }
@@ -693,8 +700,10 @@ void cache_store(const char* path, const std::string& key, const sss_options& o,
     if (!path) return;
     FILE* f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "{\"key\": \"%s\", \"k_max\": %d, \"base_threshold\": %u, \"medium_threshold\": %u, \"chunk\": %u, \"ms\": %.4f}\n",
-            key.c_str(), o.k_max, o.base_threshold, o.medium_threshold, o.chunk, ms);
+    fprintf(f,
+            "{\"key\": \"%s\", \"k_max\": %d, \"base_threshold\": %u, \"medium_threshold\": %u, \"chunk\": %u, "
+            "\"key_bytes\": %u, \"ms\": %.4f}\n",
+            key.c_str(), o.k_max, o.base_threshold, o.medium_threshold, o.chunk, o.key_bytes, ms);
     fclose(f);
 }
 
@@ -746,15 +755,17 @@ extern "C" int sss_autotune_batched(const uint8_t* chars, const uint64_t* offset
     const uint32_t bases[] = {32, 64, 96, 128};
     const uint32_t meds[] = {512, 1024, 2048, 4096, 8192};
     const uint32_t chunks[] = {8192, 16384, 32768, 65536};
+    const uint32_t widths[] = {8, 16};
     for (int pass = 0; pass < 2 && rc == SSS_OK; pass++) {
-        for (int knob = 0; knob < 4 && rc == SSS_OK; knob++) {
-            const int count = knob == 0 ? 6 : knob == 1 ? 4 : knob == 2 ? 5 : 4;
+        for (int knob = 0; knob < 5 && rc == SSS_OK; knob++) {
+            const int count = knob == 0 ? 6 : knob == 1 ? 4 : knob == 2 ? 5 : knob == 3 ? 4 : 2;
             for (int c = 0; c < count && rc == SSS_OK; c++) {
                 sss_options o = best;
                 if (knob == 0) o.k_max = ks[c];
                 else if (knob == 1) o.base_threshold = bases[c];
                 else if (knob == 2) o.medium_threshold = meds[c];
-                else o.chunk = chunks[c];
+                else if (knob == 3) o.chunk = chunks[c];
+                else o.key_bytes = widths[c];
                 if (o.medium_threshold < o.base_threshold) continue;
                 if (memcmp(&o, &best, sizeof(o)) == 0 || check_options(o) != SSS_OK) continue;
                 double ms = 0.0;

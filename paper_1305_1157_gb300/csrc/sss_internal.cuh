@@ -82,7 +82,8 @@ struct Hdr {
     uint32_t L, total_chunks, total_counts, total_tree;
     uint32_t n_med_snap, n_small_snap, n_bigrun_snap, small_elems_snap;
     uint32_t large_elems_snap, med_elems_snap, chunk, round;  // round: rounds done (buffer parity)
-    unsigned long long refills;   // key words gathered in rounds
+    unsigned long long refills;   // key words gathered in device-wide rounds
+    unsigned long long med_refills;  // key words gathered in medium (per-CTA) rounds
     unsigned long long base_iters;  // base-case refill iterations summed over tiles
     unsigned long long learned_keys, learned_misses;  // proposals made / rejected by the exact check
     // work queues of the persistent kernels (reset by k_plan)
@@ -116,7 +117,7 @@ struct Params {
     uint32_t chunk;           // largest work item of a device-wide round
     uint64_t seed;
     uint32_t num_sms;
-    uint32_t pad;
+    uint32_t key_bytes;       // w: 8 (one key word) or 16 (two words, wide keys)
 };
 
 // Views of the workspace and the caller's buffers for one sort.
@@ -139,6 +140,7 @@ struct Work {
     Seg* small;              // [smax]
     uint32_t* small_size;    // [smax]
     uint32_t* small_off;     // [smax + 1]
+    uint32_t* tile_first;    // [n / base_threshold + 2] first small segment packed into each base-case tile
     Seg* bigrun;             // [bmax]
     uint32_t* scan_tmp;      // [scan_tmp_max]
     Hdr* hdr;
@@ -265,6 +267,69 @@ __device__ __forceinline__ uint32_t key_chars(uint64_t k) {
     return k ? 8u - ((uint32_t)__ffsll((long long)k) - 1u) / 8u : 0u;
 }
 
+// ------------------------------------------------------------ key types
+
+// The classification key of a round: one word of w = 8 characters (Sec. 3.1)
+// or, in the wide form, two words (w = 16 characters) compared as one
+// 128-bit big-endian number.  A wide key lets one round step over 16 shared
+// characters, so inputs with long common prefixes need about half the rounds.
+struct __align__(16) Key16 {
+    uint64_t h, l;  // characters 0..7 and 8..15 at the depth
+};
+
+__device__ __forceinline__ bool kgt(uint64_t a, uint64_t b) { return a > b; }
+__device__ __forceinline__ bool kgt(const Key16& a, const Key16& b) { return a.h > b.h || (a.h == b.h && a.l > b.l); }
+__device__ __forceinline__ bool keq(uint64_t a, uint64_t b) { return a == b; }
+__device__ __forceinline__ bool keq(const Key16& a, const Key16& b) { return a.h == b.h && a.l == b.l; }
+template <class KT> __device__ __forceinline__ bool klt(const KT& a, const KT& b) { return kgt(b, a); }
+
+// The key holds the terminator (bytes after it are zero).
+__device__ __forceinline__ bool kends(uint64_t x) { return key_ends(x); }
+__device__ __forceinline__ bool kends(const Key16& x) { return key_ends(x.l); }
+// Characters before the terminator of a key that holds one.
+__device__ __forceinline__ uint32_t kchars(uint64_t x) { return key_chars(x); }
+__device__ __forceinline__ uint32_t kchars(const Key16& x) {
+    return key_ends(x.h) ? key_chars(x.h) : 8u + key_chars(x.l);
+}
+// Common leading characters of two different keys.
+__device__ __forceinline__ uint32_t klcp(uint64_t a, uint64_t b) { return key_lcp(a, b); }
+__device__ __forceinline__ uint32_t klcp(const Key16& a, const Key16& b) {
+    return a.h != b.h ? key_lcp(a.h, b.h) : 8u + key_lcp(a.l, b.l);
+}
+
+template <class KT> struct KeyTraits;
+template <> struct KeyTraits<uint64_t> {
+    static constexpr uint32_t kBytes = 8;
+    __device__ static __forceinline__ uint64_t of(const Rec& r) { return r.key; }
+    __device__ static __forceinline__ uint64_t load(const Rec* p) { return p->key; }
+    __device__ static __forceinline__ uint64_t top() { return ~0ull; }
+    __device__ static __forceinline__ uint64_t word(uint64_t x) { return x; }
+};
+template <> struct KeyTraits<Key16> {
+    static constexpr uint32_t kBytes = 16;
+    __device__ static __forceinline__ Key16 of(const Rec& r) { return Key16{r.key, r.key2}; }
+    __device__ static __forceinline__ Key16 load(const Rec* p) {
+        const ulonglong2 a = *reinterpret_cast<const ulonglong2*>(p);
+        return Key16{a.x, a.y};
+    }
+    __device__ static __forceinline__ Key16 top() { return Key16{~0ull, ~0ull}; }
+    __device__ static __forceinline__ uint64_t word(const Key16& x) { return x.h; }
+};
+
+// Moves a record's cached characters from `depth` to `new_depth`: the
+// narrow form may reuse the second cached word, the wide form needs both
+// words at the new depth and gathers them.
+template <class KT>
+__device__ __forceinline__ void refill_rec(const uint8_t* __restrict__ chars, Rec& r, uint32_t new_depth,
+                                           uint32_t depth) {
+    if (KeyTraits<KT>::kBytes == 8) {
+        refill(chars, r.key, r.key2, r.off, new_depth, new_depth - depth);
+    } else {
+        load_key2(chars, (r.off & kOffMask) + new_depth, r.key, r.key2);
+        r.off |= kK2Valid;
+    }
+}
+
 // Tree depth for a segment of `size` strings: about 16 strings per splitter.
 __host__ __device__ __forceinline__ int choose_k(uint32_t size, int k_max) {
 #ifdef __CUDA_ARCH__
@@ -280,12 +345,33 @@ __host__ __device__ __forceinline__ int choose_k(uint32_t size, int k_max) {
 
 // Branch-free descent of the level-order tree t[1..v] (Sec. 3.1, i := 2i + {0,1})
 // then one equality test against the in-order array: bucket 2j + [key = x_j].
-__device__ __forceinline__ uint32_t classify_key(uint64_t key, const uint64_t* t, const uint64_t* ino, int k) {
+template <class KT>
+__device__ __forceinline__ uint32_t classify_key(const KT& key, const KT* t, const KT* ino, int k) {
     uint32_t i = 1;
-    for (int l = 0; l < k; l++) i = 2u * i + (key > t[i] ? 1u : 0u);
+    for (int l = 0; l < k; l++) i = 2u * i + (kgt(key, t[i]) ? 1u : 0u);
     const uint32_t v = (1u << k) - 1u;
     const uint32_t j = i - (1u << k);
-    return 2u * j + ((j < v && key == ino[j]) ? 1u : 0u);
+    return 2u * j + ((j < v && keq(key, ino[j])) ? 1u : 0u);
+}
+
+// classify_key for U keys at once, descending the U paths level by level so
+// that each level issues U independent shared-memory loads (the interleaved
+// descents of Sec. 3.1).
+template <int U, class KT>
+__device__ __forceinline__ void classify_keys(const KT (&key)[U], uint32_t (&b)[U], const KT* t, const KT* ino, int k) {
+    uint32_t i[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) i[u] = 1u;
+    for (int l = 0; l < k; l++) {
+#pragma unroll
+        for (int u = 0; u < U; u++) i[u] = 2u * i[u] + (kgt(key[u], t[i[u]]) ? 1u : 0u);
+    }
+    const uint32_t v = (1u << k) - 1u;
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        const uint32_t j = i[u] - (1u << k);
+        b[u] = 2u * j + ((j < v && keq(key[u], ino[j])) ? 1u : 0u);
+    }
 }
 
 __device__ __forceinline__ uint64_t mix64(uint64_t z) {
@@ -294,11 +380,14 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
     return z ^ (z >> 31);
 }
 
-// Next work item of a persistent CTA from the queue counter q (items are
-// taken in order; the caller stops at its item count).  Contains barriers.
+// Work items of a queue-driven kernel: CTA b starts with item b, then takes
+// items gridDim.x, gridDim.x + 1, ... in order from the queue counter q (so a
+// grid of exactly one CTA per item never touches the counter); the caller
+// stops at its item count.  next_item contains barriers.
+__device__ __forceinline__ uint32_t first_item() { return blockIdx.x; }
 __device__ __forceinline__ uint32_t next_item(uint32_t* q, uint32_t* s_item) {
     __syncthreads();  // everyone is done with the previous item
-    if (threadIdx.x == 0) *s_item = atomicAdd(q, 1u);
+    if (threadIdx.x == 0) *s_item = gridDim.x + atomicAdd(q, 1u);
     __syncthreads();
     return *s_item;
 }

@@ -108,24 +108,25 @@ __device__ __forceinline__ void append_child(const Work& w, const Params& p, int
 }
 
 // Child depth of bucket b of a segment at depth `depth` (Eq. (1), Sec. 3.1):
-// b_0 and b_2v keep it, the equality bucket of x_i adds w = 8 (or is a run of
-// equal strings when x_i holds the terminator), an inner even bucket adds
-// lcp(x_{i-1}, x_i).
+// b_0 and b_2v keep it, the equality bucket of x_i adds w (8, or 16 for wide
+// keys; or is a run of equal strings when x_i holds the terminator), an inner
+// even bucket adds lcp(x_{i-1}, x_i).
 struct BucketInfo {
     uint32_t cdepth, runlcp;
     bool isrun;
 };
 
-__device__ __forceinline__ BucketInfo bucket_info(uint32_t b, uint32_t nb, uint32_t depth, const uint64_t* ino,
+template <class KT>
+__device__ __forceinline__ BucketInfo bucket_info(uint32_t b, uint32_t nb, uint32_t depth, const KT* ino,
                                                   uint32_t size) {
     BucketInfo bi{depth, 0u, false};
     if (b & 1u) {
-        const uint64_t x = ino[b >> 1];
-        if (key_ends(x)) { bi.isrun = true; bi.runlcp = depth + key_chars(x); }
-        else bi.cdepth = depth + 8u;
+        const KT x = ino[b >> 1];
+        if (kends(x)) { bi.isrun = true; bi.runlcp = depth + kchars(x); }
+        else bi.cdepth = depth + KeyTraits<KT>::kBytes;
     } else if (b != 0 && b != nb - 1 && size > 0) {
         const uint32_t i = b >> 1;
-        bi.cdepth = depth + key_lcp(ino[i - 1], ino[i]);
+        bi.cdepth = depth + klcp(ino[i - 1], ino[i]);
     }
     return bi;
 }
@@ -157,6 +158,7 @@ __global__ void k_hdr_reset(Work w) {
     h->n_large = 0; h->n_med = 0; h->n_small = 0; h->n_bigrun = 0; h->err = 0;
     h->small_elems = 0; h->med_elems = 0;
     h->refills = 0ull;
+    h->med_refills = 0ull;
     h->base_iters = 0ull;
     h->learned_keys = 0ull;
     h->learned_misses = 0ull;
@@ -248,35 +250,38 @@ __global__ void __launch_bounds__(1024) k_plan(Work w, Params p) {
 // ------------------------------------------------------------ sample + tree
 
 // Ascending bitonic sort of s[0..pw) (pw a power of two) by the whole block.
-__device__ void bitonic_sort_u64(uint64_t* s, uint32_t pw) {
+template <class KT>
+__device__ void bitonic_sort(KT* s, uint32_t pw) {
     for (uint32_t size = 2; size <= pw; size <<= 1) {
         for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
             for (uint32_t i = threadIdx.x; i < pw / 2; i += blockDim.x) {
                 uint32_t lo = 2u * i - (i & (stride - 1u));
                 uint32_t hi = lo + stride;
                 bool asc = (lo & size) == 0;
-                uint64_t a = s[lo], b = s[hi];
-                if ((a > b) == asc) { s[lo] = b; s[hi] = a; }
+                const KT a = s[lo], b = s[hi];
+                if (kgt(a, b) == asc) { s[lo] = b; s[hi] = a; }
             }
             __syncthreads();
         }
     }
 }
 
-__device__ __forceinline__ uint32_t lower_bound_u64(const uint64_t* s, uint32_t n, uint64_t x) {
+template <class KT>
+__device__ __forceinline__ uint32_t lower_bound_k(const KT* s, uint32_t n, const KT& x) {
     uint32_t lo = 0, hi = n;
     while (lo < hi) {
         uint32_t m = (lo + hi) >> 1;
-        if (s[m] < x) lo = m + 1; else hi = m;
+        if (klt(s[m], x)) lo = m + 1; else hi = m;
     }
     return lo;
 }
 
-__device__ __forceinline__ uint32_t upper_bound_u64(const uint64_t* s, uint32_t n, uint64_t x) {
+template <class KT>
+__device__ __forceinline__ uint32_t upper_bound_k(const KT* s, uint32_t n, const KT& x) {
     uint32_t lo = 0, hi = n;
     while (lo < hi) {
         uint32_t m = (lo + hi) >> 1;
-        if (s[m] <= x) lo = m + 1; else hi = m;
+        if (!kgt(s[m], x)) lo = m + 1; else hi = m;
     }
     return lo;
 }
@@ -286,7 +291,8 @@ __device__ __forceinline__ uint32_t upper_bound_u64(const uint64_t* s, uint32_t 
 // where b' and a' skip every sample equal to x.  A node whose range is empty
 // repeats its parent's splitter.  Level by level, one thread per node.
 // lvl[1..v] receives the level-order tree; ra/rb: shared scratch [v+1].
-__device__ void select_splitters(const uint64_t* s, uint32_t cnt, int k, uint64_t* lvl, int32_t* ra, int32_t* rb) {
+template <class KT>
+__device__ void select_splitters(const KT* s, uint32_t cnt, int k, KT* lvl, int32_t* ra, int32_t* rb) {
     const uint32_t v = (1u << k) - 1u;
     if (threadIdx.x == 0) { ra[1] = 0; rb[1] = (int32_t)cnt - 1; }
     __syncthreads();
@@ -294,13 +300,13 @@ __device__ void select_splitters(const uint64_t* s, uint32_t cnt, int k, uint64_
         const uint32_t first = 1u << l;
         for (uint32_t i = first + threadIdx.x; i < 2u * first; i += blockDim.x) {
             int32_t a = ra[i], b = rb[i];
-            uint64_t x;
+            KT x;
             int32_t bl, ar;
             if (a <= b) {
                 int32_t m = a + (b - a) / 2;
                 x = s[m];
-                int32_t first_eq = (int32_t)lower_bound_u64(s, cnt, x);
-                int32_t past_eq = (int32_t)upper_bound_u64(s, cnt, x);
+                int32_t first_eq = (int32_t)lower_bound_k(s, cnt, x);
+                int32_t past_eq = (int32_t)upper_bound_k(s, cnt, x);
                 bl = max(a, first_eq) - 1;
                 ar = min(b + 1, past_eq);
             } else {
@@ -320,7 +326,8 @@ __device__ void select_splitters(const uint64_t* s, uint32_t cnt, int k, uint64_
 
 // Writes the tree lvl[1..v] to out_lvl[0..v) and its in-order sequence to
 // out_ino[0..v).  Ends with __syncthreads.
-__device__ void emit_tree(const uint64_t* lvl, int k, uint64_t* out_lvl, uint64_t* out_ino) {
+template <class KT>
+__device__ void emit_tree(const KT* lvl, int k, KT* out_lvl, KT* out_ino) {
     const uint32_t v = (1u << k) - 1u;
     for (uint32_t i = 1 + threadIdx.x; i <= v; i += blockDim.x) {
         uint32_t l = 31u - __clz(i);
@@ -340,28 +347,38 @@ __device__ __forceinline__ uint32_t sample_pos(uint64_t seed, uint32_t begin, ui
     return (uint32_t)(((uint64_t)r * size) >> 32);
 }
 
+template <class KT>
+struct SampleSmem {
+    KT samp[kSampleMax];
+    KT lvl[kVMax + 1];
+    int32_t ra[kVMax + 1], rb[kVMax + 1];
+};
+
+template <class KT>
 __global__ void __launch_bounds__(1024) k_sample(Work w, Params p) {
-    __shared__ uint64_t samp[kSampleMax];
-    __shared__ uint64_t lvl[kVMax + 1];
-    __shared__ int32_t ra[kVMax + 1], rb[kVMax + 1];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SampleSmem<KT>& sm = *reinterpret_cast<SampleSmem<KT>*>(smem_raw);
     __shared__ uint32_t s_item;
     const Rec* recs = w.rec[w.hdr->round & 1u];
     const uint32_t L = w.hdr->L;
-    for (uint32_t seg = next_item(&w.hdr->q_sample, &s_item); seg < L; seg = next_item(&w.hdr->q_sample, &s_item)) {
+    KT* tree_lvl = reinterpret_cast<KT*>(w.tree_lvl);
+    KT* tree_ino = reinterpret_cast<KT*>(w.tree_ino);
+    for (uint32_t seg = first_item(); seg < L; seg = next_item(&w.hdr->q_sample, &s_item)) {
         const SegPlan P = w.plans[seg];
         const int k = (int)P.k;
         const uint32_t pw = 2u << k;
         const uint32_t cnt = pw - 1u;  // alpha (v + 1) - 1 with alpha = 2
         for (uint32_t j = threadIdx.x; j < pw; j += blockDim.x)
-            samp[j] = j < cnt ? recs[P.begin + sample_pos(p.seed, P.begin, P.size, j)].key : ~0ull;
+            sm.samp[j] = j < cnt ? KeyTraits<KT>::load(recs + P.begin + sample_pos(p.seed, P.begin, P.size, j))
+                                 : KeyTraits<KT>::top();
         __syncthreads();
-        bitonic_sort_u64(samp, pw);
+        bitonic_sort(sm.samp, pw);
         if (p.learned) {
             uint64_t* out = w.cdf_samp + (size_t)seg * kSampleMax;
-            for (uint32_t j = threadIdx.x; j < cnt; j += blockDim.x) out[j] = samp[j];
+            for (uint32_t j = threadIdx.x; j < cnt; j += blockDim.x) out[j] = KeyTraits<KT>::word(sm.samp[j]);
         }
-        select_splitters(samp, cnt, k, lvl, ra, rb);
-        emit_tree(lvl, k, w.tree_lvl + P.tree_base, w.tree_ino + P.tree_base);
+        select_splitters(sm.samp, cnt, k, sm.lvl, sm.ra, sm.rb);
+        emit_tree(sm.lvl, k, tree_lvl + P.tree_base, tree_ino + P.tree_base);
     }
 }
 
@@ -375,7 +392,7 @@ __global__ void __launch_bounds__(1024) k_build_splitters(const uint64_t* sample
     while (pw < count) pw <<= 1;
     for (uint32_t j = threadIdx.x; j < pw; j += blockDim.x) samp[j] = j < count ? sample[j] : ~0ull;
     __syncthreads();
-    bitonic_sort_u64(samp, pw);
+    bitonic_sort(samp, pw);
     select_splitters(samp, count, k, lvl, ra, rb);
     emit_tree(lvl, k, out_lvl, out_ino);
 }
@@ -383,26 +400,28 @@ __global__ void __launch_bounds__(1024) k_build_splitters(const uint64_t* sample
 // ------------------------------------------------------------ classify + count
 
 constexpr int kClassifyThreads = 256;
-constexpr int kClassifyUnroll = 4;
+constexpr int kClassifyUnroll = 8;
 
 // Adds the buckets of the key words of recs[lo, hi) to hist (warp-aggregated shared atomics);
 // bid (optional) receives each bucket at bid[e - lo].  Loop bounds are
 // uniform over the block.
-__device__ __forceinline__ void classify_range(const Rec* __restrict__ recs, uint32_t lo, uint32_t hi,
-                                               const uint64_t* t, const uint64_t* ino, int k, uint32_t nb,
-                                               uint32_t* hist, uint16_t* bid) {
+template <class KT>
+__device__ __forceinline__ void classify_range(const Rec* __restrict__ recs, uint32_t lo, uint32_t hi, const KT* t,
+                                               const KT* ino, int k, uint32_t nb, uint32_t* hist, uint16_t* bid) {
     const uint32_t lane = threadIdx.x & 31u;
     for (uint32_t base = lo; base < hi; base += blockDim.x * kClassifyUnroll) {
-        uint64_t kk[kClassifyUnroll];
+        KT kk[kClassifyUnroll];
 #pragma unroll
         for (int u = 0; u < kClassifyUnroll; u++) {
             const uint32_t e = base + u * blockDim.x + threadIdx.x;
-            kk[u] = e < hi ? recs[e].key : 0ull;
+            kk[u] = e < hi ? KeyTraits<KT>::load(recs + e) : KeyTraits<KT>::top();
         }
+        uint32_t bk[kClassifyUnroll];
+        classify_keys<kClassifyUnroll>(kk, bk, t, ino, k);
 #pragma unroll
         for (int u = 0; u < kClassifyUnroll; u++) {
             const uint32_t e = base + u * blockDim.x + threadIdx.x;
-            const uint32_t b = e < hi ? classify_key(kk[u], t, ino, k) : nb;
+            const uint32_t b = e < hi ? bk[u] : nb;
             if (bid && e < hi) bid[e - lo] = (uint16_t)b;
             const uint32_t peers = __match_any_sync(FULL_MASK, b);
             if (lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&hist[b], (uint32_t)__popc(peers));
@@ -441,15 +460,19 @@ __device__ __forceinline__ void classify_range_learned(const Rec* __restrict__ r
 
 constexpr uint32_t kCdfMMax = 4096;
 
+template <class KT>
 __global__ void __launch_bounds__(kClassifyThreads) k_classify(Work w, Params p) {
-    __shared__ uint64_t t[kVMax + 1];
-    __shared__ uint64_t ino[kVMax];
+    constexpr bool kLearned = KeyTraits<KT>::kBytes == 8;  // the learned model proposes on one word
+    __shared__ KT t[kVMax + 1];
+    __shared__ KT ino[kVMax];
     __shared__ uint32_t hist[kNBMax + 1];
-    __shared__ float C[kCdfMMax + 1];
+    __shared__ float C[kLearned ? kCdfMMax + 1 : 1];
     __shared__ uint32_t s_item;
     const int cur = w.hdr->round & 1u;
     const uint32_t total_chunks = w.hdr->total_chunks;
-    for (uint32_t c = next_item(&w.hdr->q_classify, &s_item); c < total_chunks;
+    const KT* tree_lvl = reinterpret_cast<const KT*>(w.tree_lvl);
+    const KT* tree_ino = reinterpret_cast<const KT*>(w.tree_ino);
+    for (uint32_t c = first_item(); c < total_chunks;
          c = next_item(&w.hdr->q_classify, &s_item)) {
         const uint32_t s = w.chunk_seg[c];
         const SegPlan P = w.plans[s];
@@ -457,25 +480,30 @@ __global__ void __launch_bounds__(kClassifyThreads) k_classify(Work w, Params p)
         const int k = (int)P.k;
         const uint32_t v = (1u << k) - 1u, nb = 2u * v + 1u;
         for (uint32_t i = threadIdx.x; i < v; i += blockDim.x) {
-            t[i + 1] = w.tree_lvl[P.tree_base + i];
-            ino[i] = w.tree_ino[P.tree_base + i];
+            t[i + 1] = tree_lvl[P.tree_base + i];
+            ino[i] = tree_ino[P.tree_base + i];
         }
         for (uint32_t b = threadIdx.x; b <= nb; b += blockDim.x) hist[b] = 0;
         __syncthreads();
         const uint32_t lo = P.begin + ci * P.chunk;
         const uint32_t hi = min(lo + P.chunk, P.begin + P.size);
-        if (p.learned && P.size >= kLearnedMinSize) {
-            const float* tab = w.cdf_tab + (size_t)s * (p.cdf_M + 1);
-            for (uint32_t j = threadIdx.x; j <= p.cdf_M; j += blockDim.x) C[j] = tab[j];
-            __syncthreads();
-            uint32_t misses = 0;
-            classify_range_learned(w.rec[cur], lo, hi, t, ino, k, nb, hist, C, p.cdf_M, w.cdf_kmin[s],
-                                   w.cdf_scale[s], misses);
-            misses = __reduce_add_sync(FULL_MASK, misses);
-            if ((threadIdx.x & 31u) == 0 && misses) atomicAdd(&w.hdr->learned_misses, (unsigned long long)misses);
-            if (threadIdx.x == 0) atomicAdd(&w.hdr->learned_keys, (unsigned long long)(hi - lo));
+        if constexpr (kLearned) {
+            if (p.learned && P.size >= kLearnedMinSize) {
+                const float* tab = w.cdf_tab + (size_t)s * (p.cdf_M + 1);
+                for (uint32_t j = threadIdx.x; j <= p.cdf_M; j += blockDim.x) C[j] = tab[j];
+                __syncthreads();
+                uint32_t misses = 0;
+                classify_range_learned(w.rec[cur], lo, hi, t, ino, k, nb, hist, C, p.cdf_M, w.cdf_kmin[s],
+                                       w.cdf_scale[s], misses);
+                misses = __reduce_add_sync(FULL_MASK, misses);
+                if ((threadIdx.x & 31u) == 0 && misses)
+                    atomicAdd(&w.hdr->learned_misses, (unsigned long long)misses);
+                if (threadIdx.x == 0) atomicAdd(&w.hdr->learned_keys, (unsigned long long)(hi - lo));
+            } else {
+                classify_range(w.rec[cur], lo, hi, t, ino, k, nb, hist, (uint16_t*)nullptr);
+            }
         } else {
-            classify_range(w.rec[cur], lo, hi, t, ino, k, nb, hist, nullptr);
+            classify_range(w.rec[cur], lo, hi, t, ino, k, nb, hist, (uint16_t*)nullptr);
         }
         __syncthreads();
         for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x)
@@ -505,9 +533,9 @@ struct ScatterState {
 // offset of each warp.  Needs: ss.run_pos/rdep set, ss.whist zero (columns
 // 0..nb), the tree in t/ino (or bucket ids in bid[e - lo]), 256 threads.
 // Returns this thread's number of key words gathered again.
-template <int NBCAP, bool kFromBid>
+template <int NBCAP, bool kFromBid, class KT>
 __device__ uint32_t scatter_range(const Work& w, int cur, uint32_t lo, uint32_t hi, uint32_t nb,
-                                  ScatterState<NBCAP>& ss, const uint64_t* t, const uint64_t* ino, int k,
+                                  ScatterState<NBCAP>& ss, const KT* t, const KT* ino, int k,
                                   const uint16_t* bid, uint32_t seg_end, uint32_t depth, const float* C = nullptr,
                                   uint32_t M = 0, uint64_t kmin = 0, float scale = 0.0f) {
     constexpr int kBucketsPerThread = (NBCAP + kScatterThreads) / kScatterThreads;
@@ -528,15 +556,28 @@ __device__ uint32_t scatter_range(const Work& w, int cur, uint32_t lo, uint32_t 
             else rr[j] = Rec{0ull, 0ull, 0ull, 0u, 0u};
             if (kFromBid) bb[j] = ok ? bid[e - lo] : nb;
         }
-        if (!kFromBid) {
+        bool proposed = false;
+        if constexpr (!kFromBid && KeyTraits<KT>::kBytes == 8) {
+            if (C) {
 #pragma unroll
-            for (int j = 0; j < kScatterItems; j++) {
-                const uint32_t e = wbase + j * 32u;
-                uint32_t b = nb;
-                if (e < hi && !(C && propose_bucket(rr[j].key, C, M, kmin, scale, ino, (nb - 1u) / 2u, b)))
-                    b = classify_key(rr[j].key, t, ino, k);
-                bb[j] = b;
+                for (int j = 0; j < kScatterItems; j++) {
+                    const uint32_t e = wbase + j * 32u;
+                    uint32_t b = nb;
+                    if (e < hi && !propose_bucket(rr[j].key, C, M, kmin, scale, ino, (nb - 1u) / 2u, b))
+                        b = classify_key(rr[j].key, t, ino, k);
+                    bb[j] = b;
+                }
+                proposed = true;
             }
+        }
+        if (!kFromBid && !proposed) {
+            KT kk[kScatterItems];
+#pragma unroll
+            for (int j = 0; j < kScatterItems; j++) kk[j] = KeyTraits<KT>::of(rr[j]);
+            classify_keys<kScatterItems>(kk, bb, t, ino, k);
+#pragma unroll
+            for (int j = 0; j < kScatterItems; j++)
+                if (wbase + j * 32u >= hi) bb[j] = nb;
         }
         // next key words of strings whose bucket moves deeper: all gathers are
         // issued here, before any store, and complete during the ranking
@@ -544,7 +585,7 @@ __device__ uint32_t scatter_range(const Work& w, int cur, uint32_t lo, uint32_t 
         for (int j = 0; j < kScatterItems; j++) {
             const uint32_t rd = bb[j] < nb ? ss.rdep[bb[j]] : kNoRefill;
             if (rd != kNoRefill && rd != kSingle) {
-                refill(w.chars, rr[j].key, rr[j].key2, rr[j].off, rd, rd - depth);
+                refill_rec<KT>(w.chars, rr[j], rd, depth);
                 nref++;
             }
         }
@@ -609,26 +650,30 @@ __device__ uint32_t scatter_range(const Work& w, int cur, uint32_t lo, uint32_t 
     return nref;
 }
 
-__device__ __forceinline__ void add_refills(const Work& w, uint32_t nref) {
+__device__ __forceinline__ void add_refills(unsigned long long* counter, uint32_t nref) {
     nref = __reduce_add_sync(FULL_MASK, nref);
-    if ((threadIdx.x & 31u) == 0 && nref) atomicAdd(&w.hdr->refills, (unsigned long long)nref);
+    if ((threadIdx.x & 31u) == 0 && nref) atomicAdd(counter, (unsigned long long)nref);
 }
 
+template <class KT>
 struct ScatterSmem {
-    uint64_t t[kVMax + 1];
-    uint64_t ino[kVMax];
+    KT t[kVMax + 1];
+    KT ino[kVMax];
     ScatterState<kNBMax> ss;
-    float C[kCdfMMax + 1];  // learned model knots (learned mode only)
+    float C[KeyTraits<KT>::kBytes == 8 ? kCdfMMax + 1 : 1];  // learned model knots (learned mode only)
 };
 
+template <class KT>
 __global__ void __launch_bounds__(kScatterThreads, SSS_SCATTER_MIN_BLOCKS) k_scatter(Work w, Params p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    ScatterSmem& sm = *reinterpret_cast<ScatterSmem*>(smem_raw);
+    ScatterSmem<KT>& sm = *reinterpret_cast<ScatterSmem<KT>*>(smem_raw);
+    const KT* tree_lvl = reinterpret_cast<const KT*>(w.tree_lvl);
+    const KT* tree_ino = reinterpret_cast<const KT*>(w.tree_ino);
     const int cur = w.hdr->round & 1u;
     const int med_out = cur ^ 1;
     const uint32_t total_chunks = w.hdr->total_chunks;
     __shared__ uint32_t s_item;
-    for (uint32_t c = next_item(&w.hdr->q_scatter, &s_item); c < total_chunks;
+    for (uint32_t c = first_item(); c < total_chunks;
          c = next_item(&w.hdr->q_scatter, &s_item)) {
         const uint32_t s = w.chunk_seg[c];
         const SegPlan P = w.plans[s];
@@ -636,8 +681,8 @@ __global__ void __launch_bounds__(kScatterThreads, SSS_SCATTER_MIN_BLOCKS) k_sca
         const int k = (int)P.k;
         const uint32_t v = (1u << k) - 1u, nb = 2u * v + 1u;
         for (uint32_t i = threadIdx.x; i < v; i += blockDim.x) {
-            sm.t[i + 1] = w.tree_lvl[P.tree_base + i];
-            sm.ino[i] = w.tree_ino[P.tree_base + i];
+            sm.t[i + 1] = tree_lvl[P.tree_base + i];
+            sm.ino[i] = tree_ino[P.tree_base + i];
         }
         __syncthreads();
         const uint32_t* S = w.counts_scan + P.count_base;
@@ -677,29 +722,30 @@ __global__ void __launch_bounds__(kScatterThreads, SSS_SCATTER_MIN_BLOCKS) k_sca
         const uint32_t lo = P.begin + ci * P.chunk;
         const uint32_t hi = min(lo + P.chunk, seg_end);
         const float* C = nullptr;
-        const bool model = p.learned && P.size >= kLearnedMinSize;
+        const bool model = KeyTraits<KT>::kBytes == 8 && p.learned && P.size >= kLearnedMinSize;
         if (model) {
             const float* tab = w.cdf_tab + (size_t)s * (p.cdf_M + 1);
             for (uint32_t j = threadIdx.x; j <= p.cdf_M; j += blockDim.x) sm.C[j] = tab[j];
             __syncthreads();
             C = sm.C;
         }
-        const uint32_t nref = scatter_range<kNBMax, false>(w, cur, lo, hi, nb, sm.ss, sm.t, sm.ino, k, nullptr, seg_end,
+        const uint32_t nref = scatter_range<kNBMax, false, KT>(w, cur, lo, hi, nb, sm.ss, sm.t, sm.ino, k, nullptr, seg_end,
                                                            P.depth, C, p.cdf_M, model ? w.cdf_kmin[s] : 0ull,
                                                            model ? w.cdf_scale[s] : 0.0f);
-        add_refills(w, nref);
+        add_refills(&w.hdr->refills, nref);
         __syncthreads();
     }
 }
 
 // ------------------------------------------------------------ medium round
 
+template <class KT>
 struct MedSmem {
-    uint64_t samp[1 << (kMedKMax + 1)];
-    uint64_t lvl[1 << kMedKMax];
+    KT samp[1 << (kMedKMax + 1)];
+    KT lvl[1 << kMedKMax];
     int32_t ra[1 << kMedKMax], rb[1 << kMedKMax];
-    uint64_t t[1 << kMedKMax];
-    uint64_t ino[1 << kMedKMax];
+    KT t[1 << kMedKMax];
+    KT ino[1 << kMedKMax];
     uint16_t bid[kMedMax];
     uint32_t hist[kMedNB + 1];
     uint32_t wsum[33];
@@ -709,14 +755,15 @@ struct MedSmem {
 // One CTA runs one whole distribution round for one medium segment (the
 // sequential S^5 of the paper, here on one SM): sample, tree, classify into a
 // shared bucket array, local prefix sum, stable move, child segments.
+template <class KT>
 __global__ void __launch_bounds__(kScatterThreads, SSS_SCATTER_MIN_BLOCKS) k_med_round(Work w, Params p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    MedSmem& sm = *reinterpret_cast<MedSmem*>(smem_raw);
+    MedSmem<KT>& sm = *reinterpret_cast<MedSmem<KT>*>(smem_raw);
     const int cur = w.hdr->round & 1u;
     const int med_in = cur, med_out = cur ^ 1;
     const uint32_t n_med = w.hdr->n_med_snap;
     __shared__ uint32_t s_item;
-    for (uint32_t mi = next_item(&w.hdr->q_med, &s_item); mi < n_med; mi = next_item(&w.hdr->q_med, &s_item)) {
+    for (uint32_t mi = first_item(); mi < n_med; mi = next_item(&w.hdr->q_med, &s_item)) {
         const Seg g = w.med[med_in][mi];
         const uint32_t m = g.size;
         const int k = choose_k(m, min(p.k_max, kMedKMax));
@@ -724,13 +771,14 @@ __global__ void __launch_bounds__(kScatterThreads, SSS_SCATTER_MIN_BLOCKS) k_med
         const uint32_t pw = 2u << k, cnt = pw - 1u;
         const Rec* recs = w.rec[cur];
         for (uint32_t j = threadIdx.x; j < pw; j += blockDim.x)
-            sm.samp[j] = j < cnt ? recs[g.begin + sample_pos(p.seed, g.begin, m, j)].key : ~0ull;
+            sm.samp[j] = j < cnt ? KeyTraits<KT>::load(recs + g.begin + sample_pos(p.seed, g.begin, m, j))
+                                 : KeyTraits<KT>::top();
         for (uint32_t b = threadIdx.x; b <= nb; b += blockDim.x) {
             sm.hist[b] = 0;
             for (int q = 0; q < kScatterWarps; q++) sm.ss.whist[q][b] = 0;
         }
         __syncthreads();
-        bitonic_sort_u64(sm.samp, pw);
+        bitonic_sort(sm.samp, pw);
         select_splitters(sm.samp, cnt, k, sm.lvl, sm.ra, sm.rb);
         emit_tree(sm.lvl, k, sm.t + 1, sm.ino);
         classify_range(recs, g.begin, g.begin + m, sm.t, sm.ino, k, nb, sm.hist, sm.bid);
@@ -762,9 +810,9 @@ __global__ void __launch_bounds__(kScatterThreads, SSS_SCATTER_MIN_BLOCKS) k_med
         }
         __syncthreads();
         const uint32_t nref =
-            scatter_range<kMedNB, true>(w, cur, g.begin, g.begin + m, nb, sm.ss, sm.t, sm.ino, k, sm.bid, g.begin + m,
+            scatter_range<kMedNB, true, KT>(w, cur, g.begin, g.begin + m, nb, sm.ss, sm.t, sm.ino, k, sm.bid, g.begin + m,
                                         g.depth);
-        add_refills(w, nref);
+        add_refills(&w.hdr->med_refills, nref);
         __syncthreads();
     }
 }
@@ -785,26 +833,29 @@ struct BaseSmem {
     uint32_t sbegin[kBaseMax + 2];    // its first position in the working arrays
     uint16_t R[kBaseCap];             // first slot of the run a slot belongs to
     uint32_t wmax[kBaseThreads / 32];
-    uint32_t lohi[2];
 };
 
-// First index i in [0, n) with a[i] >= x (n if none), a ascending; the warp
-// probes 32 positions per step.
-__device__ __forceinline__ uint32_t warp_lower_bound(const uint32_t* __restrict__ a, uint32_t n, uint32_t x) {
-    const uint32_t lane = threadIdx.x & 31u;
-    uint32_t lo = 0, hi = n;  // answer in [lo, hi]
-    while (hi - lo > 32u) {
-        const uint32_t p = lo + (uint32_t)(((uint64_t)(hi - lo) * (lane + 1u)) / 33u);
-        const uint32_t below = __ballot_sync(FULL_MASK, a[p] < x);
-        const uint32_t c = __popc(below);  // probes are increasing, so `below` is a prefix
-        const uint32_t plo = __shfl_sync(FULL_MASK, p, c ? c - 1u : 0u);
-        const uint32_t phi = __shfl_sync(FULL_MASK, p, c < 32u ? c : 31u);
-        if (c) lo = plo + 1u;
-        if (c < 32u) hi = phi;
+// tile_first[t]: the first small segment whose packed start lies at or after
+// t * T (segments are at most T strings, so every tile but an empty tail
+// holds the start of one).
+__global__ void k_tile_map(Work w, Params p) {
+    const uint32_t ns = w.hdr->n_small_snap, total = w.hdr->small_elems_snap;
+    const uint32_t T = p.base_threshold;
+    const uint32_t tiles = (total + T - 1) / T;
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < tiles; t += gridDim.x * blockDim.x) {
+        const uint32_t x = t * T;
+        uint32_t lo = 0, hi = ns;
+        while (lo < hi) {
+            const uint32_t m = (lo + hi) >> 1;
+            if (w.small_off[m] < x) lo = m + 1; else hi = m;
+        }
+        w.tile_first[t] = lo;
     }
-    const bool below = lo + lane < hi && a[lo + lane] < x;
-    return lo + (uint32_t)__popc(__ballot_sync(FULL_MASK, below));
 }
+
+template <class KT> __device__ __forceinline__ KT base_key(uint64_t a, uint64_t b);
+template <> __device__ __forceinline__ uint64_t base_key<uint64_t>(uint64_t a, uint64_t) { return a; }
+template <> __device__ __forceinline__ Key16 base_key<Key16>(uint64_t a, uint64_t b) { return Key16{a, b}; }
 
 // One CTA per tile of packed small segments: the segments whose packed start
 // lies in [t*T, (t+1)*T) (T = base_threshold <= kBaseMax), at most 2T - 1 <=
@@ -814,9 +865,12 @@ __device__ __forceinline__ uint32_t warp_lower_bound(const uint32_t* __restrict_
 // elements by (key word, slot) and moves it there (a stable sort of the
 // run); then a key change between neighbours fixes their LCP, equal key
 // words holding the terminator are equal strings, and groups of equal key
-// words without it become runs 8 bytes deeper (new words gathered) for the
-// next pass.
+// words without it become runs w bytes deeper (new words gathered) for the
+// next pass.  KT: the key of a pass, one word (w = 8) or both cached words
+// (w = 16).
+template <class KT>
 __global__ void __launch_bounds__(kBaseThreads) k_base(Work w, Params p) {
+    constexpr bool kWide = KeyTraits<KT>::kBytes == 16;
     __shared__ BaseSmem sm;
     const uint32_t s = threadIdx.x;
     const uint32_t lane = s & 31u, warp = s >> 5;
@@ -825,20 +879,9 @@ __global__ void __launch_bounds__(kBaseThreads) k_base(Work w, Params p) {
     const uint32_t T = p.base_threshold;
     const uint32_t tiles = (total + T - 1) / T;
     __shared__ uint32_t s_item;
-    for (uint32_t tile = next_item(&w.hdr->q_base, &s_item); tile < tiles; tile = next_item(&w.hdr->q_base, &s_item)) {
-    const uint32_t t0 = tile * T;
-    const uint32_t t1 = min(t0 + T, total);
-    if (warp == 0) {
-        const uint32_t lo = warp_lower_bound(w.small_off, ns, t0);
-        const uint32_t hi = warp_lower_bound(w.small_off, ns, t1);
-        if (lane == 0) { sm.lohi[0] = lo; sm.lohi[1] = hi; }
-    }
-    __syncthreads();
-    const uint32_t lo = sm.lohi[0], hi = sm.lohi[1];
-    if (lo >= hi) {
-        __syncthreads();  // lohi is rewritten by the next tile
-        continue;
-    }
+    for (uint32_t tile = first_item(); tile < tiles; tile = next_item(&w.hdr->q_base, &s_item)) {
+    const uint32_t lo = w.tile_first[tile], hi = tile + 1 < tiles ? w.tile_first[tile + 1] : ns;
+    if (lo >= hi) continue;  // an empty tail tile
     const uint32_t slot0 = w.small_off[lo];
     const uint32_t cnt = (hi < ns ? w.small_off[hi] : total) - slot0;
     const uint32_t nseg = hi - lo;
@@ -866,6 +909,7 @@ __global__ void __launch_bounds__(kBaseThreads) k_base(Work w, Params p) {
         id = r.idx;
         o = r.off;
         sm.K[s] = k;
+        if (kWide) sm.K2[s] = k2;
     }
     __syncthreads();
     uint32_t iter = 0;
@@ -880,16 +924,29 @@ __global__ void __launch_bounds__(kBaseThreads) k_base(Work w, Params p) {
             const uint32_t r = sm.R[s];
             const uint32_t e = r + sm.RL[r];
             uint32_t rank = 0, q = r;
-            for (; q + 4 <= e; q += 4) {
-                const uint64_t k0 = sm.K[q], k1 = sm.K[q + 1], k2 = sm.K[q + 2], k3 = sm.K[q + 3];
-                rank += (k0 < k || (k0 == k && q < s)) ? 1u : 0u;
-                rank += (k1 < k || (k1 == k && q + 1 < s)) ? 1u : 0u;
-                rank += (k2 < k || (k2 == k && q + 2 < s)) ? 1u : 0u;
-                rank += (k3 < k || (k3 == k && q + 3 < s)) ? 1u : 0u;
-            }
-            for (; q < e; q++) {
-                const uint64_t kq = sm.K[q];
-                rank += (kq < k || (kq == k && q < s)) ? 1u : 0u;
+            if constexpr (kWide) {
+                // (word, second word, slot) order
+                for (; q + 2 <= e; q += 2) {
+                    const uint64_t a0 = sm.K[q], a1 = sm.K[q + 1], b0 = sm.K2[q], b1 = sm.K2[q + 1];
+                    rank += (a0 < k || (a0 == k && (b0 < k2 || (b0 == k2 && q < s)))) ? 1u : 0u;
+                    rank += (a1 < k || (a1 == k && (b1 < k2 || (b1 == k2 && q + 1 < s)))) ? 1u : 0u;
+                }
+                for (; q < e; q++) {
+                    const uint64_t a = sm.K[q], b = sm.K2[q];
+                    rank += (a < k || (a == k && (b < k2 || (b == k2 && q < s)))) ? 1u : 0u;
+                }
+            } else {
+                for (; q + 4 <= e; q += 4) {
+                    const uint64_t k0 = sm.K[q], k1 = sm.K[q + 1], k2 = sm.K[q + 2], k3 = sm.K[q + 3];
+                    rank += (k0 < k || (k0 == k && q < s)) ? 1u : 0u;
+                    rank += (k1 < k || (k1 == k && q + 1 < s)) ? 1u : 0u;
+                    rank += (k2 < k || (k2 == k && q + 2 < s)) ? 1u : 0u;
+                    rank += (k3 < k || (k3 == k && q + 3 < s)) ? 1u : 0u;
+                }
+                for (; q < e; q++) {
+                    const uint64_t kq = sm.K[q];
+                    rank += (kq < k || (kq == k && q < s)) ? 1u : 0u;
+                }
             }
             np = r + rank;
         }
@@ -912,12 +969,13 @@ __global__ void __launch_bounds__(kBaseThreads) k_base(Work w, Params p) {
             const uint32_t r = sm.R[s];
             dold = sm.drun[r];
             if (s != r) {
-                const uint64_t pk = sm.K[s - 1];
-                if (pk != k) {
-                    w.out_lcp[G] = dold + key_lcp(pk, k);
+                const KT pk = base_key<KT>(sm.K[s - 1], sm.K2[s - 1]);
+                const KT ck = base_key<KT>(k, k2);
+                if (!keq(pk, ck)) {
+                    w.out_lcp[G] = dold + klcp(pk, ck);
                 } else {
                     head = false;
-                    if (key_ends(k)) w.out_lcp[G] = dold + key_chars(k);
+                    if (kends(ck)) w.out_lcp[G] = dold + kchars(ck);
                 }
             }
         }
@@ -935,17 +993,18 @@ __global__ void __launch_bounds__(kBaseThreads) k_base(Work w, Params p) {
         sm.SR[s] = sr;
         __syncthreads();
         const bool multi = (s != sr) || (s + 1 < cnt && sm.SR[s + 1] == s);
-        const bool go = act && multi && !key_ends(k);
+        const bool go = act && multi && !kends(base_key<KT>(k, k2));
         if (act) {
             if (go) {
-                const uint32_t d = dold + 8u;
+                const uint32_t d = dold + KeyTraits<KT>::kBytes;
                 if (s == sr) {
                     sm.drun[s] = d;
                     sm.RL[s] = 0;
                 }
                 sm.R[s] = (uint16_t)sr;
-                refill(w.chars, k, k2, o, d, 8u);
+                refill(w.chars, k, k2, o, d, KeyTraits<KT>::kBytes);
                 sm.K[s] = k;
+                if (kWide) sm.K2[s] = k2;
             } else {
                 sm.R[s] = (uint16_t)s;
             }
@@ -966,7 +1025,7 @@ __global__ void k_bigrun(Work w) {
     const int buf = w.hdr->round & 1u;
     const uint32_t nrun = w.hdr->n_bigrun_snap;
     __shared__ uint32_t s_item;
-    for (uint32_t r = next_item(&w.hdr->q_bigrun, &s_item); r < nrun; r = next_item(&w.hdr->q_bigrun, &s_item)) {
+    for (uint32_t r = first_item(); r < nrun; r = next_item(&w.hdr->q_bigrun, &s_item)) {
         const Seg g = w.bigrun[r];
         for (uint32_t i = threadIdx.x; i < g.size; i += blockDim.x) {
             const uint32_t q = g.begin + i;
@@ -991,10 +1050,13 @@ __global__ void k_fixup(Work w) {
                 atomicOr(&w.hdr->err, kErrPosition);
                 continue;
             }
-            const uint64_t a = load_key(w.chars, w.offsets[pa] + l);
-            const uint64_t b = load_key(w.chars, w.offsets[pb] + l);
-            if (a == b) atomicOr(&w.hdr->err, kErrEqualBoundary);
-            w.out_lcp[q] = l + (a == b ? 8u : key_lcp(a, b));
+            // the two strings share l characters and differ within the next
+            // w <= 16 (the key that put them in different buckets)
+            Key16 a, b;
+            load_key2(w.chars, w.offsets[pa] + l, a.h, a.l);
+            load_key2(w.chars, w.offsets[pb] + l, b.h, b.l);
+            if (keq(a, b)) atomicOr(&w.hdr->err, kErrEqualBoundary);
+            w.out_lcp[q] = l + klcp(a, b);
         }
     }
 }
@@ -1142,13 +1204,14 @@ static uint32_t grid_of(uint32_t fixed, const Hdr* hc, uint32_t known) { return 
 
 __global__ void k_advance(Work w) { w.hdr->round += 1u; }
 
-cudaError_t launch_round(const Work& w, const Params& p, const Hdr* hc, Prof* pf, cudaStream_t st) {
+template <class KT>
+static cudaError_t launch_round_t(const Work& w, const Params& p, const Hdr* hc, Prof* pf, cudaStream_t st) {
     const uint32_t sms = p.num_sms;
     const uint32_t gL = grid_of(sms * 2u, hc, hc ? hc->L : 0u);
     if (gL) {
         {
             ProfScope ps(pf, kSample, st);
-            k_sample<<<gL, 1024, 0, st>>>(w, p);
+            k_sample<KT><<<gL, 1024, sizeof(SampleSmem<KT>), st>>>(w, p);
         }
         if (p.learned) {
             cudaError_t e = launch_cdf_fit(w, p, grid_of(sms, hc, hc ? hc->L : 0u), pf, st);
@@ -1157,23 +1220,27 @@ cudaError_t launch_round(const Work& w, const Params& p, const Hdr* hc, Prof* pf
         const uint32_t gc = grid_of(sms * 4u, hc, hc ? hc->total_chunks : 0u);
         {
             ProfScope ps(pf, kClassify, st);
-            k_classify<<<gc, kClassifyThreads, 0, st>>>(w, p);
+            k_classify<KT><<<gc, kClassifyThreads, 0, st>>>(w, p);
         }
         cudaError_t e = launch_scan_u32(w.counts, w.counts_scan, &w.hdr->total_counts, hc ? &hc->total_counts : nullptr,
                                         w.scan_tmp, pf, st);
         if (e != cudaSuccess) return e;
         {
             ProfScope ps(pf, kScatter, st);
-            k_scatter<<<grid_of(sms * 2u, hc, hc ? hc->total_chunks : 0u), kScatterThreads, sizeof(ScatterSmem),
-                        st>>>(w, p);
+            k_scatter<KT><<<grid_of(sms * 2u, hc, hc ? hc->total_chunks : 0u), kScatterThreads,
+                            sizeof(ScatterSmem<KT>), st>>>(w, p);
         }
     }
     const uint32_t gm = grid_of(sms * 2u, hc, hc ? hc->n_med_snap : 0u);
     if (gm) {
         ProfScope ps(pf, kMedium, st);
-        k_med_round<<<gm, kScatterThreads, sizeof(MedSmem), st>>>(w, p);
+        k_med_round<KT><<<gm, kScatterThreads, sizeof(MedSmem<KT>), st>>>(w, p);
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_round(const Work& w, const Params& p, const Hdr* hc, Prof* pf, cudaStream_t st) {
+    return p.key_bytes == 16 ? launch_round_t<Key16>(w, p, hc, pf, st) : launch_round_t<uint64_t>(w, p, hc, pf, st);
 }
 
 // Loop condition of the graph form: another round is needed while the last
@@ -1189,10 +1256,20 @@ cudaError_t launch_set_cond(const Work& w, cudaGraphConditionalHandle cond, cuda
 
 // Shared-memory limits of the kernels that need more than 48 KB (set once,
 // outside any stream capture).
+template <class KT>
+static cudaError_t prepare_kernels_t() {
+    const auto set = [](const void* f, size_t bytes) {
+        return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    };
+    cudaError_t e = set((const void*)k_scatter<KT>, sizeof(ScatterSmem<KT>));
+    if (e == cudaSuccess) e = set((const void*)k_med_round<KT>, sizeof(MedSmem<KT>));
+    if (e == cudaSuccess) e = set((const void*)k_sample<KT>, sizeof(SampleSmem<KT>));
+    return e;
+}
+
 cudaError_t prepare_kernels(uint32_t cdf_M) {
-    cudaError_t e = cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ScatterSmem));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_med_round, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MedSmem));
+    cudaError_t e = prepare_kernels_t<uint64_t>();
+    if (e == cudaSuccess) e = prepare_kernels_t<Key16>();
     if (e == cudaSuccess) e = prepare_cdf_kernels(cdf_M);
     return e;
 }
@@ -1211,8 +1288,13 @@ cudaError_t launch_small(const Work& w, const Params& p, const Hdr* hc, uint32_t
         cudaError_t e = launch_scan_u32(w.small_size, w.small_off, &w.hdr->n_small_snap,
                                         hc ? &hc->n_small_snap : nullptr, w.scan_tmp, pf, st);
         if (e != cudaSuccess) return e;
+        {
+            ProfScope ps(pf, kBase, st);
+            k_tile_map<<<hc ? grid_for(tiles, 256, 4, sms) : sms, 256, 0, st>>>(w, p);
+        }
         ProfScope ps(pf, kBase, st);
-        k_base<<<grid_of(sms * 8u, hc, tiles), kBaseThreads, 0, st>>>(w, p);
+        if (p.key_bytes == 16) k_base<Key16><<<grid_of(sms * 8u, hc, tiles), kBaseThreads, 0, st>>>(w, p);
+        else k_base<uint64_t><<<grid_of(sms * 8u, hc, tiles), kBaseThreads, 0, st>>>(w, p);
     }
     const uint32_t gr = grid_of(sms * 4u, hc, hc ? hc->n_bigrun_snap : 0u);
     if (gr) {

@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(kFitThreads) k_cdf_fit(Work w, Params p) {
     const uint32_t M = p.cdf_M;
     const uint32_t L = w.hdr->L;
     __shared__ uint32_t s_item;
-    for (uint32_t seg = next_item(&w.hdr->q_fit, &s_item); seg < L; seg = next_item(&w.hdr->q_fit, &s_item)) {
+    for (uint32_t seg = first_item(); seg < L; seg = next_item(&w.hdr->q_fit, &s_item)) {
     const SegPlan P = w.plans[seg];
     if (P.size < kLearnedMinSize) continue;
     const uint32_t S = (2u << P.k) - 1u;

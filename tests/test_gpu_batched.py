@@ -83,11 +83,12 @@ def test_autotune_picks_valid_options_and_caches_them(tmp_path):
     assert len(lines) == 1 and lines[0]["k_max"] == best.k_max and lines[0]["ms"] == pytest.approx(ms, rel=1e-3)
     # the tuned options are current; a second call is answered from the cache
     cur = sss.sss_get_options()
-    assert (cur.k_max, cur.base_threshold, cur.medium_threshold, cur.chunk) == \
-        (best.k_max, best.base_threshold, best.medium_threshold, best.chunk)
+    assert (cur.k_max, cur.base_threshold, cur.medium_threshold, cur.chunk, cur.key_bytes) == \
+        (best.k_max, best.base_threshold, best.medium_threshold, best.chunk, best.key_bytes)
     best2, ms2 = sss.sss_autotune_batched(chars, offsets, tune.strings.n, tune.set_begin, 300, perm, lcp,
                                           str(cache))
-    assert (best2.k_max, best2.chunk) == (best.k_max, best.chunk) and ms2 == pytest.approx(ms, rel=1e-3)
+    assert (best2.k_max, best2.chunk, best2.key_bytes) == (best.k_max, best.chunk, best.key_bytes)
+    assert ms2 == pytest.approx(ms, rel=1e-3) and best.key_bytes in (8, 16)
     assert len(cache.read_text().splitlines()) == 1
     # the tuned options sort another batch of the same shape exactly
     real = gen.generate_batch(300, 100, 4000, 32)

@@ -137,8 +137,10 @@ def test_uniform_100k_full_workload():
     assert_same(s, perm, lcp)
 
 
+@pytest.mark.parametrize("key_bytes", [8, 16])
 @pytest.mark.parametrize("kind,n,seed", [(2, 300_000, 12), (3, 200_000, 13), (1, 50_000, 14)])
-def test_generated_kinds(kind, n, seed):
+def test_generated_kinds(kind, n, seed, key_bytes):
+    sss.sss_set_options(key_bytes=key_bytes)
     s = gen.generate(kind, n, seed)
     perm, lcp = gpu_sort(s)
     assert_same(s, perm, lcp)
@@ -147,13 +149,17 @@ def test_generated_kinds(kind, n, seed):
 # options that push small inputs through many distribution rounds, tiny
 # trees and one-tile chunks
 SMALL_OPTS = [
-    # every bucket above 16 strings through device-wide rounds, tiny trees
-    dict(base_threshold=16, medium_threshold=16, k_max=2, chunk=2048),
+    # every bucket above 16 strings through device-wide rounds, tiny trees,
+    # one-word keys
+    dict(base_threshold=16, medium_threshold=16, k_max=2, chunk=2048, key_bytes=8),
     # small base case, everything else per-CTA rounds
-    dict(base_threshold=16, medium_threshold=8192, k_max=10, chunk=2048),
-    dict(base_threshold=100, medium_threshold=300, k_max=5, chunk=4096),
+    dict(base_threshold=16, medium_threshold=8192, k_max=10, chunk=2048, key_bytes=16),
+    dict(base_threshold=100, medium_threshold=300, k_max=5, chunk=4096, key_bytes=8),
     # defaults
-    dict(base_threshold=128, medium_threshold=8192, k_max=10, chunk=32768),
+    dict(base_threshold=128, medium_threshold=8192, k_max=10, chunk=32768, key_bytes=16),
+    # as above with two-word keys and one-word keys
+    dict(base_threshold=16, medium_threshold=16, k_max=2, chunk=2048, key_bytes=16),
+    dict(base_threshold=16, medium_threshold=8192, k_max=10, chunk=2048, key_bytes=8),
 ]
 
 
@@ -189,7 +195,7 @@ EDGE_CASES = {
 
 
 @pytest.mark.parametrize("name", sorted(EDGE_CASES))
-@pytest.mark.parametrize("opts", [SMALL_OPTS[0], SMALL_OPTS[1], SMALL_OPTS[3]])
+@pytest.mark.parametrize("opts", [SMALL_OPTS[0], SMALL_OPTS[1], SMALL_OPTS[3], SMALL_OPTS[4], SMALL_OPTS[5]])
 def test_edge_cases(name, opts):
     sss.sss_set_options(**opts)
     items = list(EDGE_CASES[name])
@@ -273,10 +279,12 @@ def test_stats_report_rounds():
 
 # ------------------------------------------------------------------ full sizes
 
+@pytest.mark.parametrize("key_bytes", [8, 16])
 @pytest.mark.parametrize("name", ["url-16m", "dna-20m"])
-def test_full_size_workloads_verified(name):
+def test_full_size_workloads_verified(name, key_bytes):
     # the unique answer: permutation, strict (string, index) order of every
     # adjacent pair and every LCP entry, checked by the oracle one by one
+    sss.sss_set_options(key_bytes=key_bytes)
     s = gen.workload(name)
     perm, lcp = gpu_sort(s)
     code, bad = oracle.verify(s.chars, s.offsets, perm, lcp)
