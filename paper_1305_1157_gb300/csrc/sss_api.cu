@@ -1,11 +1,12 @@
 // Host driver and C ABI of the GB300 S^5 library (declared in include/sss.h).
 //
 // The round loop: every distribution round runs over all large segments at
-// once (k_sample, k_classify, scan, k_scatter, k_plan), then the host reads
-// back a 64-byte header holding the next round's sizes and launches the base
-// case for the buckets that became small.  The loop ends when no large
-// segment is left; a final pass resolves the LCP entries at bucket
-// boundaries.
+// once (k_sample, k_classify, scan, k_scatter), beside the per-CTA rounds of
+// the medium segments and the base case of the buckets that became small in
+// the previous round; then k_plan lays out the next round and the host reads
+// back the header holding its sizes.  The loop ends when no large or medium
+// segment is left; the base case of the last round's small buckets and a
+// pass that resolves the LCP entries at bucket boundaries finish the sort.
 #include <cuda_runtime.h>
 
 #include <cstdarg>
@@ -39,6 +40,8 @@ struct DevPool {
     size_t io_bytes = 0;
 };
 DevPool g_pool[kMaxDevices];
+Branches g_branches[kMaxDevices];  // concurrent round-body branches, created on first use
+
 
 int fail(int code, const char* fmt, ...) {
     va_list ap;
@@ -58,12 +61,40 @@ int cuda_fail(cudaError_t e, const char* where) {
         if (e_ != cudaSuccess) return cuda_fail(e_, where); \
     } while (0)
 
+// The branch streams and events of the current device (created once).
+int get_branches(const Branches** out) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return fail(SSS_ERR_INVALID, "device %d out of range", dev);
+    Branches& b = g_branches[dev];
+    if (!b.base) {
+        Branches n;
+        cudaError_t e = cudaStreamCreateWithFlags(&n.base, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&n.medium, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&n.fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&n.join_base, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&n.join_medium, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            if (n.base) cudaStreamDestroy(n.base);
+            if (n.medium) cudaStreamDestroy(n.medium);
+            if (n.fork) cudaEventDestroy(n.fork);
+            if (n.join_base) cudaEventDestroy(n.join_base);
+            if (n.join_medium) cudaEventDestroy(n.join_medium);
+            return cuda_fail(e, "branch streams");
+        }
+        b = n;
+    }
+    *out = &b;
+    return SSS_OK;
+}
+
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct Layout {
     size_t total = 0;
     size_t o_rec0, o_rec1, o_counts, o_counts_scan, o_tlvl, o_tino, o_plans, o_chunk_seg,
-        o_large, o_med0, o_med1, o_small, o_small_size, o_small_off, o_tile_first, o_bigrun, o_scan_tmp, o_hdr, o_roots,
+        o_large, o_med0, o_med1, o_small0, o_small1, o_small_size0, o_small_size1, o_small_off, o_tile_first,
+        o_bigrun0, o_bigrun1, o_scan_tmp, o_scan_tmp2, o_hdr, o_roots,
         o_cdf_samp, o_cdf_tab, o_cdf_kmin, o_cdf_scale;
     uint32_t cmax, tmax, lmax, chmax, smax, bmax, scan_tmp_max, mmax;
 };
@@ -121,12 +152,16 @@ Layout layout_for(uint32_t n, const sss_options& o, uint32_t num_roots, bool lea
     L.o_large = take(sizeof(Seg) * lmax);
     L.o_med0 = take(sizeof(Seg) * mmax);
     L.o_med1 = take(sizeof(Seg) * mmax);
-    L.o_small = take(sizeof(Seg) * smax);
-    L.o_small_size = take(4 * smax);
+    L.o_small0 = take(sizeof(Seg) * smax);
+    L.o_small1 = take(sizeof(Seg) * smax);
+    L.o_small_size0 = take(4 * smax);
+    L.o_small_size1 = take(4 * smax);
     L.o_small_off = take(4 * (smax + 1));
     L.o_tile_first = take(4 * (nn / T + 2));
-    L.o_bigrun = take(sizeof(Seg) * bmax);
+    L.o_bigrun0 = take(sizeof(Seg) * bmax);
+    L.o_bigrun1 = take(sizeof(Seg) * bmax);
     L.o_scan_tmp = take(4 * scan_tmp);
+    L.o_scan_tmp2 = take(4 * scan_tmp);
     L.o_hdr = take(sizeof(Hdr));
     L.o_roots = take(sizeof(Seg) * (num_roots ? num_roots : 1));
     L.o_cdf_samp = L.o_cdf_tab = L.o_cdf_kmin = L.o_cdf_scale = 0;
@@ -156,12 +191,16 @@ Work make_work(const Layout& L, char* ws, const uint8_t* chars, const uint64_t* 
     w.large = (Seg*)(ws + L.o_large);
     w.med[0] = (Seg*)(ws + L.o_med0);
     w.med[1] = (Seg*)(ws + L.o_med1);
-    w.small = (Seg*)(ws + L.o_small);
-    w.small_size = (uint32_t*)(ws + L.o_small_size);
+    w.small[0] = (Seg*)(ws + L.o_small0);
+    w.small[1] = (Seg*)(ws + L.o_small1);
+    w.small_size[0] = (uint32_t*)(ws + L.o_small_size0);
+    w.small_size[1] = (uint32_t*)(ws + L.o_small_size1);
     w.small_off = (uint32_t*)(ws + L.o_small_off);
     w.tile_first = (uint32_t*)(ws + L.o_tile_first);
-    w.bigrun = (Seg*)(ws + L.o_bigrun);
+    w.bigrun[0] = (Seg*)(ws + L.o_bigrun0);
+    w.bigrun[1] = (Seg*)(ws + L.o_bigrun1);
     w.scan_tmp = (uint32_t*)(ws + L.o_scan_tmp);
+    w.scan_tmp2 = (uint32_t*)(ws + L.o_scan_tmp2);
     w.hdr = (Hdr*)(ws + L.o_hdr);
     if (L.o_cdf_samp) {
         w.cdf_samp = (uint64_t*)(ws + L.o_cdf_samp);
@@ -217,9 +256,12 @@ int read_hdr(Hdr* hh, const Work& w, cudaStream_t st) {
 }
 
 // The whole sort on an initialised Work with the host driving the rounds
-// (see the file comment): one header readback per round.
+// (see the file comment): one header readback per round.  Each round body
+// runs the base case of the previous round's small children, the
+// device-wide round and the medium rounds as concurrent branches (br), or
+// one after the other on st (br null).
 int run_sort(const Work& w, const sss_options& o, const Seg* roots_dev, uint32_t num_roots, Hdr* hh,
-             cudaStream_t st, sss_stats* stats, bool learned = false) {
+             cudaStream_t st, sss_stats* stats, bool learned = false, bool concurrent = true) {
     Params p{learned ? 1 : 0, o.cdf_segments, o.cdf_steps, o.cdf_lr, o.k_max, o.base_threshold,
              o.medium_threshold, o.chunk, o.seed, device_sms(), learned ? 8u : o.key_bytes};
     Prof* pf = &g_prof;
@@ -229,14 +271,12 @@ int run_sort(const Work& w, const sss_options& o, const Seg* roots_dev, uint32_t
     CK(launch_init(w, pf, st), "init");
     CK(launch_roots(w, p, roots_dev, num_roots, pf, st), "roots");
     CK(launch_plan(w, p, pf, st), "plan");
-    int rc = read_hdr(hh, w, st);
+    const Branches* br = nullptr;
+    int rc = concurrent ? get_branches(&br) : SSS_OK;
     if (rc) return rc;
-    for (uint32_t round = 0;; round++) {
-        uint32_t tiles = 0;
-        CK(launch_small(w, p, hh, &tiles, pf, st), "base case");
-        stats->base_tiles += tiles;
-        stats->base_strings += hh->small_elems_snap;
-        if (hh->L == 0 && hh->n_med_snap == 0) break;
+    rc = read_hdr(hh, w, st);
+    if (rc) return rc;
+    for (uint32_t round = 0; hh->L > 0 || hh->n_med_snap > 0; round++) {
         if (round >= 1u << 22) return fail(SSS_ERR_INTERNAL, "round limit exceeded");
         if (round < SSS_MAX_ROUNDS_LOGGED) {
             stats->round_segments[round] = hh->L + hh->n_med_snap;
@@ -245,11 +285,20 @@ int run_sort(const Work& w, const sss_options& o, const Seg* roots_dev, uint32_t
         stats->rounds++;
         stats->round_strings += (uint64_t)hh->large_elems_snap + hh->med_elems_snap;
         stats->medium_strings += hh->med_elems_snap;
-        CK(launch_round(w, p, hh, pf, st), "round");
+        stats->base_strings += hh->small_elems_snap;
+        uint32_t tiles = 0;
+        CK(launch_body(w, p, hh, &tiles, pf, st, br), "round");
+        stats->base_tiles += tiles;
         CK(launch_plan(w, p, pf, st), "plan");
         CK(launch_advance(w, pf, st), "advance");
         rc = read_hdr(hh, w, st);
         if (rc) return rc;
+    }
+    {
+        uint32_t tiles = 0;
+        CK(launch_small(w, p, hh, &tiles, pf, st), "base case");
+        stats->base_tiles += tiles;
+        stats->base_strings += hh->small_elems_snap;
     }
     CK(launch_fixup(w, pf, st), "lcp fixup");
     if (roots_dev) CK(launch_localize(w.out_perm, roots_dev, num_roots, pf, st), "localize");
@@ -270,10 +319,12 @@ int run_sort(const Work& w, const sss_options& o, const Seg* roots_dev, uint32_t
 
 // ------------------------------------------------------------ graph form
 //
-// The same sort as one CUDA graph: prologue (init, roots, plan, base case),
-// a conditional WHILE node whose body is one round (round kernels, plan,
-// advance, base case) and whose last kernel decides on the device whether
-// another round is needed, then the epilogue (LCP fixup, index rebasing).
+// The same sort as one CUDA graph: prologue (init, roots, plan), a
+// conditional WHILE node whose body is one round (three concurrent branches:
+// base case of the previous round's small children, device-wide round,
+// medium rounds; then plan and advance) and whose last kernel decides on the
+// device whether another round is needed, then the epilogue (base case of
+// the last round's children, LCP fixup, index rebasing).
 // Kernels take their work counts from the device header, so one launch runs
 // the whole sort without host round-trips.  Instantiated graphs are cached
 // per device and reused while the call's buffers and options are unchanged.
@@ -298,10 +349,26 @@ int build_graph(const Work& w, const Params& p, const Seg* roots_dev, uint32_t n
     // captured on streams of our own (the caller's may be the legacy default
     // stream, which cannot be captured); the graph is launched on the caller's
     cudaStream_t st = nullptr, body_st = nullptr;
+    Branches br;  // the body's concurrent branches (capture streams and fork/join events)
     CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "capture stream");
-    if (cudaStreamCreateWithFlags(&body_st, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaError_t se = cudaStreamCreateWithFlags(&body_st, cudaStreamNonBlocking);
+    if (se == cudaSuccess) se = cudaStreamCreateWithFlags(&br.base, cudaStreamNonBlocking);
+    if (se == cudaSuccess) se = cudaStreamCreateWithFlags(&br.medium, cudaStreamNonBlocking);
+    if (se == cudaSuccess) se = cudaEventCreateWithFlags(&br.fork, cudaEventDisableTiming);
+    if (se == cudaSuccess) se = cudaEventCreateWithFlags(&br.join_base, cudaEventDisableTiming);
+    if (se == cudaSuccess) se = cudaEventCreateWithFlags(&br.join_medium, cudaEventDisableTiming);
+    auto free_branches = [&]() {
+        if (br.base) cudaStreamDestroy(br.base);
+        if (br.medium) cudaStreamDestroy(br.medium);
+        if (br.fork) cudaEventDestroy(br.fork);
+        if (br.join_base) cudaEventDestroy(br.join_base);
+        if (br.join_medium) cudaEventDestroy(br.join_medium);
+    };
+    if (se != cudaSuccess) {
+        free_branches();
+        if (body_st) cudaStreamDestroy(body_st);
         cudaStreamDestroy(st);
-        return cuda_fail(cudaGetLastError(), "stream for the round body");
+        return cuda_fail(se, "capture streams");
     }
     cudaGraph_t graph = nullptr;
     cudaError_t err = cudaSuccess;
@@ -312,6 +379,7 @@ int build_graph(const Work& w, const Params& p, const Seg* roots_dev, uint32_t n
             cudaStreamEndCapture(st, &g2);
             if (g2) cudaGraphDestroy(g2);
         }
+        free_branches();
         cudaStreamDestroy(body_st);
         cudaStreamDestroy(st);
         cudaGetLastError();
@@ -333,7 +401,6 @@ int build_graph(const Work& w, const Params& p, const Seg* roots_dev, uint32_t n
     if ((err = launch_init(w, &counter, st)) != cudaSuccess ||
         (err = launch_roots(w, p, roots_dev, num_roots, &counter, st)) != cudaSuccess ||
         (err = launch_plan(w, p, &counter, st)) != cudaSuccess ||
-        (err = launch_small(w, p, nullptr, nullptr, &counter, st)) != cudaSuccess ||
         (err = launch_set_cond(w, cond, st)) != cudaSuccess)
         return done(err, "graph prologue");
     gc.launches_prologue = counter.launches + 1;
@@ -356,10 +423,9 @@ int build_graph(const Work& w, const Params& p, const Seg* roots_dev, uint32_t n
         cudaSuccess)
         return done(err, "begin body capture");
     counter.reset(false);
-    if ((err = launch_round(w, p, nullptr, &counter, body_st)) != cudaSuccess ||
+    if ((err = launch_body(w, p, nullptr, nullptr, &counter, body_st, &br)) != cudaSuccess ||
         (err = launch_plan(w, p, &counter, body_st)) != cudaSuccess ||
         (err = launch_advance(w, &counter, body_st)) != cudaSuccess ||
-        (err = launch_small(w, p, nullptr, nullptr, &counter, body_st)) != cudaSuccess ||
         (err = launch_set_cond(w, cond, body_st)) != cudaSuccess) {
         cudaGraph_t b2 = nullptr;
         cudaStreamEndCapture(body_st, &b2);
@@ -370,12 +436,14 @@ int build_graph(const Work& w, const Params& p, const Seg* roots_dev, uint32_t n
     if ((err = cudaStreamEndCapture(body_st, &body_out)) != cudaSuccess) return done(err, "end body capture");
     // epilogue
     counter.reset(false);
-    if ((err = launch_fixup(w, &counter, st)) != cudaSuccess ||
+    if ((err = launch_small(w, p, nullptr, nullptr, &counter, st)) != cudaSuccess ||
+        (err = launch_fixup(w, &counter, st)) != cudaSuccess ||
         (roots_dev && (err = launch_localize(w.out_perm, roots_dev, num_roots, &counter, st)) != cudaSuccess))
         return done(err, "graph epilogue");
     gc.launches_epilogue = counter.launches;
     cudaGraph_t full = nullptr;
     if ((err = cudaStreamEndCapture(st, &full)) != cudaSuccess) return done(err, "end capture");
+    free_branches();
     cudaStreamDestroy(body_st);
     cudaStreamDestroy(st);
     cudaGraphExec_t exec = nullptr;
@@ -625,6 +693,16 @@ int sss_release(void) {
             cudaGraphExecDestroy(g_graph[d].exec);
             g_graph[d] = GraphCache();
         }
+        Branches& b = g_branches[d];
+        if (b.base) {
+            cudaSetDevice(d);
+            cudaStreamDestroy(b.base);
+            cudaStreamDestroy(b.medium);
+            cudaEventDestroy(b.fork);
+            cudaEventDestroy(b.join_base);
+            cudaEventDestroy(b.join_medium);
+            b = Branches();
+        }
         if (!P.ws && !P.io && !P.hh) continue;
         cudaSetDevice(d);
         if (P.ws) cudaFree(P.ws);
@@ -834,7 +912,8 @@ extern "C" int sss_sort_noalloc(const uint8_t* chars, const uint64_t* offsets, u
     sss_options o = g_opt;
     o.profile = 0;  // no timing events
     sss_stats stats;
-    rc = run_sort(w, o, nullptr, 0, &g_noalloc_hdr[dev], (cudaStream_t)stream, &stats);
+    // serial round bodies: no library streams or events are created for it
+    rc = run_sort(w, o, nullptr, 0, &g_noalloc_hdr[dev], (cudaStream_t)stream, &stats, false, false);
     if (rc) return rc;
     g_stats = stats;
     return SSS_OK;

@@ -131,18 +131,22 @@ struct Work {
     Rec* rec[2];             // the string at each position (ping-pong per round)
     uint32_t* counts;        // [cmax] per (segment, bucket, chunk) counts
     uint32_t* counts_scan;   // [cmax] exclusive scan of counts
-    uint64_t* tree_lvl;      // [tmax]
-    uint64_t* tree_ino;      // [tmax]
+    uint64_t* tree_lvl;      // [2 * tmax] level-order trees (one or two words a node)
+    uint64_t* tree_ino;      // [2 * tmax] the same splitters in order
     SegPlan* plans;          // [lmax]
     uint32_t* chunk_seg;     // [chmax]
     Seg* large;              // [lmax] children for the next device-wide round
-    Seg* med[2];             // [mmax] children for the next per-CTA round (alternating)
-    Seg* small;              // [smax]
-    uint32_t* small_size;    // [smax]
-    uint32_t* small_off;     // [smax + 1]
+    // child lists by parity: a round with round counter r appends to parity
+    // (r + 1) & 1 while the base case of the children of round r - 1 reads
+    // parity r & 1 concurrently
+    Seg* med[2];             // [mmax] children for the next per-CTA round
+    Seg* small[2];           // [smax] children for the base case
+    uint32_t* small_size[2]; // [smax] their sizes
+    Seg* bigrun[2];          // [bmax] large runs of equal strings
+    uint32_t* small_off;     // [smax + 1] packed start of each small segment
     uint32_t* tile_first;    // [n / base_threshold + 2] first small segment packed into each base-case tile
-    Seg* bigrun;             // [bmax]
-    uint32_t* scan_tmp;      // [scan_tmp_max]
+    uint32_t* scan_tmp;      // [scan_tmp_max] scan scratch of the distribution rounds
+    uint32_t* scan_tmp2;     // [scan_tmp_max] scan scratch of the base case
     Hdr* hdr;
     // learned proposal (allocated for sss_sort_learned only)
     uint64_t* cdf_samp;      // [lmax * kSampleMax] sorted splitter sample of each segment
@@ -503,7 +507,20 @@ cudaError_t launch_plan(const Work& w, const Params& p, Prof* pf, cudaStream_t s
 // (hdr->round) from device memory.  hc: host copy of the header when known
 // (exact grids, empty launches skipped), nullptr for persistent grids (graph
 // capture).
-cudaError_t launch_round(const Work& w, const Params& p, const Hdr* hc, Prof* pf, cudaStream_t st);
+// Streams and events for running the base case, the device-wide round and
+// the medium round of one round body concurrently (forked from and joined
+// back into the caller's stream).
+struct Branches {
+    cudaStream_t base = nullptr, medium = nullptr;
+    cudaEvent_t fork = nullptr, join_base = nullptr, join_medium = nullptr;
+};
+
+// One round body: the base case of the last round's small children, the
+// device-wide round of the large segments and the per-CTA rounds of the
+// medium ones.  With br, the three run as concurrent branches of st; without,
+// one after the other on st.  *out_tiles: base-case tiles (host-driven only).
+cudaError_t launch_body(const Work& w, const Params& p, const Hdr* hc, uint32_t* out_tiles, Prof* pf,
+                        cudaStream_t st, const Branches* br);
 cudaError_t launch_set_cond(const Work& w, cudaGraphConditionalHandle cond, cudaStream_t st);
 cudaError_t prepare_kernels(uint32_t cdf_M);
 cudaError_t prepare_cdf_kernels(uint32_t M);

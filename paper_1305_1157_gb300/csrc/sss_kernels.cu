@@ -74,19 +74,19 @@ __device__ uint32_t block_excl_sum(uint32_t x, uint32_t* wsum, uint32_t* total) 
 
 // Where a bucket of `size` strings goes next (Sec. 3.1 "Parallelization of
 // S^5": size classes).  isrun: all its strings are equal (finished).
-__device__ __forceinline__ void append_child(const Work& w, const Params& p, int med_out, uint32_t start,
+__device__ __forceinline__ void append_child(const Work& w, const Params& p, int out, uint32_t start,
                                              uint32_t size, uint32_t cdepth, bool isrun, uint32_t runlcp) {
     Hdr* h = w.hdr;
     if (size <= 1) return;
     if (isrun && size > p.base_threshold) {
         uint32_t s = atomicAdd(&h->n_bigrun, 1u);
-        if (s < w.bmax) w.bigrun[s] = Seg{start, size, cdepth, runlcp};
+        if (s < w.bmax) w.bigrun[out][s] = Seg{start, size, cdepth, runlcp};
         else atomicOr(&h->err, kErrRunOverflow);
     } else if (size <= p.base_threshold) {
         uint32_t s = atomicAdd(&h->n_small, 1u);
         if (s < w.smax) {
-            w.small[s] = Seg{start, size, cdepth, 0u};
-            w.small_size[s] = size;
+            w.small[out][s] = Seg{start, size, cdepth, 0u};
+            w.small_size[out][s] = size;
             atomicAdd(&h->small_elems, size);
             atomicAdd(&h->small_hist[min(31 - __clz(size), 7)], 1u);
         } else {
@@ -95,7 +95,7 @@ __device__ __forceinline__ void append_child(const Work& w, const Params& p, int
     } else if (size <= p.med_threshold) {
         uint32_t s = atomicAdd(&h->n_med, 1u);
         if (s < w.mmax) {
-            w.med[med_out][s] = Seg{start, size, cdepth, 0u};
+            w.med[out][s] = Seg{start, size, cdepth, 0u};
             atomicAdd(&h->med_elems, size);
         } else {
             atomicOr(&h->err, kErrMedOverflow);
@@ -887,7 +887,7 @@ __global__ void __launch_bounds__(kBaseThreads) k_base(Work w, Params p) {
     const uint32_t nseg = hi - lo;
     for (uint32_t i = s; i < nseg; i += blockDim.x) {
         const uint32_t b = w.small_off[lo + i] - slot0;
-        const Seg g = w.small[lo + i];
+        const Seg g = w.small[buf][lo + i];
         sm.sbase[i] = b;
         sm.sbegin[i] = g.begin;
         sm.drun[b] = g.depth;
@@ -1026,7 +1026,7 @@ __global__ void k_bigrun(Work w) {
     const uint32_t nrun = w.hdr->n_bigrun_snap;
     __shared__ uint32_t s_item;
     for (uint32_t r = first_item(); r < nrun; r = next_item(&w.hdr->q_bigrun, &s_item)) {
-        const Seg g = w.bigrun[r];
+        const Seg g = w.bigrun[buf][r];
         for (uint32_t i = threadIdx.x; i < g.size; i += blockDim.x) {
             const uint32_t q = g.begin + i;
             w.out_perm[q] = w.rec[buf][q].idx;
@@ -1069,10 +1069,18 @@ constexpr uint32_t kScanTile = kScanThreads * kScanPer;
 
 size_t scan_tmp_elems(uint32_t n) { return (size_t)(n + kScanTile - 1) / kScanTile + 1; }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* in, const uint32_t* n_ptr,
-                                                              uint32_t* sums) {
+// Scan input: in[0], or in[*sel & 1] when sel is given (a list chosen by
+// round parity on the device).
+struct ScanIn {
+    const uint32_t* in[2];
+    const uint32_t* sel;
+    __device__ __forceinline__ const uint32_t* get() const { return sel ? in[*sel & 1u] : in[0]; }
+};
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(ScanIn src, const uint32_t* n_ptr, uint32_t* sums) {
     __shared__ uint32_t wsum[33];
     const uint32_t n = *n_ptr;
+    const uint32_t* in = src.get();
     const uint32_t tiles = (n + kScanTile - 1) / kScanTile;
     for (uint32_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
         const uint32_t base = tile * kScanTile;
@@ -1106,10 +1114,11 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(uint32_t* sums, const uint3
     if (threadIdx.x == 0) out[n] = tot;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* in, uint32_t* out, const uint32_t* n_ptr,
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(ScanIn src, uint32_t* out, const uint32_t* n_ptr,
                                                             const uint32_t* sums) {
     __shared__ uint32_t wsum[33];
     const uint32_t n = *n_ptr;
+    const uint32_t* in = src.get();
     const uint32_t tiles = (n + kScanTile - 1) / kScanTile;
     for (uint32_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
         const uint32_t base = tile * kScanTile + threadIdx.x * kScanPer;
@@ -1131,22 +1140,30 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* in, 
     }
 }
 
-// out[0..n) = exclusive prefix sums of in, out[n] = total, with n read from
-// device memory (*n_ptr); n_host (if known) only sizes the grid.  tmp holds
-// scan_tmp_elems(n) entries.
-cudaError_t launch_scan_u32(const uint32_t* in, uint32_t* out, const uint32_t* n_ptr, const uint32_t* n_host,
-                            uint32_t* tmp, Prof* pf, cudaStream_t st) {
+// out[0..n) = exclusive prefix sums of the input, out[n] = total, with n read
+// from device memory (*n_ptr); n_host (if known) only sizes the grid.  tmp
+// holds scan_tmp_elems(n) entries.  The input is in, or with sel given
+// in_alt when *sel is odd.
+static cudaError_t launch_scan_sel(const uint32_t* in, const uint32_t* in_alt, const uint32_t* sel, uint32_t* out,
+                                   const uint32_t* n_ptr, const uint32_t* n_host, uint32_t* tmp, Prof* pf,
+                                   cudaStream_t st) {
+    const ScanIn src{{in, in_alt}, sel};
     uint32_t grid = device_sms() * 8u;
     if (n_host) {
         const uint32_t tiles = (*n_host + kScanTile - 1) / kScanTile;
         grid = max(1u, min(grid, tiles));
     }
     ProfScope ps(pf, kScan, st);
-    k_scan_reduce<<<grid, kScanThreads, 0, st>>>(in, n_ptr, tmp);
+    k_scan_reduce<<<grid, kScanThreads, 0, st>>>(src, n_ptr, tmp);
     k_scan_tiles<<<1, 1024, 0, st>>>(tmp, n_ptr, out);
-    k_scan_down<<<grid, kScanThreads, 0, st>>>(in, out, n_ptr, tmp);
+    k_scan_down<<<grid, kScanThreads, 0, st>>>(src, out, n_ptr, tmp);
     if (pf) { pf->launches += 2; pf->cls_launches[kScan] += 2; }
     return cudaGetLastError();
+}
+
+cudaError_t launch_scan_u32(const uint32_t* in, uint32_t* out, const uint32_t* n_ptr, const uint32_t* n_host,
+                            uint32_t* tmp, Prof* pf, cudaStream_t st) {
+    return launch_scan_sel(in, in, nullptr, out, n_ptr, n_host, tmp, pf, st);
 }
 
 // ------------------------------------------------------------ launches
@@ -1231,7 +1248,12 @@ static cudaError_t launch_round_t(const Work& w, const Params& p, const Hdr* hc,
                             sizeof(ScatterSmem<KT>), st>>>(w, p);
         }
     }
-    const uint32_t gm = grid_of(sms * 2u, hc, hc ? hc->n_med_snap : 0u);
+    return cudaGetLastError();
+}
+
+template <class KT>
+static cudaError_t launch_medium_t(const Work& w, const Params& p, const Hdr* hc, Prof* pf, cudaStream_t st) {
+    const uint32_t gm = grid_of(p.num_sms * 2u, hc, hc ? hc->n_med_snap : 0u);
     if (gm) {
         ProfScope ps(pf, kMedium, st);
         k_med_round<KT><<<gm, kScatterThreads, sizeof(MedSmem<KT>), st>>>(w, p);
@@ -1239,8 +1261,30 @@ static cudaError_t launch_round_t(const Work& w, const Params& p, const Hdr* hc,
     return cudaGetLastError();
 }
 
-cudaError_t launch_round(const Work& w, const Params& p, const Hdr* hc, Prof* pf, cudaStream_t st) {
-    return p.key_bytes == 16 ? launch_round_t<Key16>(w, p, hc, pf, st) : launch_round_t<uint64_t>(w, p, hc, pf, st);
+cudaError_t launch_body(const Work& w, const Params& p, const Hdr* hc, uint32_t* out_tiles, Prof* pf,
+                        cudaStream_t st, const Branches* br) {
+    const bool wide = p.key_bytes == 16;
+    cudaStream_t sb = st, sm = st;
+    cudaError_t e = cudaSuccess;
+    if (br) {
+        sb = br->base;
+        sm = br->medium;
+        if ((e = cudaEventRecord(br->fork, st)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(sb, br->fork, 0)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(sm, br->fork, 0)) != cudaSuccess) return e;
+    }
+    if ((e = launch_small(w, p, hc, out_tiles, pf, sb)) != cudaSuccess) return e;
+    e = wide ? launch_medium_t<Key16>(w, p, hc, pf, sm) : launch_medium_t<uint64_t>(w, p, hc, pf, sm);
+    if (e != cudaSuccess) return e;
+    e = wide ? launch_round_t<Key16>(w, p, hc, pf, st) : launch_round_t<uint64_t>(w, p, hc, pf, st);
+    if (e != cudaSuccess) return e;
+    if (br) {
+        if ((e = cudaEventRecord(br->join_base, sb)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(br->join_medium, sm)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(st, br->join_base, 0)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(st, br->join_medium, 0)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 // Loop condition of the graph form: another round is needed while the last
@@ -1285,8 +1329,8 @@ cudaError_t launch_small(const Work& w, const Params& p, const Hdr* hc, uint32_t
     const uint32_t sms = p.num_sms;
     uint32_t tiles = hc ? (hc->small_elems_snap + p.base_threshold - 1) / p.base_threshold : 0u;
     if (!hc || hc->n_small_snap) {
-        cudaError_t e = launch_scan_u32(w.small_size, w.small_off, &w.hdr->n_small_snap,
-                                        hc ? &hc->n_small_snap : nullptr, w.scan_tmp, pf, st);
+        cudaError_t e = launch_scan_sel(w.small_size[0], w.small_size[1], &w.hdr->round, w.small_off,
+                                        &w.hdr->n_small_snap, hc ? &hc->n_small_snap : nullptr, w.scan_tmp2, pf, st);
         if (e != cudaSuccess) return e;
         {
             ProfScope ps(pf, kBase, st);
