@@ -256,6 +256,15 @@ int sss_cdf_loss_grad(const float* theta, uint32_t M, const float* u, const floa
 int sss_set_options(const sss_options* opt);   /* opt (host) */
 int sss_get_options(sss_options* opt);         /* opt (host) */
 int sss_get_last_stats(sss_stats* stats);      /* stats (host) */
+
+/* Launch timeline of the last host-driven call made with options.profile = 1
+ * (empty otherwise): for each timed launch i in launch order, its kernel class
+ * cls[i] (SSS_K_*) and its start and end in milliseconds from the first
+ * launch's start, measured with CUDA events on the stream it ran on (the
+ * concurrent branches of a round overlap).  Writes min(count, cap) entries
+ * (all arrays host, cap entries each; NULL allowed when cap = 0) and the
+ * total count to *out_count. */
+int sss_get_last_timeline(uint32_t cap, int32_t* cls, double* start_ms, double* end_ms, uint32_t* out_count);
 const char* sss_last_error(void);              /* static storage, never NULL */
 int sss_release(void);                         /* frees the workspace cache of every device */
 const char* sss_version(void);

@@ -21,7 +21,8 @@ from . import build as _build
 __all__ = [
     "SSSError", "sss_sort", "sss_sort_ws", "sss_sort_noalloc", "sss_sort_host", "sss_sort_batched", "sss_sort_learned",
     "sss_workspace_size", "sss_gather_keys", "sss_build_splitters", "sss_classify", "sss_cdf_loss_grad",
-    "sss_set_options", "sss_get_options", "sss_get_last_stats", "sss_last_error", "sss_release",
+    "sss_set_options", "sss_get_options", "sss_get_last_stats", "sss_get_last_timeline", "sss_last_error",
+    "sss_release",
     "sss_version", "sss_options", "sss_stats", "load", "lib_path", "sort", "sss_autotune_batched",
 ]
 
@@ -96,6 +97,7 @@ _SIG = {
     "sss_set_options": ([ctypes.POINTER(sss_options)], ctypes.c_int),
     "sss_get_options": ([ctypes.POINTER(sss_options)], ctypes.c_int),
     "sss_get_last_stats": ([ctypes.POINTER(sss_stats)], ctypes.c_int),
+    "sss_get_last_timeline": ([ctypes.c_uint32, _P, _P, _P, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
     "sss_last_error": ([], ctypes.c_char_p),
     "sss_release": ([], ctypes.c_int),
     "sss_version": ([], ctypes.c_char_p),
@@ -231,6 +233,19 @@ def sss_get_last_stats() -> sss_stats:
     s = sss_stats()
     _check(load().sss_get_last_stats(ctypes.byref(s)))
     return s
+
+
+def sss_get_last_timeline():
+    """[(class name, start ms, end ms)] of the last profiled host-driven call."""
+    lib = load()
+    cnt = ctypes.c_uint32(0)
+    _check(lib.sss_get_last_timeline(0, None, None, None, ctypes.byref(cnt)))
+    n = cnt.value
+    cls = (ctypes.c_int32 * max(n, 1))()
+    t0 = (ctypes.c_double * max(n, 1))()
+    t1 = (ctypes.c_double * max(n, 1))()
+    _check(lib.sss_get_last_timeline(n, cls, t0, t1, ctypes.byref(cnt)))
+    return [(K_CLASSES[cls[i]], t0[i], t1[i]) for i in range(min(n, cnt.value))]
 
 
 def sss_last_error() -> str:

@@ -28,6 +28,8 @@ std::mutex g_mu;
 sss_options g_opt = {10, 128u, 2048u, 32768u, 0x5eedull, 4096u, 16u, 0.05f, 0u, 0u, 16u};
 sss_stats g_stats;
 Prof g_prof;
+std::vector<int> g_tl_cls;       // timeline of the last profiled host-driven call
+std::vector<double> g_tl_start, g_tl_end;
 char g_err[512] = "no error";
 
 constexpr int kMaxDevices = 64;
@@ -67,23 +69,7 @@ int get_branches(const Branches** out) {
     CK(cudaGetDevice(&dev), "cudaGetDevice");
     if (dev < 0 || dev >= kMaxDevices) return fail(SSS_ERR_INVALID, "device %d out of range", dev);
     Branches& b = g_branches[dev];
-    if (!b.base) {
-        Branches n;
-        cudaError_t e = cudaStreamCreateWithFlags(&n.base, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&n.medium, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&n.fork, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&n.join_base, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&n.join_medium, cudaEventDisableTiming);
-        if (e != cudaSuccess) {
-            if (n.base) cudaStreamDestroy(n.base);
-            if (n.medium) cudaStreamDestroy(n.medium);
-            if (n.fork) cudaEventDestroy(n.fork);
-            if (n.join_base) cudaEventDestroy(n.join_base);
-            if (n.join_medium) cudaEventDestroy(n.join_medium);
-            return cuda_fail(e, "branch streams");
-        }
-        b = n;
-    }
+    if (!b.base) CK(branches_create(b), "branch streams");
     *out = &b;
     return SSS_OK;
 }
@@ -93,10 +79,10 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 struct Layout {
     size_t total = 0;
     size_t o_rec0, o_rec1, o_counts, o_counts_scan, o_tlvl, o_tino, o_plans, o_chunk_seg,
-        o_large, o_med0, o_med1, o_small0, o_small1, o_small_size0, o_small_size1, o_small_off, o_tile_first,
+        o_large, o_med0, o_med1, o_small0, o_small1, o_tiny0, o_tiny1, o_small_size0, o_small_size1, o_small_off, o_tile_first,
         o_bigrun0, o_bigrun1, o_scan_tmp, o_scan_tmp2, o_hdr, o_roots,
         o_cdf_samp, o_cdf_tab, o_cdf_kmin, o_cdf_scale;
-    uint32_t cmax, tmax, lmax, chmax, smax, bmax, scan_tmp_max, mmax;
+    uint32_t cmax, tmax, lmax, chmax, smax, ymax, bmax, scan_tmp_max, mmax;
 };
 
 uint32_t g_sms = 0;  // SM count of the first device used (sizes the count matrix)
@@ -133,11 +119,14 @@ Layout layout_for(uint32_t n, const sss_options& o, uint32_t num_roots, bool lea
     const uint64_t cmax = (uint64_t)kNBMax * chmax + 64;
     const uint64_t tmax = nn / 16 + 2 * lmax + 64;  // 2^k <= size / 16 per segment
     const uint64_t mmax = nn / (T + 1) + 2;
-    const uint64_t smax = nn / 2 + num_roots + 2;
+    // tile-form small buckets hold more than kTinyMax strings (when the
+    // threshold allows any), warp-form ones at least 2
+    const uint64_t smax = (T > kTinyMax ? nn / (kTinyMax + 1) : 0) + num_roots + 2;
+    const uint64_t ymax = nn / 2 + num_roots + 2;
     const uint64_t bmax = nn / (T + 1) + 2;
     const uint64_t scan_tmp = scan_tmp_elems((uint32_t)(cmax > smax ? cmax : smax)) + 1;
     L.cmax = (uint32_t)cmax; L.tmax = (uint32_t)tmax; L.lmax = (uint32_t)lmax; L.chmax = (uint32_t)chmax;
-    L.smax = (uint32_t)smax; L.bmax = (uint32_t)bmax; L.scan_tmp_max = (uint32_t)scan_tmp;
+    L.smax = (uint32_t)smax; L.ymax = (uint32_t)ymax; L.bmax = (uint32_t)bmax; L.scan_tmp_max = (uint32_t)scan_tmp;
     L.mmax = (uint32_t)mmax;
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t r = off; off = align_up(off + bytes, 256); return r; };
@@ -154,6 +143,8 @@ Layout layout_for(uint32_t n, const sss_options& o, uint32_t num_roots, bool lea
     L.o_med1 = take(sizeof(Seg) * mmax);
     L.o_small0 = take(sizeof(Seg) * smax);
     L.o_small1 = take(sizeof(Seg) * smax);
+    L.o_tiny0 = take(sizeof(Seg) * ymax);
+    L.o_tiny1 = take(sizeof(Seg) * ymax);
     L.o_small_size0 = take(4 * smax);
     L.o_small_size1 = take(4 * smax);
     L.o_small_off = take(4 * (smax + 1));
@@ -193,6 +184,8 @@ Work make_work(const Layout& L, char* ws, const uint8_t* chars, const uint64_t* 
     w.med[1] = (Seg*)(ws + L.o_med1);
     w.small[0] = (Seg*)(ws + L.o_small0);
     w.small[1] = (Seg*)(ws + L.o_small1);
+    w.tiny[0] = (Seg*)(ws + L.o_tiny0);
+    w.tiny[1] = (Seg*)(ws + L.o_tiny1);
     w.small_size[0] = (uint32_t*)(ws + L.o_small_size0);
     w.small_size[1] = (uint32_t*)(ws + L.o_small_size1);
     w.small_off = (uint32_t*)(ws + L.o_small_off);
@@ -209,7 +202,7 @@ Work make_work(const Layout& L, char* ws, const uint8_t* chars, const uint64_t* 
         w.cdf_scale = (float*)(ws + L.o_cdf_scale);
     }
     w.cmax = L.cmax; w.tmax = L.tmax; w.lmax = L.lmax; w.chmax = L.chmax;
-    w.smax = L.smax; w.bmax = L.bmax; w.scan_tmp_max = L.scan_tmp_max; w.mmax = L.mmax;
+    w.smax = L.smax; w.ymax = L.ymax; w.bmax = L.bmax; w.scan_tmp_max = L.scan_tmp_max; w.mmax = L.mmax;
     return w;
 }
 
@@ -285,7 +278,7 @@ int run_sort(const Work& w, const sss_options& o, const Seg* roots_dev, uint32_t
         stats->rounds++;
         stats->round_strings += (uint64_t)hh->large_elems_snap + hh->med_elems_snap;
         stats->medium_strings += hh->med_elems_snap;
-        stats->base_strings += hh->small_elems_snap;
+        stats->base_strings += (uint64_t)hh->small_elems_snap + hh->tiny_elems_snap;
         uint32_t tiles = 0;
         CK(launch_body(w, p, hh, &tiles, pf, st, br), "round");
         stats->base_tiles += tiles;
@@ -298,7 +291,7 @@ int run_sort(const Work& w, const sss_options& o, const Seg* roots_dev, uint32_t
         uint32_t tiles = 0;
         CK(launch_small(w, p, hh, &tiles, pf, st), "base case");
         stats->base_tiles += tiles;
-        stats->base_strings += hh->small_elems_snap;
+        stats->base_strings += (uint64_t)hh->small_elems_snap + hh->tiny_elems_snap;
     }
     CK(launch_fixup(w, pf, st), "lcp fixup");
     if (roots_dev) CK(launch_localize(w.out_perm, roots_dev, num_roots, pf, st), "localize");
@@ -314,6 +307,7 @@ int run_sort(const Work& w, const sss_options& o, const Seg* roots_dev, uint32_t
     stats->profiled = pf->enabled ? 1u : 0u;
     for (int i = 0; i < kClasses; i++) stats->prof_launches[i] = pf->cls_launches[i];
     pf->collect(stats->prof_ms);
+    pf->timeline(g_tl_cls, g_tl_start, g_tl_end);
     return SSS_OK;
 }
 
@@ -352,18 +346,8 @@ int build_graph(const Work& w, const Params& p, const Seg* roots_dev, uint32_t n
     Branches br;  // the body's concurrent branches (capture streams and fork/join events)
     CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "capture stream");
     cudaError_t se = cudaStreamCreateWithFlags(&body_st, cudaStreamNonBlocking);
-    if (se == cudaSuccess) se = cudaStreamCreateWithFlags(&br.base, cudaStreamNonBlocking);
-    if (se == cudaSuccess) se = cudaStreamCreateWithFlags(&br.medium, cudaStreamNonBlocking);
-    if (se == cudaSuccess) se = cudaEventCreateWithFlags(&br.fork, cudaEventDisableTiming);
-    if (se == cudaSuccess) se = cudaEventCreateWithFlags(&br.join_base, cudaEventDisableTiming);
-    if (se == cudaSuccess) se = cudaEventCreateWithFlags(&br.join_medium, cudaEventDisableTiming);
-    auto free_branches = [&]() {
-        if (br.base) cudaStreamDestroy(br.base);
-        if (br.medium) cudaStreamDestroy(br.medium);
-        if (br.fork) cudaEventDestroy(br.fork);
-        if (br.join_base) cudaEventDestroy(br.join_base);
-        if (br.join_medium) cudaEventDestroy(br.join_medium);
-    };
+    if (se == cudaSuccess) se = branches_create(br);
+    auto free_branches = [&]() { branches_destroy(br); };
     if (se != cudaSuccess) {
         free_branches();
         if (body_st) cudaStreamDestroy(body_st);
@@ -447,7 +431,8 @@ int build_graph(const Work& w, const Params& p, const Seg* roots_dev, uint32_t n
     cudaStreamDestroy(body_st);
     cudaStreamDestroy(st);
     cudaGraphExec_t exec = nullptr;
-    err = cudaGraphInstantiate(&exec, full, 0);
+    // kernel nodes keep the priority of the stream they were captured on
+    err = cudaGraphInstantiate(&exec, full, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(full);
     if (err != cudaSuccess) {
         cudaGetLastError();
@@ -680,6 +665,19 @@ int sss_get_last_stats(sss_stats* stats) {
     return SSS_OK;
 }
 
+int sss_get_last_timeline(uint32_t cap, int32_t* cls, double* start_ms, double* end_ms, uint32_t* out_count) {
+    std::lock_guard<std::mutex> g(g_mu);
+    if (!out_count || (cap && (!cls || !start_ms || !end_ms))) return fail(SSS_ERR_INVALID, "null pointer argument");
+    const size_t n = g_tl_cls.size();
+    *out_count = (uint32_t)n;
+    for (size_t i = 0; i < n && i < cap; i++) {
+        cls[i] = g_tl_cls[i];
+        start_ms[i] = g_tl_start[i];
+        end_ms[i] = g_tl_end[i];
+    }
+    return SSS_OK;
+}
+
 const char* sss_last_error(void) { return g_err; }
 
 int sss_release(void) {
@@ -693,15 +691,9 @@ int sss_release(void) {
             cudaGraphExecDestroy(g_graph[d].exec);
             g_graph[d] = GraphCache();
         }
-        Branches& b = g_branches[d];
-        if (b.base) {
+        if (g_branches[d].base) {
             cudaSetDevice(d);
-            cudaStreamDestroy(b.base);
-            cudaStreamDestroy(b.medium);
-            cudaEventDestroy(b.fork);
-            cudaEventDestroy(b.join_base);
-            cudaEventDestroy(b.join_medium);
-            b = Branches();
+            branches_destroy(g_branches[d]);
         }
         if (!P.ws && !P.io && !P.hh) continue;
         cudaSetDevice(d);

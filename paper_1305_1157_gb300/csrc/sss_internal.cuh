@@ -18,6 +18,7 @@ constexpr int kNBMax = 2 * kVMax + 1;           // 2047 buckets (Sec. 3.1: k = 2
 constexpr int kSampleMax = 1 << (kKMax + 1);    // sample buffer, 2v + 1 keys padded to 2^(k+1)
 constexpr uint32_t kBaseCap = 256;              // slots of one base-case tile
 constexpr uint32_t kBaseMax = kBaseCap / 2;     // largest base-case bucket (128)
+constexpr uint32_t kTinyMax = 32;               // base-case buckets this small get one warp each
 constexpr uint32_t kMedMax = 8192;              // largest bucket one CTA distributes alone
 constexpr int kMedKMax = 9;                     // its deepest tree: choose_k(8192) = 9
 constexpr int kMedNB = (2 << kMedKMax) - 1;     // 1023 buckets
@@ -77,11 +78,12 @@ struct SegPlan {
 // Device header: live append counters and the snapshot the host reads back.
 struct Hdr {
     // live, appended to by the round kernels
-    uint32_t n_large, n_med, n_small, n_bigrun, err, small_elems, med_elems, pad0;
+    uint32_t n_large, n_med, n_small, n_bigrun, err, small_elems, med_elems, n_tiny, tiny_elems, pad0[3];
     // snapshot for the host, written by k_plan
     uint32_t L, total_chunks, total_counts, total_tree;
     uint32_t n_med_snap, n_small_snap, n_bigrun_snap, small_elems_snap;
     uint32_t large_elems_snap, med_elems_snap, chunk, round;  // round: rounds done (buffer parity)
+    uint32_t n_tiny_snap, tiny_elems_snap, pad1[2];
     unsigned long long refills;   // key words gathered in device-wide rounds
     unsigned long long med_refills;  // key words gathered in medium (per-CTA) rounds
     unsigned long long base_iters;  // base-case refill iterations summed over tiles
@@ -140,7 +142,8 @@ struct Work {
     // (r + 1) & 1 while the base case of the children of round r - 1 reads
     // parity r & 1 concurrently
     Seg* med[2];             // [mmax] children for the next per-CTA round
-    Seg* small[2];           // [smax] children for the base case
+    Seg* small[2];           // [smax] children for the base case (tile form)
+    Seg* tiny[2];            // [ymax] children of at most kTinyMax strings (warp form)
     uint32_t* small_size[2]; // [smax] their sizes
     Seg* bigrun[2];          // [bmax] large runs of equal strings
     uint32_t* small_off;     // [smax + 1] packed start of each small segment
@@ -154,7 +157,7 @@ struct Work {
     uint64_t* cdf_kmin;      // [lmax] smallest sample key (u = 0)
     float* cdf_scale;        // [lmax] 1 / (largest - smallest sample key)
 
-    uint32_t cmax, tmax, lmax, chmax, smax, bmax, scan_tmp_max, mmax;
+    uint32_t cmax, tmax, lmax, chmax, smax, ymax, bmax, scan_tmp_max, mmax;
 };
 
 // ------------------------------------------------------------ device helpers
@@ -477,6 +480,20 @@ struct Prof {
         cudaEventRecord(pool[next + 1], st);
         next += 2;
     }
+    // after the streams are idle: each timed launch as (class, start, end) in
+    // milliseconds from the first launch's start
+    void timeline(std::vector<int>& cls, std::vector<double>& t0, std::vector<double>& t1) const {
+        cls.clear(); t0.clear(); t1.clear();
+        if (!enabled) return;
+        for (size_t i = 0; i < used_cls.size(); i++) {
+            float a = 0.f, b = 0.f;
+            cudaEventElapsedTime(&a, pool[0], pool[2 * i]);
+            cudaEventElapsedTime(&b, pool[0], pool[2 * i + 1]);
+            cls.push_back(used_cls[i]);
+            t0.push_back(a);
+            t1.push_back(b);
+        }
+    }
     // after the stream is idle: summed milliseconds per class
     void collect(double* ms) const {
         for (int i = 0; i < kClasses; i++) ms[i] = 0.0;
@@ -509,11 +526,16 @@ cudaError_t launch_plan(const Work& w, const Params& p, Prof* pf, cudaStream_t s
 // capture).
 // Streams and events for running the base case, the device-wide round and
 // the medium round of one round body concurrently (forked from and joined
-// back into the caller's stream).
+// back into the caller's stream).  The device-wide round's stream has the
+// highest priority: it is the chain the next round waits on, and the other
+// two fill the SMs around it.
 struct Branches {
-    cudaStream_t base = nullptr, medium = nullptr;
-    cudaEvent_t fork = nullptr, join_base = nullptr, join_medium = nullptr;
+    cudaStream_t large = nullptr, base = nullptr, medium = nullptr;
+    cudaEvent_t fork = nullptr, join_large = nullptr, join_base = nullptr, join_medium = nullptr;
 };
+// Creates / destroys the streams and events of a Branches.
+cudaError_t branches_create(Branches& b);
+void branches_destroy(Branches& b);
 
 // One round body: the base case of the last round's small children, the
 // device-wide round of the large segments and the per-CTA rounds of the

@@ -82,6 +82,15 @@ __device__ __forceinline__ void append_child(const Work& w, const Params& p, int
         uint32_t s = atomicAdd(&h->n_bigrun, 1u);
         if (s < w.bmax) w.bigrun[out][s] = Seg{start, size, cdepth, runlcp};
         else atomicOr(&h->err, kErrRunOverflow);
+    } else if (size <= min(p.base_threshold, kTinyMax)) {
+        uint32_t s = atomicAdd(&h->n_tiny, 1u);
+        if (s < w.ymax) {
+            w.tiny[out][s] = Seg{start, size, cdepth, 0u};
+            atomicAdd(&h->tiny_elems, size);
+            atomicAdd(&h->small_hist[min(31 - __clz(size), 7)], 1u);
+        } else {
+            atomicOr(&h->err, kErrSmallOverflow);
+        }
     } else if (size <= p.base_threshold) {
         uint32_t s = atomicAdd(&h->n_small, 1u);
         if (s < w.smax) {
@@ -156,7 +165,7 @@ __global__ void k_init(Work w) {
 __global__ void k_hdr_reset(Work w) {
     Hdr* h = w.hdr;
     h->n_large = 0; h->n_med = 0; h->n_small = 0; h->n_bigrun = 0; h->err = 0;
-    h->small_elems = 0; h->med_elems = 0;
+    h->small_elems = 0; h->med_elems = 0; h->n_tiny = 0; h->tiny_elems = 0;
     h->refills = 0ull;
     h->med_refills = 0ull;
     h->base_iters = 0ull;
@@ -234,6 +243,10 @@ __global__ void __launch_bounds__(1024) k_plan(Work w, Params p) {
         h->n_med_snap = min(h->n_med, w.mmax);
         h->med_elems_snap = h->med_elems;
         h->n_small_snap = h->n_small;
+        h->n_tiny_snap = h->n_tiny;
+        h->tiny_elems_snap = h->tiny_elems;
+        h->n_tiny = 0;
+        h->tiny_elems = 0;
         h->n_bigrun_snap = h->n_bigrun;
         h->small_elems_snap = h->small_elems;
         h->n_large = 0;
@@ -925,15 +938,15 @@ __global__ void __launch_bounds__(kBaseThreads) k_base(Work w, Params p) {
             const uint32_t e = r + sm.RL[r];
             uint32_t rank = 0, q = r;
             if constexpr (kWide) {
-                // (word, second word, slot) order
-                for (; q + 2 <= e; q += 2) {
-                    const uint64_t a0 = sm.K[q], a1 = sm.K[q + 1], b0 = sm.K2[q], b1 = sm.K2[q + 1];
-                    rank += (a0 < k || (a0 == k && (b0 < k2 || (b0 == k2 && q < s)))) ? 1u : 0u;
-                    rank += (a1 < k || (a1 == k && (b1 < k2 || (b1 == k2 && q + 1 < s)))) ? 1u : 0u;
-                }
+                // (word, second word, slot) order; the second word only on a tie
                 for (; q < e; q++) {
-                    const uint64_t a = sm.K[q], b = sm.K2[q];
-                    rank += (a < k || (a == k && (b < k2 || (b == k2 && q < s)))) ? 1u : 0u;
+                    const uint64_t a = sm.K[q];
+                    if (a != k) {
+                        rank += a < k ? 1u : 0u;
+                    } else {
+                        const uint64_t b = sm.K2[q];
+                        rank += (b < k2 || (b == k2 && q < s)) ? 1u : 0u;
+                    }
                 }
             } else {
                 for (; q + 4 <= e; q += 4) {
@@ -1018,6 +1031,125 @@ __global__ void __launch_bounds__(kBaseThreads) k_base(Work w, Params p) {
     if (s == 0) atomicAdd(&w.hdr->base_iters, (unsigned long long)(iter + 1));
     __syncthreads();  // shared arrays are rewritten by the next tile
     }
+}
+
+// Base case of the buckets of at most kTinyMax strings: one warp per bucket,
+// lane i holds the bucket's i-th string.  The passes are those of k_base
+// (rank every string of an active run by (key, lane), move it there, fix the
+// LCP of neighbours whose keys differ, turn groups of equal keys without the
+// terminator into runs w bytes deeper) with a per-warp shared buffer and
+// ballots instead of block-wide barriers, so a warp stops as soon as its own
+// bucket is sorted.
+constexpr int kTinyWarps = 8;
+
+template <class KT>
+__global__ void __launch_bounds__(32 * kTinyWarps) k_tiny(Work w, Params p) {
+    constexpr uint32_t kW = KeyTraits<KT>::kBytes;
+    __shared__ uint64_t sK[kTinyWarps][32], sK2[kTinyWarps][32], sO[kTinyWarps][32];
+    __shared__ uint32_t sI[kTinyWarps][32];
+    __shared__ unsigned long long s_iters;
+    const int buf = w.hdr->round & 1u;
+    const uint32_t nt = w.hdr->n_tiny_snap;
+    const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+    const uint32_t le = lanemask_lt() | (1u << lane);
+    if (threadIdx.x == 0) s_iters = 0ull;
+    __syncthreads();
+    uint32_t my_iters = 0;
+    for (uint32_t t = blockIdx.x * kTinyWarps + wid; t < nt; t += gridDim.x * kTinyWarps) {
+        const Seg g = w.tiny[buf][t];
+        const uint32_t r = g.size;  // 2..kTinyMax
+        const bool live = lane < r;
+        const uint32_t G = g.begin + lane;
+        uint64_t k = 0, k2 = 0, o = 0;
+        uint32_t id = 0;
+        if (live) {
+            const Rec rc = load_rec(&w.rec[buf][G]);
+            k = rc.key;
+            k2 = rc.key2;
+            o = rc.off;
+            id = rc.idx;
+        }
+        uint32_t rs = 0, re = r, d = g.depth;  // my run [rs, re) and its common prefix
+        bool act = live;
+        for (uint32_t iter = 0;; iter++) {
+            if (iter >= kBaseMaxIters) {  // never expected: strings end, so runs end
+                if (lane == 0) atomicOr(&w.hdr->err, kErrBaseIters);
+                break;
+            }
+            my_iters++;
+            // ---- rank inside the run: (key, lane) order keeps index order for ties
+            sK[wid][lane] = k;
+            sK2[wid][lane] = k2;
+            __syncwarp();
+            uint32_t rank = 0;
+            if (act) {
+                for (uint32_t q = rs; q < re; q++) {
+                    const uint64_t kq = sK[wid][q];
+                    bool less;
+                    if (kq != k) {
+                        less = kq < k;
+                    } else if constexpr (kW == 16) {  // first words tie: the second word, then the lane
+                        const uint64_t k2q = sK2[wid][q];
+                        less = k2q < k2 || (k2q == k2 && q < lane);
+                    } else {
+                        less = q < lane;
+                    }
+                    rank += less ? 1u : 0u;
+                }
+            }
+            const uint32_t np = act ? rs + rank : lane;
+            __syncwarp();
+            if (live) {
+                sK[wid][np] = k;
+                sK2[wid][np] = k2;
+                sO[wid][np] = o;
+                sI[wid][np] = id;
+            }
+            __syncwarp();
+            uint64_t pk = 0, pk2 = 0;
+            if (live) {
+                k = sK[wid][lane];
+                k2 = sK2[wid][lane];
+                o = sO[wid][lane];
+                id = sI[wid][lane];
+                if (lane) {
+                    pk = sK[wid][lane - 1];
+                    pk2 = sK2[wid][lane - 1];
+                }
+            }
+            __syncwarp();
+            // ---- decide neighbours inside the ranked runs
+            const KT ck = base_key<KT>(k, k2);
+            bool head = true;
+            if (act && lane != rs) {
+                const KT pkk = base_key<KT>(pk, pk2);
+                if (!keq(pkk, ck)) {
+                    w.out_lcp[G] = d + klcp(pkk, ck);
+                } else {
+                    head = false;
+                    if (kends(ck)) w.out_lcp[G] = d + kchars(ck);
+                }
+            }
+            // groups of equal keys: [highest head <= lane, next head above lane)
+            const uint32_t heads = __ballot_sync(FULL_MASK, head);
+            const uint32_t gs = 31u - (uint32_t)__clz(heads & le);
+            const uint32_t above = heads & ~le;
+            const uint32_t ge = above ? (uint32_t)__ffs(above) - 1u : 32u;
+            const bool go = act && ge - gs >= 2u && !kends(ck);
+            if (go) {
+                rs = gs;
+                re = ge;
+                d += kW;
+                refill(w.chars, k, k2, o, d, kW);
+            }
+            act = go;
+            if (!__any_sync(FULL_MASK, go)) break;
+        }
+        if (live) w.out_perm[G] = id;
+    }
+    if ((threadIdx.x & 31u) == 0 && my_iters) atomicAdd(&s_iters, (unsigned long long)my_iters);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_iters) atomicAdd(&w.hdr->base_iters, s_iters);
 }
 
 // Buckets too large for the base case whose strings are all equal.
@@ -1261,26 +1393,60 @@ static cudaError_t launch_medium_t(const Work& w, const Params& p, const Hdr* hc
     return cudaGetLastError();
 }
 
+#ifndef SSS_BRANCH_PRIORITIES
+#define SSS_BRANCH_PRIORITIES 1
+#endif
+
+cudaError_t branches_create(Branches& b) {
+    int least = 0, greatest = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (!SSS_BRANCH_PRIORITIES) greatest = least;
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b.large, cudaStreamNonBlocking, greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b.base, cudaStreamNonBlocking, least);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b.medium, cudaStreamNonBlocking, least);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.join_large, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.join_base, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.join_medium, cudaEventDisableTiming);
+    if (e != cudaSuccess) branches_destroy(b);
+    return e;
+}
+
+void branches_destroy(Branches& b) {
+    if (b.large) cudaStreamDestroy(b.large);
+    if (b.base) cudaStreamDestroy(b.base);
+    if (b.medium) cudaStreamDestroy(b.medium);
+    if (b.fork) cudaEventDestroy(b.fork);
+    if (b.join_large) cudaEventDestroy(b.join_large);
+    if (b.join_base) cudaEventDestroy(b.join_base);
+    if (b.join_medium) cudaEventDestroy(b.join_medium);
+    b = Branches();
+}
+
 cudaError_t launch_body(const Work& w, const Params& p, const Hdr* hc, uint32_t* out_tiles, Prof* pf,
                         cudaStream_t st, const Branches* br) {
     const bool wide = p.key_bytes == 16;
-    cudaStream_t sb = st, sm = st;
+    cudaStream_t sl = st, sb = st, sm = st;
     cudaError_t e = cudaSuccess;
     if (br) {
+        sl = br->large;
         sb = br->base;
         sm = br->medium;
         if ((e = cudaEventRecord(br->fork, st)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(sl, br->fork, 0)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(sb, br->fork, 0)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(sm, br->fork, 0)) != cudaSuccess) return e;
     }
-    if ((e = launch_small(w, p, hc, out_tiles, pf, sb)) != cudaSuccess) return e;
+    e = wide ? launch_round_t<Key16>(w, p, hc, pf, sl) : launch_round_t<uint64_t>(w, p, hc, pf, sl);
+    if (e != cudaSuccess) return e;
     e = wide ? launch_medium_t<Key16>(w, p, hc, pf, sm) : launch_medium_t<uint64_t>(w, p, hc, pf, sm);
     if (e != cudaSuccess) return e;
-    e = wide ? launch_round_t<Key16>(w, p, hc, pf, st) : launch_round_t<uint64_t>(w, p, hc, pf, st);
-    if (e != cudaSuccess) return e;
+    if ((e = launch_small(w, p, hc, out_tiles, pf, sb)) != cudaSuccess) return e;
     if (br) {
+        if ((e = cudaEventRecord(br->join_large, sl)) != cudaSuccess) return e;
         if ((e = cudaEventRecord(br->join_base, sb)) != cudaSuccess) return e;
         if ((e = cudaEventRecord(br->join_medium, sm)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(st, br->join_large, 0)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(st, br->join_base, 0)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(st, br->join_medium, 0)) != cudaSuccess) return e;
     }
@@ -1339,6 +1505,12 @@ cudaError_t launch_small(const Work& w, const Params& p, const Hdr* hc, uint32_t
         ProfScope ps(pf, kBase, st);
         if (p.key_bytes == 16) k_base<Key16><<<grid_of(sms * 8u, hc, tiles), kBaseThreads, 0, st>>>(w, p);
         else k_base<uint64_t><<<grid_of(sms * 8u, hc, tiles), kBaseThreads, 0, st>>>(w, p);
+    }
+    const uint32_t gt = grid_of(sms * 8u, hc, hc ? (hc->n_tiny_snap + kTinyWarps - 1) / kTinyWarps : 0u);
+    if (gt) {
+        ProfScope ps(pf, kBase, st);
+        if (p.key_bytes == 16) k_tiny<Key16><<<gt, 32 * kTinyWarps, 0, st>>>(w, p);
+        else k_tiny<uint64_t><<<gt, 32 * kTinyWarps, 0, st>>>(w, p);
     }
     const uint32_t gr = grid_of(sms * 4u, hc, hc ? hc->n_bigrun_snap : 0u);
     if (gr) {

@@ -337,3 +337,18 @@ def test_graph_form_learned():
     s = gen.generate(2, 300_000, 65)
     perm, lcp = gpu_sort(s, learned=True)
     assert_same(s, perm, lcp)
+
+
+def test_profiled_timeline():
+    sss.sss_set_options(profile=1)
+    s = gen.generate(2, 200_000, 71)
+    perm, lcp = gpu_sort(s)
+    assert_same(s, perm, lcp)
+    tl = sss.sss_get_last_timeline()
+    st = sss.sss_get_last_stats()
+    assert tl and tl[0][1] == 0.0
+    assert all(c in sss.K_CLASSES and 0.0 <= a <= b for c, a, b in tl)
+    # every kernel class with timed launches appears in the timeline as often
+    for i, c in enumerate(sss.K_CLASSES):
+        if c != "scan":  # one timed entry covers the scan's three kernels
+            assert sum(1 for x in tl if x[0] == c) == st.prof_launches[i], c
