@@ -526,9 +526,9 @@ cudaError_t launch_plan(const Work& w, const Params& p, Prof* pf, cudaStream_t s
 // capture).
 // Streams and events for running the base case, the device-wide round and
 // the medium round of one round body concurrently (forked from and joined
-// back into the caller's stream).  The device-wide round's stream has the
-// highest priority: it is the chain the next round waits on, and the other
-// two fill the SMs around it.
+// back into the caller's stream).  Stream priorities: the device-wide round
+// (the chain the next round waits on) highest, the base case next, the
+// medium round lowest; the lower branches fill the SMs around the higher.
 struct Branches {
     cudaStream_t large = nullptr, base = nullptr, medium = nullptr;
     cudaEvent_t fork = nullptr, join_large = nullptr, join_base = nullptr, join_medium = nullptr;

@@ -762,12 +762,17 @@ struct MedSmem {
     uint16_t bid[kMedMax];
     uint32_t hist[kMedNB + 1];
     uint32_t wsum[33];
+    uint32_t full;  // a bucket holding the whole segment, or kNoRefill
     ScatterState<kMedNB> ss;
 };
 
 // One CTA runs one whole distribution round for one medium segment (the
 // sequential S^5 of the paper, here on one SM): sample, tree, classify into a
-// shared bucket array, local prefix sum, stable move, child segments.
+// shared bucket array, local prefix sum, stable move, child segments.  When
+// every string lands in the equality bucket of one splitter without the
+// terminator (they all share the next w characters), the CTA steps over
+// those characters in place (gathers the keys w deeper, same positions) and
+// classifies again, instead of moving the whole segment into one child.
 template <class KT>
 __global__ void __launch_bounds__(kScatterThreads, SSS_SCATTER_MIN_BLOCKS) k_med_round(Work w, Params p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -777,25 +782,44 @@ __global__ void __launch_bounds__(kScatterThreads, SSS_SCATTER_MIN_BLOCKS) k_med
     const uint32_t n_med = w.hdr->n_med_snap;
     __shared__ uint32_t s_item;
     for (uint32_t mi = first_item(); mi < n_med; mi = next_item(&w.hdr->q_med, &s_item)) {
-        const Seg g = w.med[med_in][mi];
+        Seg g = w.med[med_in][mi];
         const uint32_t m = g.size;
         const int k = choose_k(m, min(p.k_max, kMedKMax));
         const uint32_t v = (1u << k) - 1u, nb = 2u * v + 1u;
         const uint32_t pw = 2u << k, cnt = pw - 1u;
-        const Rec* recs = w.rec[cur];
-        for (uint32_t j = threadIdx.x; j < pw; j += blockDim.x)
-            sm.samp[j] = j < cnt ? KeyTraits<KT>::load(recs + g.begin + sample_pos(p.seed, g.begin, m, j))
-                                 : KeyTraits<KT>::top();
-        for (uint32_t b = threadIdx.x; b <= nb; b += blockDim.x) {
-            sm.hist[b] = 0;
-            for (int q = 0; q < kScatterWarps; q++) sm.ss.whist[q][b] = 0;
+        Rec* recs = w.rec[cur];
+        for (uint32_t level = 0;; level++) {
+            for (uint32_t j = threadIdx.x; j < pw; j += blockDim.x)
+                sm.samp[j] = j < cnt ? KeyTraits<KT>::load(recs + g.begin + sample_pos(p.seed, g.begin, m, j))
+                                     : KeyTraits<KT>::top();
+            for (uint32_t b = threadIdx.x; b <= nb; b += blockDim.x) {
+                sm.hist[b] = 0;
+                for (int q = 0; q < kScatterWarps; q++) sm.ss.whist[q][b] = 0;
+            }
+            if (threadIdx.x == 0) sm.full = kNoRefill;
+            __syncthreads();
+            bitonic_sort(sm.samp, pw);
+            select_splitters(sm.samp, cnt, k, sm.lvl, sm.ra, sm.rb);
+            emit_tree(sm.lvl, k, sm.t + 1, sm.ino);
+            classify_range(recs, g.begin, g.begin + m, sm.t, sm.ino, k, nb, sm.hist, sm.bid);
+            __syncthreads();
+            for (uint32_t b = 1u + 2u * threadIdx.x; b < nb; b += 2u * blockDim.x)
+                if (sm.hist[b] == m && !kends(sm.ino[b >> 1])) sm.full = b;
+            __syncthreads();
+            if (sm.full == kNoRefill || level >= kBaseMaxIters) break;
+            // all strings share the next w characters: gather their keys w
+            // deeper in place and classify again
+            uint32_t nref = 0;
+            for (uint32_t e = g.begin + threadIdx.x; e < g.begin + m; e += blockDim.x) {
+                Rec r = load_rec(recs + e);
+                refill_rec<KT>(w.chars, r, g.depth + KeyTraits<KT>::kBytes, g.depth);
+                store_rec(recs + e, r);
+                nref++;
+            }
+            add_refills(&w.hdr->med_refills, nref);
+            g.depth += KeyTraits<KT>::kBytes;
+            __syncthreads();
         }
-        __syncthreads();
-        bitonic_sort(sm.samp, pw);
-        select_splitters(sm.samp, cnt, k, sm.lvl, sm.ra, sm.rb);
-        emit_tree(sm.lvl, k, sm.t + 1, sm.ino);
-        classify_range(recs, g.begin, g.begin + m, sm.t, sm.ino, k, nb, sm.hist, sm.bid);
-        __syncthreads();
         // bucket starts: consecutive buckets per thread
         constexpr int kPer = (kMedNB + 1) / kScatterThreads;
         uint32_t cnts[kPer], sum = 0;
@@ -1398,11 +1422,15 @@ static cudaError_t launch_medium_t(const Work& w, const Params& p, const Hdr* hc
 #endif
 
 cudaError_t branches_create(Branches& b) {
+    // priorities: the device-wide round first, then the base case (short
+    // kernels that would otherwise queue behind the medium round's CTAs), the
+    // medium round fills what is left
     int least = 0, greatest = 0;
     cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
     if (!SSS_BRANCH_PRIORITIES) greatest = least;
+    const int middle = greatest < least ? greatest + 1 : greatest;
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b.large, cudaStreamNonBlocking, greatest);
-    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b.base, cudaStreamNonBlocking, least);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b.base, cudaStreamNonBlocking, middle);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b.medium, cudaStreamNonBlocking, least);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.join_large, cudaEventDisableTiming);
