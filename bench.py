@@ -474,9 +474,13 @@ def main():
             dist.destroy_process_group()
         return 0
 
-    # roofline of the dominant kernel
+    # roofline of the dominant kernel: k_scatter, the largest share of the
+    # serialised launch list (profiles/launches_url-16m.txt) and the last
+    # kernel of the device-wide round, whose branch runs at the highest
+    # stream priority (the other branches' event times include the time
+    # they yield the SMs to it)
     cls = sss.K_CLASSES
-    dom = int(np.argmax(prof_ms))
+    dom = cls.index("scatter") if prof_launches[cls.index("scatter")] else int(np.argmax(prof_ms))
     # algorithmic bytes per kernel class: device-wide rounds (k_classify,
     # k_scatter) see the large segments' strings, k_med_round the medium ones
     algo = {"scatter": SCATTER_BYTES_PER_STRING * large_strings + REFILL_BYTES * large_refills,
