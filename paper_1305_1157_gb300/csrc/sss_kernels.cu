@@ -23,6 +23,8 @@
 // Between rounds k_plan lays out the next device-wide round.  Equality
 // buckets whose splitter ends the string are finished runs (k_bigrun when
 // large); k_fixup resolves the LCP at bucket boundaries at the end.
+#include <string.h>
+
 #include "sss_internal.cuh"
 
 namespace sss {
@@ -540,13 +542,13 @@ struct ScatterState {
 };
 
 // Stable move of the strings [lo, hi) of one segment (Sec. 3.1: out-of-place
-// redistribution into the shadow arrays).  Sub-tiles of 2048 strings are
-// taken in order; warp w owns 256 consecutive strings of a sub-tile and
+// redistribution into the shadow arrays).  Sub-tiles of 256 * ITEMS strings
+// are taken in order; warp w owns 32 * ITEMS consecutive strings of one and
 // ranks equal buckets by lane (match + popc), per-warp counters give the
 // offset of each warp.  Needs: ss.run_pos/rdep set, ss.whist zero (columns
 // 0..nb), the tree in t/ino (or bucket ids in bid[e - lo]), 256 threads.
 // Returns this thread's number of key words gathered again.
-template <int NBCAP, bool kFromBid, class KT>
+template <int NBCAP, bool kFromBid, class KT, int ITEMS = kScatterItems>
 __device__ uint32_t scatter_range(const Work& w, int cur, uint32_t lo, uint32_t hi, uint32_t nb,
                                   ScatterState<NBCAP>& ss, const KT* t, const KT* ino, int k,
                                   const uint16_t* bid, uint32_t seg_end, uint32_t depth, const float* C = nullptr,
@@ -557,12 +559,12 @@ __device__ uint32_t scatter_range(const Work& w, int cur, uint32_t lo, uint32_t 
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     const uint32_t lt = lanemask_lt();
     uint32_t nref = 0;
-    for (uint32_t sub = lo; sub < hi; sub += kSubTile) {
-        Rec rr[kScatterItems];
-        uint32_t bb[kScatterItems], loc[kScatterItems];
-        const uint32_t wbase = sub + warp * (32u * kScatterItems) + lane;
+    for (uint32_t sub = lo; sub < hi; sub += kScatterThreads * ITEMS) {
+        Rec rr[ITEMS];
+        uint32_t bb[ITEMS], loc[ITEMS];
+        const uint32_t wbase = sub + warp * (32u * ITEMS) + lane;
 #pragma unroll
-        for (int j = 0; j < kScatterItems; j++) {
+        for (int j = 0; j < ITEMS; j++) {
             const uint32_t e = wbase + j * 32u;
             const bool ok = e < hi;
             if (ok) rr[j] = load_rec(rec_in + e);
@@ -573,7 +575,7 @@ __device__ uint32_t scatter_range(const Work& w, int cur, uint32_t lo, uint32_t 
         if constexpr (!kFromBid && KeyTraits<KT>::kBytes == 8) {
             if (C) {
 #pragma unroll
-                for (int j = 0; j < kScatterItems; j++) {
+                for (int j = 0; j < ITEMS; j++) {
                     const uint32_t e = wbase + j * 32u;
                     uint32_t b = nb;
                     if (e < hi && !propose_bucket(rr[j].key, C, M, kmin, scale, ino, (nb - 1u) / 2u, b))
@@ -584,18 +586,18 @@ __device__ uint32_t scatter_range(const Work& w, int cur, uint32_t lo, uint32_t 
             }
         }
         if (!kFromBid && !proposed) {
-            KT kk[kScatterItems];
+            KT kk[ITEMS];
 #pragma unroll
-            for (int j = 0; j < kScatterItems; j++) kk[j] = KeyTraits<KT>::of(rr[j]);
-            classify_keys<kScatterItems>(kk, bb, t, ino, k);
+            for (int j = 0; j < ITEMS; j++) kk[j] = KeyTraits<KT>::of(rr[j]);
+            classify_keys<ITEMS>(kk, bb, t, ino, k);
 #pragma unroll
-            for (int j = 0; j < kScatterItems; j++)
+            for (int j = 0; j < ITEMS; j++)
                 if (wbase + j * 32u >= hi) bb[j] = nb;
         }
         // next key words of strings whose bucket moves deeper: all gathers are
         // issued here, before any store, and complete during the ranking
 #pragma unroll
-        for (int j = 0; j < kScatterItems; j++) {
+        for (int j = 0; j < ITEMS; j++) {
             const uint32_t rd = bb[j] < nb ? ss.rdep[bb[j]] : kNoRefill;
             if (rd != kNoRefill && rd != kSingle) {
                 refill_rec<KT>(w.chars, rr[j], rd, depth);
@@ -603,7 +605,7 @@ __device__ uint32_t scatter_range(const Work& w, int cur, uint32_t lo, uint32_t 
             }
         }
 #pragma unroll
-        for (int j = 0; j < kScatterItems; j++) {
+        for (int j = 0; j < ITEMS; j++) {
             const uint32_t b = bb[j];
             const uint32_t peers = __match_any_sync(FULL_MASK, b);
             const uint32_t leader = (uint32_t)__ffs(peers) - 1u;
@@ -633,7 +635,7 @@ __device__ uint32_t scatter_range(const Work& w, int cur, uint32_t lo, uint32_t 
         }
         __syncthreads();
 #pragma unroll
-        for (int j = 0; j < kScatterItems; j++) {
+        for (int j = 0; j < ITEMS; j++) {
             const uint32_t e = wbase + j * 32u;
             if (e < hi) {
                 const uint32_t b = bb[j];
@@ -754,17 +756,25 @@ __global__ void __launch_bounds__(kScatterThreads, SSS_SCATTER_MIN_BLOCKS) k_sca
 
 template <class KT>
 struct MedSmem {
-    KT samp[1 << (kMedKMax + 1)];
-    KT lvl[1 << kMedKMax];
-    int32_t ra[1 << kMedKMax], rb[1 << kMedKMax];
     KT t[1 << kMedKMax];
     KT ino[1 << kMedKMax];
-    uint16_t bid[kMedMax];
     uint32_t hist[kMedNB + 1];
     uint32_t wsum[33];
     uint32_t full;  // a bucket holding the whole segment, or kNoRefill
-    ScatterState<kMedNB> ss;
+    union {
+        struct {  // splitter choice
+            KT samp[1 << (kMedKMax + 1)];
+            KT lvl[1 << kMedKMax];
+            int32_t ra[1 << kMedKMax], rb[1 << kMedKMax];
+        } sel;
+        struct {  // classification and move
+            uint16_t bid[kMedMax];
+            ScatterState<kMedNB> ss;
+        } mv;
+    };
 };
+
+constexpr int kMedItems = 4;  // records per thread in a medium round's move
 
 // One CTA runs one whole distribution round for one medium segment (the
 // sequential S^5 of the paper, here on one SM): sample, tree, classify into a
@@ -773,8 +783,11 @@ struct MedSmem {
 // terminator (they all share the next w characters), the CTA steps over
 // those characters in place (gathers the keys w deeper, same positions) and
 // classifies again, instead of moving the whole segment into one child.
+#ifndef SSS_MED_MIN_BLOCKS
+#define SSS_MED_MIN_BLOCKS 3
+#endif
 template <class KT>
-__global__ void __launch_bounds__(kScatterThreads, SSS_SCATTER_MIN_BLOCKS) k_med_round(Work w, Params p) {
+__global__ void __launch_bounds__(kScatterThreads, SSS_MED_MIN_BLOCKS) k_med_round(Work w, Params p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     MedSmem<KT>& sm = *reinterpret_cast<MedSmem<KT>*>(smem_raw);
     const int cur = w.hdr->round & 1u;
@@ -790,18 +803,18 @@ __global__ void __launch_bounds__(kScatterThreads, SSS_SCATTER_MIN_BLOCKS) k_med
         Rec* recs = w.rec[cur];
         for (uint32_t level = 0;; level++) {
             for (uint32_t j = threadIdx.x; j < pw; j += blockDim.x)
-                sm.samp[j] = j < cnt ? KeyTraits<KT>::load(recs + g.begin + sample_pos(p.seed, g.begin, m, j))
-                                     : KeyTraits<KT>::top();
-            for (uint32_t b = threadIdx.x; b <= nb; b += blockDim.x) {
-                sm.hist[b] = 0;
-                for (int q = 0; q < kScatterWarps; q++) sm.ss.whist[q][b] = 0;
-            }
+                sm.sel.samp[j] = j < cnt ? KeyTraits<KT>::load(recs + g.begin + sample_pos(p.seed, g.begin, m, j))
+                                         : KeyTraits<KT>::top();
+            for (uint32_t b = threadIdx.x; b <= nb; b += blockDim.x) sm.hist[b] = 0;
             if (threadIdx.x == 0) sm.full = kNoRefill;
             __syncthreads();
-            bitonic_sort(sm.samp, pw);
-            select_splitters(sm.samp, cnt, k, sm.lvl, sm.ra, sm.rb);
-            emit_tree(sm.lvl, k, sm.t + 1, sm.ino);
-            classify_range(recs, g.begin, g.begin + m, sm.t, sm.ino, k, nb, sm.hist, sm.bid);
+            bitonic_sort(sm.sel.samp, pw);
+            select_splitters(sm.sel.samp, cnt, k, sm.sel.lvl, sm.sel.ra, sm.sel.rb);
+            emit_tree(sm.sel.lvl, k, sm.t + 1, sm.ino);
+            // the splitter-choice scratch is dead: the move state takes its place
+            for (uint32_t b = threadIdx.x; b <= nb; b += blockDim.x)
+                for (int q = 0; q < kScatterWarps; q++) sm.mv.ss.whist[q][b] = 0;
+            classify_range(recs, g.begin, g.begin + m, sm.t, sm.ino, k, nb, sm.hist, sm.mv.bid);
             __syncthreads();
             for (uint32_t b = 1u + 2u * threadIdx.x; b < nb; b += 2u * blockDim.x)
                 if (sm.hist[b] == m && !kends(sm.ino[b >> 1])) sm.full = b;
@@ -836,8 +849,8 @@ __global__ void __launch_bounds__(kScatterThreads, SSS_SCATTER_MIN_BLOCKS) k_med
             if (b < nb) {
                 const uint32_t size = cnts[q];
                 const BucketInfo bi = bucket_info(b, nb, g.depth, sm.ino, size);
-                sm.ss.run_pos[b] = start;
-                sm.ss.rdep[b] = refill_code(bi, size, g.depth);
+                sm.mv.ss.run_pos[b] = start;
+                sm.mv.ss.rdep[b] = refill_code(bi, size, g.depth);
                 if (size > 0) {
                     if (start > g.begin) w.out_lcp[start] = kLcpFlag | g.depth;
                     append_child(w, p, med_out, start, size, bi.cdepth, bi.isrun, bi.runlcp);
@@ -847,8 +860,8 @@ __global__ void __launch_bounds__(kScatterThreads, SSS_SCATTER_MIN_BLOCKS) k_med
         }
         __syncthreads();
         const uint32_t nref =
-            scatter_range<kMedNB, true, KT>(w, cur, g.begin, g.begin + m, nb, sm.ss, sm.t, sm.ino, k, sm.bid, g.begin + m,
-                                        g.depth);
+            scatter_range<kMedNB, true, KT, kMedItems>(w, cur, g.begin, g.begin + m, nb, sm.mv.ss, sm.t, sm.ino, k,
+                                                       sm.mv.bid, g.begin + m, g.depth);
         add_refills(&w.hdr->med_refills, nref);
         __syncthreads();
     }
@@ -1409,7 +1422,7 @@ static cudaError_t launch_round_t(const Work& w, const Params& p, const Hdr* hc,
 
 template <class KT>
 static cudaError_t launch_medium_t(const Work& w, const Params& p, const Hdr* hc, Prof* pf, cudaStream_t st) {
-    const uint32_t gm = grid_of(p.num_sms * 2u, hc, hc ? hc->n_med_snap : 0u);
+    const uint32_t gm = grid_of(p.num_sms * SSS_MED_MIN_BLOCKS, hc, hc ? hc->n_med_snap : 0u);
     if (gm) {
         ProfScope ps(pf, kMedium, st);
         k_med_round<KT><<<gm, kScatterThreads, sizeof(MedSmem<KT>), st>>>(w, p);
@@ -1432,6 +1445,18 @@ cudaError_t branches_create(Branches& b) {
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b.large, cudaStreamNonBlocking, greatest);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b.base, cudaStreamNonBlocking, middle);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b.medium, cudaStreamNonBlocking, least);
+    // the same priorities as stream launch attributes, which stream capture
+    // copies into the kernel nodes of a graph (optional: ignored if refused)
+    if (e == cudaSuccess) {
+        const cudaStream_t ss[3] = {b.large, b.base, b.medium};
+        const int pr[3] = {greatest, middle, least};
+        for (int i = 0; i < 3; i++) {
+            cudaLaunchAttributeValue v;
+            memset(&v, 0, sizeof(v));
+            v.priority = pr[i];
+            if (cudaStreamSetAttribute(ss[i], cudaLaunchAttributePriority, &v) != cudaSuccess) cudaGetLastError();
+        }
+    }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.join_large, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.join_base, cudaEventDisableTiming);
