@@ -27,8 +27,8 @@ constexpr int kMedNB = (2 << kMedKMax) - 1;     // 1023 buckets
 #endif
 constexpr int kChunksPerSM = SSS_CHUNKS_PER_SM; // device-wide rounds: target work items per SM
 constexpr int kScatterThreads = 256;
-constexpr int kScatterItems = 8;
-constexpr uint32_t kSubTile = kScatterThreads * kScatterItems;  // 2048 strings
+constexpr int kScatterItems = 4;                // records per thread in a device-wide move
+constexpr uint32_t kSubTile = 2048;             // work-chunk granularity (a multiple of every move sub-tile)
 constexpr uint32_t kLcpFlag = 0x80000000u;      // out_lcp entry still to be resolved
 constexpr uint32_t kNoRefill = 0xFFFFFFFFu;
 constexpr uint32_t kSingle = 0xFFFFFFFEu;       // bucket of one string: finished at scatter

@@ -531,21 +531,28 @@ __global__ void __launch_bounds__(kClassifyThreads) k_classify(Work w, Params p)
 
 constexpr int kScatterWarps = kScatterThreads / 32;
 #ifndef SSS_SCATTER_MIN_BLOCKS
-#define SSS_SCATTER_MIN_BLOCKS 2
+#define SSS_SCATTER_MIN_BLOCKS 3
 #endif
 
 template <int NBCAP>
 struct ScatterState {
     uint32_t run_pos[NBCAP + 1];  // next output position of each bucket
     uint32_t rdep[NBCAP + 1];     // refill code of each bucket
-    uint16_t whist[kScatterWarps][NBCAP + 1];
+    uint64_t wcnt[NBCAP + 1];     // strings of each bucket in this sub-tile, one byte per warp
 };
+static_assert(kScatterWarps == 8, "one byte per warp in ScatterState::wcnt");
+
+// Sum of the bytes of x below byte `below` (0..8).
+__device__ __forceinline__ uint32_t byte_sum_below(uint64_t x, uint32_t below) {
+    if (below < 8u) x &= below ? (~0ull >> (64u - 8u * below)) : 0ull;
+    return __dp4a((uint32_t)x, 0x01010101u, 0u) + __dp4a((uint32_t)(x >> 32), 0x01010101u, 0u);
+}
 
 // Stable move of the strings [lo, hi) of one segment (Sec. 3.1: out-of-place
 // redistribution into the shadow arrays).  Sub-tiles of 256 * ITEMS strings
 // are taken in order; warp w owns 32 * ITEMS consecutive strings of one and
 // ranks equal buckets by lane (match + popc), per-warp counters give the
-// offset of each warp.  Needs: ss.run_pos/rdep set, ss.whist zero (columns
+// offset of each warp.  Needs: ss.run_pos/rdep set, ss.wcnt zero (entries
 // 0..nb), the tree in t/ino (or bucket ids in bid[e - lo]), 256 threads.
 // Returns this thread's number of key words gathered again.
 template <int NBCAP, bool kFromBid, class KT, int ITEMS = kScatterItems>
@@ -554,6 +561,8 @@ __device__ uint32_t scatter_range(const Work& w, int cur, uint32_t lo, uint32_t 
                                   const uint16_t* bid, uint32_t seg_end, uint32_t depth, const float* C = nullptr,
                                   uint32_t M = 0, uint64_t kmin = 0, float scale = 0.0f) {
     constexpr int kBucketsPerThread = (NBCAP + kScatterThreads) / kScatterThreads;
+    static_assert(32 * ITEMS <= 255, "per-warp bucket counts must fit a byte");
+    uint8_t* wbytes = reinterpret_cast<uint8_t*>(ss.wcnt);
     const Rec* rec_in = w.rec[cur];
     Rec* rec_out = w.rec[cur ^ 1];
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
@@ -611,27 +620,11 @@ __device__ uint32_t scatter_range(const Work& w, int cur, uint32_t lo, uint32_t 
             const uint32_t leader = (uint32_t)__ffs(peers) - 1u;
             uint32_t off = 0;
             if (lane == leader) {
-                off = ss.whist[warp][b];
-                ss.whist[warp][b] = (uint16_t)(off + (uint32_t)__popc(peers));
+                off = wbytes[8u * b + warp];
+                wbytes[8u * b + warp] = (uint8_t)(off + (uint32_t)__popc(peers));
             }
             off = __shfl_sync(FULL_MASK, off, leader);
             loc[j] = off + (uint32_t)__popc(peers & lt);
-        }
-        __syncthreads();
-        uint32_t accs[kBucketsPerThread];
-#pragma unroll
-        for (int q = 0; q < kBucketsPerThread; q++) {
-            const uint32_t b = threadIdx.x + q * kScatterThreads;
-            uint32_t acc = 0;
-            if (b < nb) {
-#pragma unroll
-                for (int ww = 0; ww < kScatterWarps; ww++) {
-                    const uint32_t cnt = ss.whist[ww][b];
-                    ss.whist[ww][b] = (uint16_t)acc;
-                    acc += cnt;
-                }
-            }
-            accs[q] = acc;
         }
         __syncthreads();
 #pragma unroll
@@ -639,7 +632,8 @@ __device__ uint32_t scatter_range(const Work& w, int cur, uint32_t lo, uint32_t 
             const uint32_t e = wbase + j * 32u;
             if (e < hi) {
                 const uint32_t b = bb[j];
-                const uint32_t pos = ss.run_pos[b] + ss.whist[warp][b] + loc[j];
+                // the strings of bucket b held by the warps before this one
+                const uint32_t pos = ss.run_pos[b] + byte_sum_below(ss.wcnt[b], warp) + loc[j];
                 const uint32_t rd = ss.rdep[b];
                 if (pos >= seg_end) {
                     atomicOr(&w.hdr->err, kErrPosition);
@@ -654,11 +648,8 @@ __device__ uint32_t scatter_range(const Work& w, int cur, uint32_t lo, uint32_t 
 #pragma unroll
         for (int q = 0; q < kBucketsPerThread; q++) {
             const uint32_t b = threadIdx.x + q * kScatterThreads;
-            if (b < nb) ss.run_pos[b] += accs[q];
-            if (b <= nb) {
-#pragma unroll
-                for (int ww = 0; ww < kScatterWarps; ww++) ss.whist[ww][b] = 0;
-            }
+            if (b < nb) ss.run_pos[b] += byte_sum_below(ss.wcnt[b], 8u);
+            if (b <= nb) ss.wcnt[b] = 0ull;
         }
         __syncthreads();
     }
@@ -717,9 +708,7 @@ __global__ void __launch_bounds__(kScatterThreads, SSS_SCATTER_MIN_BLOCKS) k_sca
 #pragma unroll
         for (int q = 0; q < kBPT; q++) {
             const uint32_t b = threadIdx.x + q * kScatterThreads;
-            if (b <= nb) {
-                for (int ww = 0; ww < kScatterWarps; ww++) sm.ss.whist[ww][b] = 0;
-            }
+            if (b <= nb) sm.ss.wcnt[b] = 0ull;
             if (b < nb) {
                 const uint32_t start = P.begin + (s_first[q] - S0);
                 const uint32_t end = (b + 1 < nb) ? P.begin + (s_next[q] - S0) : seg_end;
@@ -812,8 +801,7 @@ __global__ void __launch_bounds__(kScatterThreads, SSS_MED_MIN_BLOCKS) k_med_rou
             select_splitters(sm.sel.samp, cnt, k, sm.sel.lvl, sm.sel.ra, sm.sel.rb);
             emit_tree(sm.sel.lvl, k, sm.t + 1, sm.ino);
             // the splitter-choice scratch is dead: the move state takes its place
-            for (uint32_t b = threadIdx.x; b <= nb; b += blockDim.x)
-                for (int q = 0; q < kScatterWarps; q++) sm.mv.ss.whist[q][b] = 0;
+            for (uint32_t b = threadIdx.x; b <= nb; b += blockDim.x) sm.mv.ss.wcnt[b] = 0ull;
             classify_range(recs, g.begin, g.begin + m, sm.t, sm.ino, k, nb, sm.hist, sm.mv.bid);
             __syncthreads();
             for (uint32_t b = 1u + 2u * threadIdx.x; b < nb; b += 2u * blockDim.x)
@@ -1413,7 +1401,7 @@ static cudaError_t launch_round_t(const Work& w, const Params& p, const Hdr* hc,
         if (e != cudaSuccess) return e;
         {
             ProfScope ps(pf, kScatter, st);
-            k_scatter<KT><<<grid_of(sms * 2u, hc, hc ? hc->total_chunks : 0u), kScatterThreads,
+            k_scatter<KT><<<grid_of(sms * SSS_SCATTER_MIN_BLOCKS, hc, hc ? hc->total_chunks : 0u), kScatterThreads,
                             sizeof(ScatterSmem<KT>), st>>>(w, p);
         }
     }
