@@ -524,23 +524,25 @@ cudaError_t launch_plan(const Work& w, const Params& p, Prof* pf, cudaStream_t s
 // (hdr->round) from device memory.  hc: host copy of the header when known
 // (exact grids, empty launches skipped), nullptr for persistent grids (graph
 // capture).
-// Streams and events for running the base case, the device-wide round and
-// the medium round of one round body concurrently (forked from and joined
-// back into the caller's stream).  Stream priorities: the device-wide round
-// (the chain the next round waits on) highest, the base case next, the
-// medium round lowest; the lower branches fill the SMs around the higher.
+// Streams and events for running the base case (tile form and warp form),
+// the device-wide round and the medium round of one round body concurrently
+// (forked from and joined back into the caller's stream).  Stream
+// priorities: the device-wide round (the chain the next round waits on)
+// highest, the base case next, the medium round lowest; the lower branches
+// fill the SMs around the higher.
 struct Branches {
-    cudaStream_t large = nullptr, base = nullptr, medium = nullptr;
-    cudaEvent_t fork = nullptr, join_large = nullptr, join_base = nullptr, join_medium = nullptr;
+    cudaStream_t large = nullptr, base = nullptr, medium = nullptr, tiny = nullptr;
+    cudaEvent_t fork = nullptr, join_large = nullptr, join_base = nullptr, join_medium = nullptr,
+                join_tiny = nullptr;
 };
 // Creates / destroys the streams and events of a Branches.
 cudaError_t branches_create(Branches& b);
 void branches_destroy(Branches& b);
 
-// One round body: the base case of the last round's small children, the
-// device-wide round of the large segments and the per-CTA rounds of the
-// medium ones.  With br, the three run as concurrent branches of st; without,
-// one after the other on st.  *out_tiles: base-case tiles (host-driven only).
+// One round body: the base case of the last round's small children (tile and
+// warp forms), the device-wide round of the large segments and the per-CTA
+// rounds of the medium ones.  With br, the four run as concurrent branches
+// of st; without, one after the other on st.  *out_tiles: base-case tiles (host-driven only).
 cudaError_t launch_body(const Work& w, const Params& p, const Hdr* hc, uint32_t* out_tiles, Prof* pf,
                         cudaStream_t st, const Branches* br);
 cudaError_t launch_set_cond(const Work& w, cudaGraphConditionalHandle cond, cudaStream_t st);

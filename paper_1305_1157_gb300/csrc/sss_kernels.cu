@@ -1433,12 +1433,13 @@ cudaError_t branches_create(Branches& b) {
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b.large, cudaStreamNonBlocking, greatest);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b.base, cudaStreamNonBlocking, middle);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b.medium, cudaStreamNonBlocking, least);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b.tiny, cudaStreamNonBlocking, middle);
     // the same priorities as stream launch attributes, which stream capture
     // copies into the kernel nodes of a graph (optional: ignored if refused)
     if (e == cudaSuccess) {
-        const cudaStream_t ss[3] = {b.large, b.base, b.medium};
-        const int pr[3] = {greatest, middle, least};
-        for (int i = 0; i < 3; i++) {
+        const cudaStream_t ss[4] = {b.large, b.base, b.medium, b.tiny};
+        const int pr[4] = {greatest, middle, least, middle};
+        for (int i = 0; i < 4; i++) {
             cudaLaunchAttributeValue v;
             memset(&v, 0, sizeof(v));
             v.priority = pr[i];
@@ -1449,6 +1450,7 @@ cudaError_t branches_create(Branches& b) {
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.join_large, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.join_base, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.join_medium, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.join_tiny, cudaEventDisableTiming);
     if (e != cudaSuccess) branches_destroy(b);
     return e;
 }
@@ -1457,39 +1459,46 @@ void branches_destroy(Branches& b) {
     if (b.large) cudaStreamDestroy(b.large);
     if (b.base) cudaStreamDestroy(b.base);
     if (b.medium) cudaStreamDestroy(b.medium);
+    if (b.tiny) cudaStreamDestroy(b.tiny);
     if (b.fork) cudaEventDestroy(b.fork);
     if (b.join_large) cudaEventDestroy(b.join_large);
     if (b.join_base) cudaEventDestroy(b.join_base);
     if (b.join_medium) cudaEventDestroy(b.join_medium);
+    if (b.join_tiny) cudaEventDestroy(b.join_tiny);
     b = Branches();
 }
+
+static cudaError_t launch_tiny(const Work& w, const Params& p, const Hdr* hc, Prof* pf, cudaStream_t st);
+static cudaError_t launch_tiles(const Work& w, const Params& p, const Hdr* hc, uint32_t* out_tiles, Prof* pf,
+                                cudaStream_t st);
 
 cudaError_t launch_body(const Work& w, const Params& p, const Hdr* hc, uint32_t* out_tiles, Prof* pf,
                         cudaStream_t st, const Branches* br) {
     const bool wide = p.key_bytes == 16;
-    cudaStream_t sl = st, sb = st, sm = st;
+    cudaStream_t sl = st, sb = st, sm = st, sy = st;
     cudaError_t e = cudaSuccess;
     if (br) {
         sl = br->large;
         sb = br->base;
         sm = br->medium;
+        sy = br->tiny;
         if ((e = cudaEventRecord(br->fork, st)) != cudaSuccess) return e;
-        if ((e = cudaStreamWaitEvent(sl, br->fork, 0)) != cudaSuccess) return e;
-        if ((e = cudaStreamWaitEvent(sb, br->fork, 0)) != cudaSuccess) return e;
-        if ((e = cudaStreamWaitEvent(sm, br->fork, 0)) != cudaSuccess) return e;
+        for (cudaStream_t x : {sl, sb, sm, sy})
+            if ((e = cudaStreamWaitEvent(x, br->fork, 0)) != cudaSuccess) return e;
     }
     e = wide ? launch_round_t<Key16>(w, p, hc, pf, sl) : launch_round_t<uint64_t>(w, p, hc, pf, sl);
     if (e != cudaSuccess) return e;
     e = wide ? launch_medium_t<Key16>(w, p, hc, pf, sm) : launch_medium_t<uint64_t>(w, p, hc, pf, sm);
     if (e != cudaSuccess) return e;
-    if ((e = launch_small(w, p, hc, out_tiles, pf, sb)) != cudaSuccess) return e;
+    if ((e = launch_tiles(w, p, hc, out_tiles, pf, sb)) != cudaSuccess) return e;
+    if ((e = launch_tiny(w, p, hc, pf, sy)) != cudaSuccess) return e;
     if (br) {
-        if ((e = cudaEventRecord(br->join_large, sl)) != cudaSuccess) return e;
-        if ((e = cudaEventRecord(br->join_base, sb)) != cudaSuccess) return e;
-        if ((e = cudaEventRecord(br->join_medium, sm)) != cudaSuccess) return e;
-        if ((e = cudaStreamWaitEvent(st, br->join_large, 0)) != cudaSuccess) return e;
-        if ((e = cudaStreamWaitEvent(st, br->join_base, 0)) != cudaSuccess) return e;
-        if ((e = cudaStreamWaitEvent(st, br->join_medium, 0)) != cudaSuccess) return e;
+        const cudaEvent_t joins[4] = {br->join_large, br->join_base, br->join_medium, br->join_tiny};
+        const cudaStream_t from[4] = {sl, sb, sm, sy};
+        for (int i = 0; i < 4; i++) {
+            if ((e = cudaEventRecord(joins[i], from[i])) != cudaSuccess) return e;
+            if ((e = cudaStreamWaitEvent(st, joins[i], 0)) != cudaSuccess) return e;
+        }
     }
     return cudaSuccess;
 }
@@ -1531,8 +1540,21 @@ cudaError_t launch_advance(const Work& w, Prof* pf, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_small(const Work& w, const Params& p, const Hdr* hc, uint32_t* out_tiles, Prof* pf,
-                         cudaStream_t st) {
+// The warp-form base case (buckets of at most kTinyMax strings).
+static cudaError_t launch_tiny(const Work& w, const Params& p, const Hdr* hc, Prof* pf, cudaStream_t st) {
+    const uint32_t gt = grid_of(p.num_sms * 8u, hc, hc ? (hc->n_tiny_snap + kTinyWarps - 1) / kTinyWarps : 0u);
+    if (gt) {
+        ProfScope ps(pf, kBase, st);
+        if (p.key_bytes == 16) k_tiny<Key16><<<gt, 32 * kTinyWarps, 0, st>>>(w, p);
+        else k_tiny<uint64_t><<<gt, 32 * kTinyWarps, 0, st>>>(w, p);
+    }
+    return cudaGetLastError();
+}
+
+// The tile-form base case (scan of the bucket sizes, tile map, k_base) and
+// the large runs of equal strings.
+static cudaError_t launch_tiles(const Work& w, const Params& p, const Hdr* hc, uint32_t* out_tiles, Prof* pf,
+                                cudaStream_t st) {
     const uint32_t sms = p.num_sms;
     uint32_t tiles = hc ? (hc->small_elems_snap + p.base_threshold - 1) / p.base_threshold : 0u;
     if (!hc || hc->n_small_snap) {
@@ -1547,12 +1569,6 @@ cudaError_t launch_small(const Work& w, const Params& p, const Hdr* hc, uint32_t
         if (p.key_bytes == 16) k_base<Key16><<<grid_of(sms * 8u, hc, tiles), kBaseThreads, 0, st>>>(w, p);
         else k_base<uint64_t><<<grid_of(sms * 8u, hc, tiles), kBaseThreads, 0, st>>>(w, p);
     }
-    const uint32_t gt = grid_of(sms * 8u, hc, hc ? (hc->n_tiny_snap + kTinyWarps - 1) / kTinyWarps : 0u);
-    if (gt) {
-        ProfScope ps(pf, kBase, st);
-        if (p.key_bytes == 16) k_tiny<Key16><<<gt, 32 * kTinyWarps, 0, st>>>(w, p);
-        else k_tiny<uint64_t><<<gt, 32 * kTinyWarps, 0, st>>>(w, p);
-    }
     const uint32_t gr = grid_of(sms * 4u, hc, hc ? hc->n_bigrun_snap : 0u);
     if (gr) {
         ProfScope ps(pf, kRuns, st);
@@ -1560,6 +1576,12 @@ cudaError_t launch_small(const Work& w, const Params& p, const Hdr* hc, uint32_t
     }
     if (out_tiles) *out_tiles = tiles;
     return cudaGetLastError();
+}
+
+cudaError_t launch_small(const Work& w, const Params& p, const Hdr* hc, uint32_t* out_tiles, Prof* pf,
+                         cudaStream_t st) {
+    cudaError_t e = launch_tiles(w, p, hc, out_tiles, pf, st);
+    return e != cudaSuccess ? e : launch_tiny(w, p, hc, pf, st);
 }
 
 cudaError_t launch_fixup(const Work& w, Prof* pf, cudaStream_t st) {
