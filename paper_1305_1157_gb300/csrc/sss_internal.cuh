@@ -350,12 +350,40 @@ __host__ __device__ __forceinline__ int choose_k(uint32_t size, int k_max) {
     return k;
 }
 
+// Level-order splitter trees in shared memory.  A wide-key tree keeps the
+// first and second words in separate arrays: a descent step reads the first
+// word (8 bytes) and the second only when the first words tie, which halves
+// the shared-memory traffic of the descent.
+struct SplitTree {
+    const uint64_t* h;
+    const uint64_t* l;
+};
+template <class KT, int N> struct LevelTree;
+template <int N> struct LevelTree<uint64_t, N> {
+    uint64_t w[N];
+    __device__ __forceinline__ void set(uint32_t i, uint64_t x) { w[i] = x; }
+    __device__ __forceinline__ const uint64_t* view() const { return w; }
+};
+template <int N> struct LevelTree<Key16, N> {
+    uint64_t h[N], l[N];
+    __device__ __forceinline__ void set(uint32_t i, const Key16& x) { h[i] = x.h; l[i] = x.l; }
+    __device__ __forceinline__ SplitTree view() const { return SplitTree{h, l}; }
+};
+
+// key > node i of a level-order tree
+__device__ __forceinline__ bool node_gt(uint64_t key, const uint64_t* t, uint32_t i) { return key > t[i]; }
+__device__ __forceinline__ bool node_gt(const Key16& key, const Key16* t, uint32_t i) { return kgt(key, t[i]); }
+__device__ __forceinline__ bool node_gt(const Key16& key, const SplitTree& t, uint32_t i) {
+    const uint64_t h = t.h[i];
+    return key.h != h ? key.h > h : key.l > t.l[i];
+}
+
 // Branch-free descent of the level-order tree t[1..v] (Sec. 3.1, i := 2i + {0,1})
 // then one equality test against the in-order array: bucket 2j + [key = x_j].
-template <class KT>
-__device__ __forceinline__ uint32_t classify_key(const KT& key, const KT* t, const KT* ino, int k) {
+template <class KT, class TT>
+__device__ __forceinline__ uint32_t classify_key(const KT& key, const TT& t, const KT* ino, int k) {
     uint32_t i = 1;
-    for (int l = 0; l < k; l++) i = 2u * i + (kgt(key, t[i]) ? 1u : 0u);
+    for (int l = 0; l < k; l++) i = 2u * i + (node_gt(key, t, i) ? 1u : 0u);
     const uint32_t v = (1u << k) - 1u;
     const uint32_t j = i - (1u << k);
     return 2u * j + ((j < v && keq(key, ino[j])) ? 1u : 0u);
@@ -364,14 +392,14 @@ __device__ __forceinline__ uint32_t classify_key(const KT& key, const KT* t, con
 // classify_key for U keys at once, descending the U paths level by level so
 // that each level issues U independent shared-memory loads (the interleaved
 // descents of Sec. 3.1).
-template <int U, class KT>
-__device__ __forceinline__ void classify_keys(const KT (&key)[U], uint32_t (&b)[U], const KT* t, const KT* ino, int k) {
+template <int U, class KT, class TT>
+__device__ __forceinline__ void classify_keys(const KT (&key)[U], uint32_t (&b)[U], const TT& t, const KT* ino, int k) {
     uint32_t i[U];
 #pragma unroll
     for (int u = 0; u < U; u++) i[u] = 1u;
     for (int l = 0; l < k; l++) {
 #pragma unroll
-        for (int u = 0; u < U; u++) i[u] = 2u * i[u] + (kgt(key[u], t[i[u]]) ? 1u : 0u);
+        for (int u = 0; u < U; u++) i[u] = 2u * i[u] + (node_gt(key[u], t, i[u]) ? 1u : 0u);
     }
     const uint32_t v = (1u << k) - 1u;
 #pragma unroll

@@ -354,6 +354,20 @@ __device__ void emit_tree(const KT* lvl, int k, KT* out_lvl, KT* out_ino) {
     __syncthreads();
 }
 
+// emit_tree into a shared-memory level-order tree (node i at t[i]).
+template <class KT, int N>
+__device__ void emit_tree_smem(const KT* lvl, int k, LevelTree<KT, N>& t, KT* out_ino) {
+    const uint32_t v = (1u << k) - 1u;
+    for (uint32_t i = 1 + threadIdx.x; i <= v; i += blockDim.x) {
+        uint32_t l = 31u - __clz(i);
+        uint32_t q = i - (1u << l);
+        uint32_t pos = (2u * q + 1u) * (1u << (k - 1 - (int)l)) - 1u;
+        t.set(i, lvl[i]);
+        out_ino[pos] = lvl[i];
+    }
+    __syncthreads();
+}
+
 // Pseudo-random sample position j of a segment (Sec. 3.1: the sample is drawn
 // pseudo-randomly).
 __device__ __forceinline__ uint32_t sample_pos(uint64_t seed, uint32_t begin, uint32_t size, uint32_t j) {
@@ -420,8 +434,8 @@ constexpr int kClassifyUnroll = 8;
 // Adds the buckets of the key words of recs[lo, hi) to hist (warp-aggregated shared atomics);
 // bid (optional) receives each bucket at bid[e - lo].  Loop bounds are
 // uniform over the block.
-template <class KT>
-__device__ __forceinline__ void classify_range(const Rec* __restrict__ recs, uint32_t lo, uint32_t hi, const KT* t,
+template <class KT, class TT>
+__device__ __forceinline__ void classify_range(const Rec* __restrict__ recs, uint32_t lo, uint32_t hi, const TT& t,
                                                const KT* ino, int k, uint32_t nb, uint32_t* hist, uint16_t* bid) {
     const uint32_t lane = threadIdx.x & 31u;
     for (uint32_t base = lo; base < hi; base += blockDim.x * kClassifyUnroll) {
@@ -478,7 +492,7 @@ constexpr uint32_t kCdfMMax = 4096;
 template <class KT>
 __global__ void __launch_bounds__(kClassifyThreads) k_classify(Work w, Params p) {
     constexpr bool kLearned = KeyTraits<KT>::kBytes == 8;  // the learned model proposes on one word
-    __shared__ KT t[kVMax + 1];
+    __shared__ LevelTree<KT, kVMax + 1> t;
     __shared__ KT ino[kVMax];
     __shared__ uint32_t hist[kNBMax + 1];
     __shared__ float C[kLearned ? kCdfMMax + 1 : 1];
@@ -495,7 +509,7 @@ __global__ void __launch_bounds__(kClassifyThreads) k_classify(Work w, Params p)
         const int k = (int)P.k;
         const uint32_t v = (1u << k) - 1u, nb = 2u * v + 1u;
         for (uint32_t i = threadIdx.x; i < v; i += blockDim.x) {
-            t[i + 1] = tree_lvl[P.tree_base + i];
+            t.set(i + 1, tree_lvl[P.tree_base + i]);
             ino[i] = tree_ino[P.tree_base + i];
         }
         for (uint32_t b = threadIdx.x; b <= nb; b += blockDim.x) hist[b] = 0;
@@ -508,17 +522,17 @@ __global__ void __launch_bounds__(kClassifyThreads) k_classify(Work w, Params p)
                 for (uint32_t j = threadIdx.x; j <= p.cdf_M; j += blockDim.x) C[j] = tab[j];
                 __syncthreads();
                 uint32_t misses = 0;
-                classify_range_learned(w.rec[cur], lo, hi, t, ino, k, nb, hist, C, p.cdf_M, w.cdf_kmin[s],
+                classify_range_learned(w.rec[cur], lo, hi, t.view(), ino, k, nb, hist, C, p.cdf_M, w.cdf_kmin[s],
                                        w.cdf_scale[s], misses);
                 misses = __reduce_add_sync(FULL_MASK, misses);
                 if ((threadIdx.x & 31u) == 0 && misses)
                     atomicAdd(&w.hdr->learned_misses, (unsigned long long)misses);
                 if (threadIdx.x == 0) atomicAdd(&w.hdr->learned_keys, (unsigned long long)(hi - lo));
             } else {
-                classify_range(w.rec[cur], lo, hi, t, ino, k, nb, hist, (uint16_t*)nullptr);
+                classify_range(w.rec[cur], lo, hi, t.view(), ino, k, nb, hist, (uint16_t*)nullptr);
             }
         } else {
-            classify_range(w.rec[cur], lo, hi, t, ino, k, nb, hist, (uint16_t*)nullptr);
+            classify_range(w.rec[cur], lo, hi, t.view(), ino, k, nb, hist, (uint16_t*)nullptr);
         }
         __syncthreads();
         for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x)
@@ -555,9 +569,9 @@ __device__ __forceinline__ uint32_t byte_sum_below(uint64_t x, uint32_t below) {
 // offset of each warp.  Needs: ss.run_pos/rdep set, ss.wcnt zero (entries
 // 0..nb), the tree in t/ino (or bucket ids in bid[e - lo]), 256 threads.
 // Returns this thread's number of key words gathered again.
-template <int NBCAP, bool kFromBid, class KT, int ITEMS = kScatterItems>
+template <int NBCAP, bool kFromBid, class KT, int ITEMS = kScatterItems, class TT>
 __device__ uint32_t scatter_range(const Work& w, int cur, uint32_t lo, uint32_t hi, uint32_t nb,
-                                  ScatterState<NBCAP>& ss, const KT* t, const KT* ino, int k,
+                                  ScatterState<NBCAP>& ss, const TT& t, const KT* ino, int k,
                                   const uint16_t* bid, uint32_t seg_end, uint32_t depth, const float* C = nullptr,
                                   uint32_t M = 0, uint64_t kmin = 0, float scale = 0.0f) {
     constexpr int kBucketsPerThread = (NBCAP + kScatterThreads) / kScatterThreads;
@@ -663,7 +677,7 @@ __device__ __forceinline__ void add_refills(unsigned long long* counter, uint32_
 
 template <class KT>
 struct ScatterSmem {
-    KT t[kVMax + 1];
+    LevelTree<KT, kVMax + 1> t;
     KT ino[kVMax];
     ScatterState<kNBMax> ss;
     float C[KeyTraits<KT>::kBytes == 8 ? kCdfMMax + 1 : 1];  // learned model knots (learned mode only)
@@ -687,7 +701,7 @@ __global__ void __launch_bounds__(kScatterThreads, SSS_SCATTER_MIN_BLOCKS) k_sca
         const int k = (int)P.k;
         const uint32_t v = (1u << k) - 1u, nb = 2u * v + 1u;
         for (uint32_t i = threadIdx.x; i < v; i += blockDim.x) {
-            sm.t[i + 1] = tree_lvl[P.tree_base + i];
+            sm.t.set(i + 1, tree_lvl[P.tree_base + i]);
             sm.ino[i] = tree_ino[P.tree_base + i];
         }
         __syncthreads();
@@ -733,7 +747,7 @@ __global__ void __launch_bounds__(kScatterThreads, SSS_SCATTER_MIN_BLOCKS) k_sca
             __syncthreads();
             C = sm.C;
         }
-        const uint32_t nref = scatter_range<kNBMax, false, KT>(w, cur, lo, hi, nb, sm.ss, sm.t, sm.ino, k, nullptr, seg_end,
+        const uint32_t nref = scatter_range<kNBMax, false, KT>(w, cur, lo, hi, nb, sm.ss, sm.t.view(), sm.ino, k, nullptr, seg_end,
                                                            P.depth, C, p.cdf_M, model ? w.cdf_kmin[s] : 0ull,
                                                            model ? w.cdf_scale[s] : 0.0f);
         add_refills(&w.hdr->refills, nref);
@@ -745,7 +759,7 @@ __global__ void __launch_bounds__(kScatterThreads, SSS_SCATTER_MIN_BLOCKS) k_sca
 
 template <class KT>
 struct MedSmem {
-    KT t[1 << kMedKMax];
+    LevelTree<KT, 1 << kMedKMax> t;
     KT ino[1 << kMedKMax];
     uint32_t hist[kMedNB + 1];
     uint32_t wsum[33];
@@ -799,10 +813,10 @@ __global__ void __launch_bounds__(kScatterThreads, SSS_MED_MIN_BLOCKS) k_med_rou
             __syncthreads();
             bitonic_sort(sm.sel.samp, pw);
             select_splitters(sm.sel.samp, cnt, k, sm.sel.lvl, sm.sel.ra, sm.sel.rb);
-            emit_tree(sm.sel.lvl, k, sm.t + 1, sm.ino);
+            emit_tree_smem(sm.sel.lvl, k, sm.t, sm.ino);
             // the splitter-choice scratch is dead: the move state takes its place
             for (uint32_t b = threadIdx.x; b <= nb; b += blockDim.x) sm.mv.ss.wcnt[b] = 0ull;
-            classify_range(recs, g.begin, g.begin + m, sm.t, sm.ino, k, nb, sm.hist, sm.mv.bid);
+            classify_range(recs, g.begin, g.begin + m, sm.t.view(), sm.ino, k, nb, sm.hist, sm.mv.bid);
             __syncthreads();
             for (uint32_t b = 1u + 2u * threadIdx.x; b < nb; b += 2u * blockDim.x)
                 if (sm.hist[b] == m && !kends(sm.ino[b >> 1])) sm.full = b;
@@ -848,7 +862,7 @@ __global__ void __launch_bounds__(kScatterThreads, SSS_MED_MIN_BLOCKS) k_med_rou
         }
         __syncthreads();
         const uint32_t nref =
-            scatter_range<kMedNB, true, KT, kMedItems>(w, cur, g.begin, g.begin + m, nb, sm.mv.ss, sm.t, sm.ino, k,
+            scatter_range<kMedNB, true, KT, kMedItems>(w, cur, g.begin, g.begin + m, nb, sm.mv.ss, sm.t.view(), sm.ino, k,
                                                        sm.mv.bid, g.begin + m, g.depth);
         add_refills(&w.hdr->med_refills, nref);
         __syncthreads();
