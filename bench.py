@@ -276,31 +276,48 @@ def leg_keys8(sss, torch, chars, offsets, perm, lcp, n, stream, dev, args, world
             "key_bytes": 8, "gpu_launches_per_step": int(st.launches), "rounds": int(st.rounds)}
 
 
-def leg_learned(sss, torch, chars, offsets, perm, lcp, n, stream, dev, args, world, dist):
-    """Learned bucket proposal (fitted CDF, exact verify, tree fallback) on the same workload."""
-    o = sss.sss_get_options()
-    o.graph, o.profile = 0, 0
+def leg_learned(sss, torch, stream, dev, args, world, dist):
+    """Learned bucket proposal (fitted CDF, exact verify, tree fallback) on the
+    64M-string URL workload, beside the plain tree classifier with the same
+    one-word keys on the same input (host-driven rounds both)."""
+    s = gen.workload("url-64m")
+    n = s.n
+    chars = torch.from_numpy(s.chars).to(dev)
+    offsets = torch.from_numpy(s.offsets.view(np.int64)).to(dev)
+    perm = torch.empty(n, dtype=torch.int32, device=dev)
+    lcp = torch.empty(n, dtype=torch.int32, device=dev)
+    saved = sss.sss_get_options()
+    o = sss.sss_options.from_buffer_copy(saved)
+    o.graph, o.profile, o.key_bytes = 0, 0, 8
     sss.sss_set_options(o)
-    fn = lambda: sss.sss_sort_learned(chars, offsets, n, perm, lcp, stream)
-    for _ in range(max(2, args.warmup)):
+    steps = max(3, args.steps // 6)
+    out = {"workload": WORKLOAD_TEXT["url-64m"], "n": n, "chars_bytes": int(s.total)}
+    for name, fn in (("tree", lambda: sss.sss_sort(chars, offsets, n, perm, lcp, stream)),
+                     ("learned", lambda: sss.sss_sort_learned(chars, offsets, n, perm, lcp, stream))):
+        for _ in range(max(2, args.warmup)):
+            fn()
+        ms = _timed(torch, stream, dev, fn, steps, dist)
+        st = sss.sss_get_last_stats()
+        # per-kernel split of one profiled run
+        o.profile = 1
+        sss.sss_set_options(o)
         fn()
-    steps = max(3, args.steps // 4)
-    ms = _timed(torch, stream, dev, fn, steps, dist)
-    st = sss.sss_get_last_stats()
-    # per-kernel split of one profiled run
-    o.profile = 1
-    sss.sss_set_options(o)
-    fn()
-    torch.cuda.synchronize(dev)
-    pst = sss.sss_get_last_stats().as_dict()
-    o.profile = 0
-    sss.sss_set_options(o)
-    prof = pst["profile"] or {}
-    return {"value": n * world / (ms * 1e-3), "unit": "strings/s", "ms_per_step": ms, "steps": steps,
-            "proposals": int(st.learned_keys), "misses": int(st.learned_misses),
-            "miss_rate": (st.learned_misses / st.learned_keys) if st.learned_keys else None,
-            "fit_ms": prof.get("learned", {}).get("ms"), "classify_ms": prof.get("classify", {}).get("ms"),
-            "cdf_segments": int(o.cdf_segments), "cdf_steps": int(o.cdf_steps)}
+        torch.cuda.synchronize(dev)
+        prof = sss.sss_get_last_stats().as_dict()["profile"] or {}
+        o.profile = 0
+        sss.sss_set_options(o)
+        r = {"value": n * world / (ms * 1e-3), "unit": "strings/s", "ms_per_step": ms, "steps": steps,
+             "classify_ms": prof.get("classify", {}).get("ms"), "scatter_ms": prof.get("scatter", {}).get("ms")}
+        if name == "learned":
+            r.update({"proposals": int(st.learned_keys), "misses": int(st.learned_misses),
+                      "miss_rate": (st.learned_misses / st.learned_keys) if st.learned_keys else None,
+                      "fit_ms": prof.get("learned", {}).get("ms"),
+                      "cdf_segments": int(o.cdf_segments), "cdf_steps": int(o.cdf_steps)})
+        out[name] = r
+    sss.sss_set_options(saved)
+    del chars, offsets, perm, lcp
+    torch.cuda.empty_cache()
+    return out
 
 
 def leg_batched(sss, torch, stream, dev, args, world, dist):
@@ -465,7 +482,7 @@ def main():
         extra["graph_form_keys8"] = leg_keys8(sss, torch, chars, offsets, perm, lcp, n, stream, dev, args, world,
                                               dist)
     if "learned" in legs:
-        extra["learned"] = leg_learned(sss, torch, chars, offsets, perm, lcp, n, stream, dev, args, world, dist)
+        extra["learned"] = leg_learned(sss, torch, stream, dev, args, world, dist)
     if "batched" in legs:
         extra["batched"] = leg_batched(sss, torch, stream, dev, args, world, dist)
 

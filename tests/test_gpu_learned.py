@@ -120,3 +120,14 @@ def test_training_lowers_the_miss_rate(kind):
     assert rates[16] < rates[0]
     code, bad = oracle.verify(s.chars, s.offsets, perm, lcp)
     assert code == 0
+
+
+def test_learned_full_size_url_64m_verified():
+    # the 64M-string URL workload the learned proposal is measured on: the
+    # unique answer, every entry checked by the oracle one by one
+    s = gen.workload("url-64m")
+    perm, lcp = _learned_sort(s)
+    st = sss.sss_get_last_stats()
+    assert st.learned_keys > 0 and st.learned_misses < st.learned_keys
+    code, bad = oracle.verify(s.chars, s.offsets, perm, lcp)
+    assert code == 0, (oracle.VERIFY_CODES[code], bad)

@@ -352,3 +352,21 @@ def test_profiled_timeline():
     for i, c in enumerate(sss.K_CLASSES):
         if c != "scan":  # one timed entry covers the scan's three kernels
             assert sum(1 for x in tl if x[0] == c) == st.prof_launches[i], c
+
+
+@pytest.mark.parametrize("key_bytes", [8, 16])
+def test_medium_rounds_step_over_shared_prefixes(key_bytes):
+    # medium-sized groups whose strings share 100+ characters: the per-CTA
+    # round steps over them in place (gathering keys deeper) before it moves
+    rng = random.Random(17)
+    items = []
+    for gi in range(12):
+        prefix = b"group%02d/" % gi + bytes(rng.choice(b"abcdef") for _ in range(100 + 7 * gi))
+        for _ in range(1500 + 97 * gi):
+            items.append(prefix + bytes(rng.choice(b"ab") for _ in range(rng.randint(0, 12))))
+    rng.shuffle(items)
+    s = gen.from_list(items)
+    sss.sss_set_options(base_threshold=32, medium_threshold=8192, k_max=10, chunk=2048, key_bytes=key_bytes)
+    perm, lcp = gpu_sort(s)
+    assert_same(s, perm, lcp)
+    assert sss.sss_get_last_stats().medium_refilled_strings > 0
