@@ -63,8 +63,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle child (no D, no cpu_baseline)")
     ap.add_argument("--n", type=int, default=None,
                     help="sort only the first n strings of the workload's generator (profiling runs)")
-    ap.add_argument("--legs", default="graph,keys8,learned,batched",
-                    help="extra measurements beside the headline: graph,keys8,learned,batched (or none)")
+    ap.add_argument("--legs", default="graph,keys8,equal,learned,batched",
+                    help="extra measurements beside the headline: graph,keys8,equal,learned,batched (or none)")
     return ap.parse_args()
 
 
@@ -276,6 +276,26 @@ def leg_keys8(sss, torch, chars, offsets, perm, lcp, n, stream, dev, args, world
             "key_bytes": 8, "gpu_launches_per_step": int(st.launches), "rounds": int(st.rounds)}
 
 
+def leg_equal(sss, torch, chars, offsets, perm, lcp, n, stream, dev, args, world, dist):
+    """Graph form with the pS5-Equal classifier (equality test at every tree
+    node, early exit) instead of pS5-Unroll."""
+    o = sss.sss_get_options()
+    saved = o.classifier
+    o.graph, o.profile, o.classifier = 1, 0, 1
+    sss.sss_set_options(o)
+    fn = lambda: sss.sss_sort(chars, offsets, n, perm, lcp, stream)
+    for _ in range(max(2, args.warmup)):
+        fn()
+    steps = max(3, args.steps // 2)
+    ms = _timed(torch, stream, dev, fn, steps, dist)
+    st = sss.sss_get_last_stats()
+    o.graph, o.classifier = 0, saved
+    sss.sss_set_options(o)
+    return {"value": n * world / (ms * 1e-3), "unit": "strings/s", "ms_per_step": ms, "steps": steps,
+            "classifier": "pS5-Equal", "key_bytes": int(o.key_bytes), "gpu_launches_per_step": int(st.launches),
+            "rounds": int(st.rounds)}
+
+
 def leg_learned(sss, torch, stream, dev, args, world, dist):
     """Learned bucket proposal (fitted CDF, exact verify, tree fallback) on the
     64M-string URL workload, beside the plain tree classifier with the same
@@ -366,7 +386,8 @@ def leg_batched(sss, torch, stream, dev, args, world, dist):
             "speedup_vs_per_set": ms_ps / ms,
             "tuned": {"k_max": int(best.k_max), "base_threshold": int(best.base_threshold),
                       "medium_threshold": int(best.medium_threshold), "chunk": int(best.chunk),
-                      "key_bytes": int(best.key_bytes), "tuning_ms": tune_ms}}
+                      "key_bytes": int(best.key_bytes), "classifier": int(best.classifier),
+                      "tuning_ms": tune_ms}}
 
 
 # ------------------------------------------------------------------ gpu arm
@@ -480,6 +501,9 @@ def main():
         extra["graph_form"] = leg_graph(sss, torch, chars, offsets, perm, lcp, n, stream, dev, args, world, dist)
     if "keys8" in legs:
         extra["graph_form_keys8"] = leg_keys8(sss, torch, chars, offsets, perm, lcp, n, stream, dev, args, world,
+                                              dist)
+    if "equal" in legs:
+        extra["graph_form_equal"] = leg_equal(sss, torch, chars, offsets, perm, lcp, n, stream, dev, args, world,
                                               dist)
     if "learned" in legs:
         extra["learned"] = leg_learned(sss, torch, stream, dev, args, world, dist)

@@ -56,7 +56,7 @@ typedef enum {
 
 /* Tuning knobs.  Defaults: k_max 10, base_threshold 128, medium_threshold
  * 2048, chunk 32768, seed 0x5eed, cdf_segments 4096, cdf_steps 16,
- * cdf_lr 0.05, profile 0, graph 0, key_bytes 16. */
+ * cdf_lr 0.05, profile 0, graph 0, key_bytes 16, classifier 0. */
 typedef struct sss_options {
     int32_t k_max;             /* largest splitter tree depth k: v = 2^k - 1 splitters, 1..10 */
     uint32_t base_threshold;   /* buckets of at most this many strings go to the base case, 16..128 */
@@ -82,6 +82,12 @@ typedef struct sss_options {
                                 as one 128-bit key: a round steps over up to 16
                                 shared characters).  The learned proposal always
                                 uses 8.  The output does not depend on it. */
+    uint32_t classifier;     /* 0: pS^5-Unroll, equality test against the in-order
+                                splitter after the full descent; 1: pS^5-Equal,
+                                equality test at every node with early exit (both
+                                Sec. 3.1).  The learned proposal always uses 0.  The
+                                output does not depend on it. */
+    uint32_t pad;
 } sss_options;
 
 #define SSS_MAX_ROUNDS_LOGGED 64
@@ -239,6 +245,16 @@ int sss_build_splitters(const uint64_t* sample, uint32_t count, int32_t k,
  * test against the in-order array.  out_bucket (device, uint16 per key). */
 int sss_classify(const uint64_t* keys, uint32_t n, const uint64_t* level, const uint64_t* inorder,
                  int32_t k, uint16_t* out_bucket, void* stream);
+
+/* The same classification by the pS^5-Equal descent of Sec. 3.1: an
+ * equality test at each node of the level-order tree (device, v = 2^k - 1
+ * entries) with early exit; a key equal to node i stops in the equality
+ * bucket of that splitter, whose in-order index follows from i by bit
+ * operations.  With distinct splitters the buckets equal sss_classify's; with
+ * repeated splitters a key equal to them may land in the equality bucket of
+ * another copy (consistently for equal keys).  out_bucket (device, uint16). */
+int sss_classify_equal(const uint64_t* keys, uint32_t n, const uint64_t* level, int32_t k,
+                       uint16_t* out_bucket, void* stream);
 
 /* The learned model's loss and gradient, exposed so the fit can be checked.
  * Model with M pieces on [0,1]: increments softplus(theta_j), normalised

@@ -20,7 +20,8 @@ from . import build as _build
 
 __all__ = [
     "SSSError", "sss_sort", "sss_sort_ws", "sss_sort_noalloc", "sss_sort_host", "sss_sort_batched", "sss_sort_learned",
-    "sss_workspace_size", "sss_gather_keys", "sss_build_splitters", "sss_classify", "sss_cdf_loss_grad",
+    "sss_workspace_size", "sss_gather_keys", "sss_build_splitters", "sss_classify", "sss_classify_equal",
+    "sss_cdf_loss_grad",
     "sss_set_options", "sss_get_options", "sss_get_last_stats", "sss_get_last_timeline", "sss_last_error",
     "sss_release",
     "sss_version", "sss_options", "sss_stats", "load", "lib_path", "sort", "sss_autotune_batched",
@@ -44,7 +45,7 @@ class sss_options(ctypes.Structure):
                 ("medium_threshold", ctypes.c_uint32), ("chunk", ctypes.c_uint32),
                 ("seed", ctypes.c_uint64), ("cdf_segments", ctypes.c_uint32), ("cdf_steps", ctypes.c_uint32),
                 ("cdf_lr", ctypes.c_float), ("profile", ctypes.c_uint32), ("graph", ctypes.c_uint32),
-                ("key_bytes", ctypes.c_uint32)]
+                ("key_bytes", ctypes.c_uint32), ("classifier", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
 
 
 class sss_stats(ctypes.Structure):
@@ -93,6 +94,7 @@ _SIG = {
     "sss_gather_keys": ([_P, _P, _P, _P, ctypes.c_uint32, _P, _P], ctypes.c_int),
     "sss_build_splitters": ([_P, ctypes.c_uint32, ctypes.c_int32, _P, _P, _P], ctypes.c_int),
     "sss_classify": ([_P, ctypes.c_uint32, _P, _P, ctypes.c_int32, _P, _P], ctypes.c_int),
+    "sss_classify_equal": ([_P, ctypes.c_uint32, _P, ctypes.c_int32, _P, _P], ctypes.c_int),
     "sss_cdf_loss_grad": ([_P, ctypes.c_uint32, _P, _P, ctypes.c_uint32, _P, _P, _P], ctypes.c_int),
     "sss_set_options": ([ctypes.POINTER(sss_options)], ctypes.c_int),
     "sss_get_options": ([ctypes.POINTER(sss_options)], ctypes.c_int),
@@ -208,6 +210,10 @@ def sss_build_splitters(sample, count, k, out_level, out_inorder, stream=None):
 def sss_classify(keys, n, level, inorder, k, out_bucket, stream=None):
     _check(load().sss_classify(_addr(keys), n, _addr(level), _addr(inorder), k, _addr(out_bucket),
                                _stream(stream)))
+
+
+def sss_classify_equal(keys, n, level, k, out_bucket, stream=None):
+    _check(load().sss_classify_equal(_addr(keys), n, _addr(level), k, _addr(out_bucket), _stream(stream)))
 
 
 def sss_cdf_loss_grad(theta, M, u, y, S, out_loss, out_grad, stream=None):

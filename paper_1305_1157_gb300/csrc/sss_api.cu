@@ -25,7 +25,7 @@ using namespace sss;
 namespace {
 
 std::mutex g_mu;
-sss_options g_opt = {10, 128u, 2048u, 32768u, 0x5eedull, 4096u, 16u, 0.05f, 0u, 0u, 16u};
+sss_options g_opt = {10, 128u, 2048u, 32768u, 0x5eedull, 4096u, 16u, 0.05f, 0u, 0u, 16u, 0u};
 sss_stats g_stats;
 Prof g_prof;
 std::vector<int> g_tl_cls;       // timeline of the last profiled host-driven call
@@ -216,6 +216,7 @@ int check_options(const sss_options& o) {
     if (o.cdf_segments < 16 || o.cdf_segments > 4096 || (o.cdf_segments & (o.cdf_segments - 1)))
         return fail(SSS_ERR_INVALID, "cdf_segments must be a power of two in 16..4096");
     if (o.key_bytes != 8 && o.key_bytes != 16) return fail(SSS_ERR_INVALID, "key_bytes must be 8 or 16");
+    if (o.classifier > 1) return fail(SSS_ERR_INVALID, "classifier must be 0 (unroll) or 1 (equal)");
     return SSS_OK;
 }
 
@@ -256,7 +257,8 @@ int read_hdr(Hdr* hh, const Work& w, cudaStream_t st) {
 int run_sort(const Work& w, const sss_options& o, const Seg* roots_dev, uint32_t num_roots, Hdr* hh,
              cudaStream_t st, sss_stats* stats, bool learned = false, bool concurrent = true) {
     Params p{learned ? 1 : 0, o.cdf_segments, o.cdf_steps, o.cdf_lr, o.k_max, o.base_threshold,
-             o.medium_threshold, o.chunk, o.seed, device_sms(), learned ? 8u : o.key_bytes};
+             o.medium_threshold, o.chunk, o.seed, device_sms(), learned ? 8u : o.key_bytes,
+             learned ? 0u : o.classifier, 0u};
     Prof* pf = &g_prof;
     pf->reset(o.profile != 0);
     memset(stats, 0, sizeof(*stats));
@@ -445,7 +447,8 @@ int build_graph(const Work& w, const Params& p, const Seg* roots_dev, uint32_t n
 int run_sort_graph(const Work& w, const sss_options& o, const Seg* roots_dev, uint32_t num_roots, Hdr* hh,
                    cudaStream_t st, sss_stats* stats, bool learned, const GraphKey& key) {
     Params p{learned ? 1 : 0, o.cdf_segments, o.cdf_steps, o.cdf_lr, o.k_max, o.base_threshold,
-             o.medium_threshold, o.chunk, o.seed, device_sms(), learned ? 8u : o.key_bytes};
+             o.medium_threshold, o.chunk, o.seed, device_sms(), learned ? 8u : o.key_bytes,
+             learned ? 0u : o.classifier, 0u};
     memset(stats, 0, sizeof(*stats));
     int dev = 0;
     CK(cudaGetDevice(&dev), "cudaGetDevice");
@@ -628,7 +631,18 @@ int sss_classify(const uint64_t* keys, uint32_t n, const uint64_t* level, const 
     if (k < 1 || k > kKMax) return fail(SSS_ERR_INVALID, "k must be in 1..%d", kKMax);
     if (n == 0) return SSS_OK;
     if (!keys || !level || !inorder || !out_bucket) return fail(SSS_ERR_INVALID, "null pointer argument");
-    CK(launch_classify(keys, n, level, inorder, k, out_bucket, (cudaStream_t)stream), "classify");
+    CK(launch_classify(keys, n, level, inorder, k, out_bucket, 0, (cudaStream_t)stream), "classify");
+    return SSS_OK;
+}
+
+int sss_classify_equal(const uint64_t* keys, uint32_t n, const uint64_t* level, int32_t k, uint16_t* out_bucket,
+                       void* stream) {
+    std::lock_guard<std::mutex> g(g_mu);
+    if (k < 1 || k > kKMax) return fail(SSS_ERR_INVALID, "k must be in 1..%d", kKMax);
+    if (n == 0) return SSS_OK;
+    if (!keys || !level || !out_bucket) return fail(SSS_ERR_INVALID, "null pointer argument");
+    // the equality test at every node needs no in-order array
+    CK(launch_classify(keys, n, level, level, k, out_bucket, 1, (cudaStream_t)stream), "classify");
     return SSS_OK;
 }
 
@@ -714,7 +728,8 @@ const char* sss_version(void) { return "sss-gb300 0.1"; }
 //
 // Coordinate descent over the knobs that shape the work: tree depth (v =
 // 2^k - 1 splitters, k = 5..10), base-case threshold, medium threshold, the
-// device-wide work-item size and the key width (8 or 16 characters).  Each candidate is timed as the median of
+// device-wide work-item size, the key width (8 or 16 characters) and the
+// classifier (equality test after the descent or at every node).  Each candidate is timed as the median of
 // three graph-form batched sorts of the caller's tuning batch (after one
 // untimed run that also builds its graph).  The winner is appended to a
 // JSON-lines cache keyed by device and batch shape.
@@ -751,13 +766,14 @@ bool cache_lookup(const char* path, const std::string& key, sss_options& o, doub
     while (fgets(line, sizeof(line), f)) {
         if (strncmp(line, want.c_str(), want.size()) != 0) continue;
         int k = 0;
-        unsigned b = 0, m = 0, c = 0, kb = 0;
+        unsigned b = 0, m = 0, c = 0, kb = 0, cl = 0;
         double t = 0;
         if (sscanf(line + want.size(),
                    " \"k_max\": %d, \"base_threshold\": %u, \"medium_threshold\": %u, \"chunk\": %u, "
-                   "\"key_bytes\": %u, \"ms\": %lf",
-                   &k, &b, &m, &c, &kb, &t) == 6) {
+                   "\"key_bytes\": %u, \"classifier\": %u, \"ms\": %lf",
+                   &k, &b, &m, &c, &kb, &cl, &t) == 7) {
             o.k_max = k; o.base_threshold = b; o.medium_threshold = m; o.chunk = c; o.key_bytes = kb;
+            o.classifier = cl;
             ms = t;
             found = true;  // the last entry for a key wins
         }
@@ -772,8 +788,8 @@ void cache_store(const char* path, const std::string& key, const sss_options& o,
     if (!f) return;
     fprintf(f,
             "{\"key\": \"%s\", \"k_max\": %d, \"base_threshold\": %u, \"medium_threshold\": %u, \"chunk\": %u, "
-            "\"key_bytes\": %u, \"ms\": %.4f}\n",
-            key.c_str(), o.k_max, o.base_threshold, o.medium_threshold, o.chunk, o.key_bytes, ms);
+            "\"key_bytes\": %u, \"classifier\": %u, \"ms\": %.4f}\n",
+            key.c_str(), o.k_max, o.base_threshold, o.medium_threshold, o.chunk, o.key_bytes, o.classifier, ms);
     fclose(f);
 }
 
@@ -827,7 +843,7 @@ extern "C" int sss_autotune_batched(const uint8_t* chars, const uint64_t* offset
     const uint32_t chunks[] = {8192, 16384, 32768, 65536};
     const uint32_t widths[] = {8, 16};
     for (int pass = 0; pass < 2 && rc == SSS_OK; pass++) {
-        for (int knob = 0; knob < 5 && rc == SSS_OK; knob++) {
+        for (int knob = 0; knob < 6 && rc == SSS_OK; knob++) {
             const int count = knob == 0 ? 6 : knob == 1 ? 4 : knob == 2 ? 5 : knob == 3 ? 4 : 2;
             for (int c = 0; c < count && rc == SSS_OK; c++) {
                 sss_options o = best;
@@ -835,7 +851,8 @@ extern "C" int sss_autotune_batched(const uint8_t* chars, const uint64_t* offset
                 else if (knob == 1) o.base_threshold = bases[c];
                 else if (knob == 2) o.medium_threshold = meds[c];
                 else if (knob == 3) o.chunk = chunks[c];
-                else o.key_bytes = widths[c];
+                else if (knob == 4) o.key_bytes = widths[c];
+                else o.classifier = (uint32_t)c;
                 if (o.medium_threshold < o.base_threshold) continue;
                 if (memcmp(&o, &best, sizeof(o)) == 0 || check_options(o) != SSS_OK) continue;
                 double ms = 0.0;

@@ -120,6 +120,8 @@ struct Params {
     uint64_t seed;
     uint32_t num_sms;
     uint32_t key_bytes;       // w: 8 (one key word) or 16 (two words, wide keys)
+    uint32_t equal_test;      // 1: equality test at every tree node (pS^5-Equal)
+    uint32_t pad;
 };
 
 // Views of the workspace and the caller's buffers for one sort.
@@ -409,6 +411,58 @@ __device__ __forceinline__ void classify_keys(const KT (&key)[U], uint32_t (&b)[
     }
 }
 
+// Three-way compare of a key with node i: -1, 0 (equal) or 1.
+__device__ __forceinline__ int node_cmp(uint64_t key, const uint64_t* t, uint32_t i) {
+    const uint64_t x = t[i];
+    return key == x ? 0 : (key > x ? 1 : -1);
+}
+__device__ __forceinline__ int node_cmp(const Key16& key, const SplitTree& t, uint32_t i) {
+    const uint64_t h = t.h[i];
+    if (key.h != h) return key.h > h ? 1 : -1;
+    const uint64_t l = t.l[i];
+    return key.l == l ? 0 : (key.l > l ? 1 : -1);
+}
+
+// The pS^5-Equal classifier (Sec. 3.1, the variant that tests for equality
+// at each node): a key equal to node i of level lv stops there, in the
+// equality bucket of that splitter, whose in-order index comes from the
+// node's position by bit operations; a key that reaches a leaf j without a
+// tie gets the even bucket 2j.  U keys descend level by level.
+template <int U, class KT, class TT>
+__device__ __forceinline__ void classify_keys_equal(const KT (&key)[U], uint32_t (&b)[U], const TT& t, int k) {
+    uint32_t i[U];
+    bool done[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) { i[u] = 1u; done[u] = false; }
+    for (int lv = 0; lv < k; lv++) {
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            if (!done[u]) {
+                const int c = node_cmp(key[u], t, i[u]);
+                if (c == 0) {
+                    const uint32_t q = i[u] - (1u << lv);
+                    b[u] = 2u * ((2u * q + 1u) * (1u << (k - 1 - lv)) - 1u) + 1u;
+                    done[u] = true;
+                } else {
+                    i[u] = 2u * i[u] + (c > 0 ? 1u : 0u);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++)
+        if (!done[u]) b[u] = 2u * (i[u] - (1u << k));
+}
+
+// Either classifier: equality after the full descent (pS^5-Unroll) or at
+// every node (pS^5-Equal).
+template <int U, class KT, class TT>
+__device__ __forceinline__ void classify_keys_by(bool equal_test, const KT (&key)[U], uint32_t (&b)[U], const TT& t,
+                                                 const KT* ino, int k) {
+    if (equal_test) classify_keys_equal<U>(key, b, t, k);
+    else classify_keys<U>(key, b, t, ino, k);
+}
+
 __device__ __forceinline__ uint64_t mix64(uint64_t z) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
@@ -593,7 +647,7 @@ cudaError_t launch_gather_keys(const uint8_t* chars, const uint64_t* offsets, co
 cudaError_t launch_build_splitters(const uint64_t* sample, uint32_t count, int k, uint64_t* lvl,
                                    uint64_t* ino, cudaStream_t st);
 cudaError_t launch_classify(const uint64_t* keys, uint32_t n, const uint64_t* lvl, const uint64_t* ino,
-                            int k, uint16_t* out, cudaStream_t st);
+                            int k, uint16_t* out, int equal_test, cudaStream_t st);
 // learned CDF (sss_learned.cu)
 size_t cdf_fit_smem(uint32_t M);
 cudaError_t launch_cdf_fit(const Work& w, const Params& p, uint32_t grid, Prof* pf, cudaStream_t st);

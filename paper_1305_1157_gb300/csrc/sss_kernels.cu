@@ -436,7 +436,8 @@ constexpr int kClassifyUnroll = 8;
 // uniform over the block.
 template <class KT, class TT>
 __device__ __forceinline__ void classify_range(const Rec* __restrict__ recs, uint32_t lo, uint32_t hi, const TT& t,
-                                               const KT* ino, int k, uint32_t nb, uint32_t* hist, uint16_t* bid) {
+                                               const KT* ino, int k, uint32_t nb, uint32_t* hist, uint16_t* bid,
+                                               bool equal_test) {
     const uint32_t lane = threadIdx.x & 31u;
     for (uint32_t base = lo; base < hi; base += blockDim.x * kClassifyUnroll) {
         KT kk[kClassifyUnroll];
@@ -446,7 +447,7 @@ __device__ __forceinline__ void classify_range(const Rec* __restrict__ recs, uin
             kk[u] = e < hi ? KeyTraits<KT>::load(recs + e) : KeyTraits<KT>::top();
         }
         uint32_t bk[kClassifyUnroll];
-        classify_keys<kClassifyUnroll>(kk, bk, t, ino, k);
+        classify_keys_by<kClassifyUnroll>(equal_test, kk, bk, t, ino, k);
 #pragma unroll
         for (int u = 0; u < kClassifyUnroll; u++) {
             const uint32_t e = base + u * blockDim.x + threadIdx.x;
@@ -529,10 +530,10 @@ __global__ void __launch_bounds__(kClassifyThreads) k_classify(Work w, Params p)
                     atomicAdd(&w.hdr->learned_misses, (unsigned long long)misses);
                 if (threadIdx.x == 0) atomicAdd(&w.hdr->learned_keys, (unsigned long long)(hi - lo));
             } else {
-                classify_range(w.rec[cur], lo, hi, t.view(), ino, k, nb, hist, (uint16_t*)nullptr);
+                classify_range(w.rec[cur], lo, hi, t.view(), ino, k, nb, hist, (uint16_t*)nullptr, p.equal_test != 0);
             }
         } else {
-            classify_range(w.rec[cur], lo, hi, t.view(), ino, k, nb, hist, (uint16_t*)nullptr);
+            classify_range(w.rec[cur], lo, hi, t.view(), ino, k, nb, hist, (uint16_t*)nullptr, p.equal_test != 0);
         }
         __syncthreads();
         for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x)
@@ -572,7 +573,8 @@ __device__ __forceinline__ uint32_t byte_sum_below(uint64_t x, uint32_t below) {
 template <int NBCAP, bool kFromBid, class KT, int ITEMS = kScatterItems, class TT>
 __device__ uint32_t scatter_range(const Work& w, int cur, uint32_t lo, uint32_t hi, uint32_t nb,
                                   ScatterState<NBCAP>& ss, const TT& t, const KT* ino, int k,
-                                  const uint16_t* bid, uint32_t seg_end, uint32_t depth, const float* C = nullptr,
+                                  const uint16_t* bid, uint32_t seg_end, uint32_t depth, bool equal_test,
+                                  const float* C = nullptr,
                                   uint32_t M = 0, uint64_t kmin = 0, float scale = 0.0f) {
     constexpr int kBucketsPerThread = (NBCAP + kScatterThreads) / kScatterThreads;
     static_assert(32 * ITEMS <= 255, "per-warp bucket counts must fit a byte");
@@ -612,7 +614,7 @@ __device__ uint32_t scatter_range(const Work& w, int cur, uint32_t lo, uint32_t 
             KT kk[ITEMS];
 #pragma unroll
             for (int j = 0; j < ITEMS; j++) kk[j] = KeyTraits<KT>::of(rr[j]);
-            classify_keys<ITEMS>(kk, bb, t, ino, k);
+            classify_keys_by<ITEMS>(equal_test, kk, bb, t, ino, k);
 #pragma unroll
             for (int j = 0; j < ITEMS; j++)
                 if (wbase + j * 32u >= hi) bb[j] = nb;
@@ -748,7 +750,8 @@ __global__ void __launch_bounds__(kScatterThreads, SSS_SCATTER_MIN_BLOCKS) k_sca
             C = sm.C;
         }
         const uint32_t nref = scatter_range<kNBMax, false, KT>(w, cur, lo, hi, nb, sm.ss, sm.t.view(), sm.ino, k, nullptr, seg_end,
-                                                           P.depth, C, p.cdf_M, model ? w.cdf_kmin[s] : 0ull,
+                                                           P.depth, p.equal_test != 0, C, p.cdf_M,
+                                                           model ? w.cdf_kmin[s] : 0ull,
                                                            model ? w.cdf_scale[s] : 0.0f);
         add_refills(&w.hdr->refills, nref);
         __syncthreads();
@@ -816,7 +819,8 @@ __global__ void __launch_bounds__(kScatterThreads, SSS_MED_MIN_BLOCKS) k_med_rou
             emit_tree_smem(sm.sel.lvl, k, sm.t, sm.ino);
             // the splitter-choice scratch is dead: the move state takes its place
             for (uint32_t b = threadIdx.x; b <= nb; b += blockDim.x) sm.mv.ss.wcnt[b] = 0ull;
-            classify_range(recs, g.begin, g.begin + m, sm.t.view(), sm.ino, k, nb, sm.hist, sm.mv.bid);
+            classify_range(recs, g.begin, g.begin + m, sm.t.view(), sm.ino, k, nb, sm.hist, sm.mv.bid,
+                           p.equal_test != 0);
             __syncthreads();
             for (uint32_t b = 1u + 2u * threadIdx.x; b < nb; b += 2u * blockDim.x)
                 if (sm.hist[b] == m && !kends(sm.ino[b >> 1])) sm.full = b;
@@ -863,7 +867,7 @@ __global__ void __launch_bounds__(kScatterThreads, SSS_MED_MIN_BLOCKS) k_med_rou
         __syncthreads();
         const uint32_t nref =
             scatter_range<kMedNB, true, KT, kMedItems>(w, cur, g.begin, g.begin + m, nb, sm.mv.ss, sm.t.view(), sm.ino, k,
-                                                       sm.mv.bid, g.begin + m, g.depth);
+                                                       sm.mv.bid, g.begin + m, g.depth, p.equal_test != 0);
         add_refills(&w.hdr->med_refills, nref);
         __syncthreads();
     }
@@ -1630,20 +1634,24 @@ cudaError_t launch_build_splitters(const uint64_t* sample, uint32_t count, int k
 }
 
 __global__ void k_classify_keys(const uint64_t* keys, uint32_t n, const uint64_t* lvl, const uint64_t* inorder,
-                                int k, uint16_t* out) {
+                                int k, uint16_t* out, int equal_test) {
     __shared__ uint64_t t[kVMax + 1];
     __shared__ uint64_t ino[kVMax];
     const uint32_t v = (1u << k) - 1u;
     for (uint32_t i = threadIdx.x; i < v; i += blockDim.x) { t[i + 1] = lvl[i]; ino[i] = inorder[i]; }
     __syncthreads();
     const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-        out[i] = (uint16_t)classify_key(keys[i], t, ino, k);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint64_t key[1] = {keys[i]};
+        uint32_t b[1];
+        classify_keys_by<1>(equal_test != 0, key, b, (const uint64_t*)t, (const uint64_t*)ino, k);
+        out[i] = (uint16_t)b[0];
+    }
 }
 
 cudaError_t launch_classify(const uint64_t* keys, uint32_t n, const uint64_t* lvl, const uint64_t* ino, int k,
-                            uint16_t* out, cudaStream_t st) {
-    if (n) k_classify_keys<<<grid_for(n, 256, 8, device_sms()), 256, 0, st>>>(keys, n, lvl, ino, k, out);
+                            uint16_t* out, int equal_test, cudaStream_t st) {
+    if (n) k_classify_keys<<<grid_for(n, 256, 8, device_sms()), 256, 0, st>>>(keys, n, lvl, ino, k, out, equal_test);
     return cudaGetLastError();
 }
 

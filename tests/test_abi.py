@@ -44,7 +44,7 @@ def test_python_binding_covers_every_symbol():
 def test_options_roundtrip_and_validation(lib):
     o = sss.sss_get_options()
     assert o.k_max == 10 and o.base_threshold == 128 and o.medium_threshold == 2048 and o.chunk == 32768
-    assert o.key_bytes == 16
+    assert o.key_bytes == 16 and o.classifier == 0
     bad = sss.sss_options.from_buffer_copy(o)
     bad.k_max = 11
     with pytest.raises(sss.SSSError) as e:
@@ -64,6 +64,10 @@ def test_options_roundtrip_and_validation(lib):
         sss.sss_set_options(bad)
     bad = sss.sss_options.from_buffer_copy(o)
     bad.key_bytes = 12  # keys are one or two 8-byte words
+    with pytest.raises(sss.SSSError):
+        sss.sss_set_options(bad)
+    bad = sss.sss_options.from_buffer_copy(o)
+    bad.classifier = 2  # pS5-Unroll (0) or pS5-Equal (1)
     with pytest.raises(sss.SSSError):
         sss.sss_set_options(bad)
     sss.sss_set_options(o)

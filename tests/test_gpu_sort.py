@@ -129,6 +129,51 @@ def test_classify_matches_oracle(k):
     assert np.array_equal(got, ref)
 
 
+def _classify_equal_gpu(keys, level, k):
+    kd = torch.from_numpy(keys.view(np.int64)).cuda()
+    ld = torch.from_numpy(level.view(np.int64)).cuda()
+    out = torch.zeros(len(keys), dtype=torch.int16, device="cuda")
+    sss.sss_classify_equal(kd, len(keys), ld, k, out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().view(np.uint16).astype(np.int64)
+
+
+def test_classify_equal_fig1():
+    level = np.array([20, 10, 30], dtype=np.uint64)
+    keys = np.array([0, 9, 10, 11, 19, 20, 21, 29, 30, 31, 2 ** 64 - 1], dtype=np.uint64)
+    assert list(_classify_equal_gpu(keys, level, 2)) == [0, 0, 1, 2, 2, 3, 4, 4, 5, 6, 6]
+
+
+@pytest.mark.parametrize("k", [1, 4, 10])
+def test_classify_equal_matches_oracle(k):
+    # distinct splitters: the pS5-Equal descent gives the oracle's buckets;
+    # repeated splitters: every bucket is a valid one for its key (an odd
+    # bucket holds keys equal to its splitter, an even one keys strictly
+    # between its neighbours) and equal keys share a bucket
+    rng = np.random.default_rng(200 + k)
+    sample = np.unique(rng.integers(0, 2 ** 40, size=4 * 2 ** (k + 1), dtype=np.uint64))
+    sample = rng.permutation(sample)[:2 ** (k + 1) - 1] << np.uint64(20)
+    level, ino = oracle.select_splitters(np.sort(sample), k)
+    keys = np.concatenate([rng.integers(0, 2 ** 60, size=3000, dtype=np.uint64), ino, ino + np.uint64(1)])
+    got = _classify_equal_gpu(keys, level, k)
+    ref = np.array([oracle.classify(int(q), ino) for q in keys])
+    assert np.array_equal(got, ref)
+    dup = rng.integers(0, 20, size=2 ** (k + 1) - 1, dtype=np.uint64) << np.uint64(56)
+    level, ino = oracle.select_splitters(np.sort(dup), k)
+    keys = np.concatenate([rng.integers(0, 21, size=3000, dtype=np.uint64) << np.uint64(56), ino])
+    got = _classify_equal_gpu(keys, level, k)
+    v = len(ino)
+    for q, b in zip(keys.tolist(), got.tolist()):
+        j = b >> 1
+        if b & 1:
+            assert ino[j] == q
+        else:
+            assert (j == 0 or ino[j - 1] < q) and (j == v or q < ino[j])
+    first = {}
+    for q, b in zip(keys.tolist(), got.tolist()):
+        assert first.setdefault(q, b) == b
+
+
 # ------------------------------------------------------------------ whole sort
 
 def test_uniform_100k_full_workload():
@@ -160,6 +205,9 @@ SMALL_OPTS = [
     # as above with two-word keys and one-word keys
     dict(base_threshold=16, medium_threshold=16, k_max=2, chunk=2048, key_bytes=16),
     dict(base_threshold=16, medium_threshold=8192, k_max=10, chunk=2048, key_bytes=8),
+    # the pS5-Equal classifier
+    dict(base_threshold=16, medium_threshold=16, k_max=3, chunk=2048, key_bytes=16, classifier=1),
+    dict(base_threshold=128, medium_threshold=2048, k_max=10, chunk=32768, key_bytes=8, classifier=1),
 ]
 
 
@@ -195,7 +243,8 @@ EDGE_CASES = {
 
 
 @pytest.mark.parametrize("name", sorted(EDGE_CASES))
-@pytest.mark.parametrize("opts", [SMALL_OPTS[0], SMALL_OPTS[1], SMALL_OPTS[3], SMALL_OPTS[4], SMALL_OPTS[5]])
+@pytest.mark.parametrize("opts", [SMALL_OPTS[0], SMALL_OPTS[1], SMALL_OPTS[3], SMALL_OPTS[4], SMALL_OPTS[5],
+                                  SMALL_OPTS[6], SMALL_OPTS[7]])
 def test_edge_cases(name, opts):
     sss.sss_set_options(**opts)
     items = list(EDGE_CASES[name])
@@ -279,12 +328,12 @@ def test_stats_report_rounds():
 
 # ------------------------------------------------------------------ full sizes
 
-@pytest.mark.parametrize("key_bytes", [8, 16])
+@pytest.mark.parametrize("key_bytes,classifier", [(8, 0), (16, 0), (16, 1)])
 @pytest.mark.parametrize("name", ["url-16m", "dna-20m"])
-def test_full_size_workloads_verified(name, key_bytes):
+def test_full_size_workloads_verified(name, key_bytes, classifier):
     # the unique answer: permutation, strict (string, index) order of every
     # adjacent pair and every LCP entry, checked by the oracle one by one
-    sss.sss_set_options(key_bytes=key_bytes)
+    sss.sss_set_options(key_bytes=key_bytes, classifier=classifier)
     s = gen.workload(name)
     perm, lcp = gpu_sort(s)
     code, bad = oracle.verify(s.chars, s.offsets, perm, lcp)
