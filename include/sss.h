@@ -76,7 +76,8 @@ typedef struct sss_options {
     uint32_t graph;          /* 1: run sss_sort / sss_sort_learned as one CUDA graph
                                 whose round loop is a device-side conditional node
                                 (no host round-trip per round; per-round stats not
-                                recorded).  sss_sort_batched always does. */
+                                recorded).  sss_sort_batched always does, unless
+                                profile = 1 asks for timed host-driven rounds. */
     uint32_t key_bytes;      /* w, characters per classification key: 8 (one 64-bit
                                 key word, as in Sec. 3.1) or 16 (two words compared
                                 as one 128-bit key: a round steps over up to 16
@@ -178,7 +179,8 @@ int sss_sort_host(const uint8_t* chars, uint64_t chars_bytes, const uint64_t* of
  * every set is a root segment and all sets advance through the same
  * distribution rounds together; the round loop is a conditional graph node
  * decided on the device, so the call makes one graph launch and one final
- * header readback.  The instantiated graph is cached while the buffers,
+ * header readback (with options.profile = 1 the rounds are host-driven and
+ * timed instead, as for sss_sort).  The instantiated graph is cached while the buffers,
  * sizes and options stay the same.  set_begin (host, num_sets + 1
  * entries, non-decreasing, set_begin[0] = 0, set_begin[num_sets] = n) gives
  * set j the strings with global index in [set_begin[j], set_begin[j+1]).
@@ -192,8 +194,8 @@ int sss_sort_batched(const uint8_t* chars, const uint64_t* offsets, uint32_t n,
 
 /* Autotuner for the batched sort (an addition to the paper): picks the tree
  * depth (v = 2^k - 1 splitters, k = 5..10), the base-case threshold, the
- * medium threshold and the device-wide work-item size ("tile") by coordinate
- * descent, timing graph-form sss_sort_batched runs (median of three, CUDA
+ * medium threshold, the device-wide work-item size ("tile"), the key width
+ * and the classifier by coordinate descent, timing graph-form sss_sort_batched runs (median of three, CUDA
  * events on stream) of the caller's tuning batch -- use a batch of the same
  * shape as the real work but different data.  Arguments as for
  * sss_sort_batched; out_perm/out_lcp (device) receive the last run's output.

@@ -514,7 +514,7 @@ int sort_common(const uint8_t* chars, const uint64_t* offsets, uint32_t n, uint3
         CK(cudaStreamSynchronize(st), "roots upload");
     }
     sss_stats stats;
-    if (g_opt.graph || set_begin) {
+    if (g_opt.graph || (set_begin && !g_opt.profile)) {
         GraphKey key;
         memset(&key, 0, sizeof(key));
         key.chars = chars; key.offsets = offsets; key.perm = perm; key.lcp = lcp; key.ws = ws;

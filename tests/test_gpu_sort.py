@@ -294,7 +294,8 @@ def test_sort_with_caller_workspace():
     assert e.value.code == -2
 
 
-def test_batched_matches_per_set_oracle():
+@pytest.mark.parametrize("profile", [0, 1])  # graph launch / timed host-driven rounds
+def test_batched_matches_per_set_oracle(profile):
     rng = random.Random(8)
     sizes = [0, 1, 2, 3, 17, 1000, 2047, 2048, 2049, 5000, 30000, 1, 0, 777]
     kinds = [rng.choice([1, 2, 3]) for _ in sizes]
@@ -306,7 +307,7 @@ def test_batched_matches_per_set_oracle():
     chars, offsets = to_dev(s)
     perm = torch.full((s.n,), -1, dtype=torch.int32, device="cuda")
     lcp = torch.full((s.n,), -1, dtype=torch.int32, device="cuda")
-    sss.sss_set_options(base_threshold=32, medium_threshold=600, k_max=8, chunk=2048)
+    sss.sss_set_options(base_threshold=32, medium_threshold=600, k_max=8, chunk=2048, profile=profile)
     sss.sss_sort_batched(chars, offsets, s.n, set_begin, len(sizes), perm, lcp)
     torch.cuda.synchronize()
     perm, lcp = u32(perm), u32(lcp)
