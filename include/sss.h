@@ -171,7 +171,9 @@ int sss_sort_noalloc(const uint8_t* chars, const uint64_t* offsets, uint32_t n,
 
 /* As sss_sort with every buffer in host memory: chars (host, chars_bytes
  * long), offsets (host), out_perm and out_lcp (host).  Copies the inputs to
- * the device, sorts, copies the results back and returns after the copy. */
+ * the device, sorts (as one graph launch, unless options.profile = 1),
+ * copies the results back and returns after the copy.  Pinned host buffers
+ * copy fastest. */
 int sss_sort_host(const uint8_t* chars, uint64_t chars_bytes, const uint64_t* offsets,
                   uint32_t n, uint32_t* out_perm, uint32_t* out_lcp);
 

@@ -592,7 +592,12 @@ int sss_sort_host(const uint8_t* chars, uint64_t chars_bytes, const uint64_t* of
     cudaStream_t st = 0;
     CK(cudaMemcpyAsync(d_chars, chars, chars_bytes, cudaMemcpyHostToDevice, st), "chars upload");
     CK(cudaMemcpyAsync(d_off, offsets, 8ull * n, cudaMemcpyHostToDevice, st), "offsets upload");
+    // the sort between the copies runs as one graph launch (no per-round
+    // host round-trip) unless the caller asked for timed host-driven rounds
+    const sss_options saved = g_opt;
+    if (!g_opt.profile) g_opt.graph = 1;
     rc = sort_common(d_chars, d_off, n, d_perm, d_lcp, nullptr, 0, nullptr, 0, st);
+    g_opt = saved;
     if (rc) return rc;
     CK(cudaMemcpyAsync(out_perm, d_perm, 4ull * n, cudaMemcpyDeviceToHost, st), "perm download");
     CK(cudaMemcpyAsync(out_lcp, d_lcp, 4ull * n, cudaMemcpyDeviceToHost, st), "lcp download");

@@ -129,13 +129,16 @@ struct BucketInfo {
 
 template <class KT>
 __device__ __forceinline__ BucketInfo bucket_info(uint32_t b, uint32_t nb, uint32_t depth, const KT* ino,
-                                                  uint32_t size) {
+                                                  uint32_t size, uint32_t base_threshold) {
     BucketInfo bi{depth, 0u, false};
     if (b & 1u) {
         const KT x = ino[b >> 1];
         if (kends(x)) { bi.isrun = true; bi.runlcp = depth + kchars(x); }
         else bi.cdepth = depth + KeyTraits<KT>::kBytes;
-    } else if (b != 0 && b != nb - 1 && size > 0) {
+    } else if (b != 0 && b != nb - 1 && size > base_threshold) {
+        // an inner even bucket that goes to the base case keeps the parent's
+        // depth: its cached keys at that depth still hold the characters
+        // after the shared lcp(x_{i-1}, x_i), so it needs no new gather
         const uint32_t i = b >> 1;
         bi.cdepth = depth + klcp(ino[i - 1], ino[i]);
     }
@@ -730,7 +733,7 @@ __global__ void __launch_bounds__(kScatterThreads, SSS_SCATTER_MIN_BLOCKS) k_sca
                 const uint32_t end = (b + 1 < nb) ? P.begin + (s_next[q] - S0) : seg_end;
                 const uint32_t size = end - start;
                 sm.ss.run_pos[b] = P.begin + (s_mine[q] - S0);
-                const BucketInfo bi = bucket_info(b, nb, P.depth, sm.ino, size);
+                const BucketInfo bi = bucket_info(b, nb, P.depth, sm.ino, size, p.base_threshold);
                 sm.ss.rdep[b] = refill_code(bi, size, P.depth);
                 if (ci == 0 && size > 0) {
                     if (start > P.begin) w.out_lcp[start] = kLcpFlag | P.depth;
@@ -854,7 +857,7 @@ __global__ void __launch_bounds__(kScatterThreads, SSS_MED_MIN_BLOCKS) k_med_rou
             const uint32_t b = threadIdx.x * kPer + q;
             if (b < nb) {
                 const uint32_t size = cnts[q];
-                const BucketInfo bi = bucket_info(b, nb, g.depth, sm.ino, size);
+                const BucketInfo bi = bucket_info(b, nb, g.depth, sm.ino, size, p.base_threshold);
                 sm.mv.ss.run_pos[b] = start;
                 sm.mv.ss.rdep[b] = refill_code(bi, size, g.depth);
                 if (size > 0) {
