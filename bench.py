@@ -63,8 +63,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle child (no D, no cpu_baseline)")
     ap.add_argument("--n", type=int, default=None,
                     help="sort only the first n strings of the workload's generator (profiling runs)")
-    ap.add_argument("--legs", default="graph,keys8,equal,learned,batched",
-                    help="extra measurements beside the headline: graph,keys8,equal,learned,batched (or none)")
+    ap.add_argument("--legs", default="host,keys8,equal,learned,batched,alphabet",
+                    help="extra measurements beside the headline: host,keys8,equal,learned,batched,alphabet "
+                         "(or none)")
     return ap.parse_args()
 
 
@@ -241,17 +242,19 @@ def _timed(torch, stream, dev, fn, steps, dist):
     return ms
 
 
-def leg_graph(sss, torch, chars, offsets, perm, lcp, n, stream, dev, args, world, dist):
-    """The same sort as one CUDA graph (device-side round loop)."""
+def leg_host(sss, torch, chars, offsets, perm, lcp, n, stream, dev, args, world, dist):
+    """The same sort with the rounds driven from the host (one header
+    readback per round, no kernel timing) instead of one graph launch."""
     o = sss.sss_get_options()
-    o.graph, o.profile = 1, 0
+    saved = o.graph
+    o.graph, o.profile = 0, 0
     sss.sss_set_options(o)
     fn = lambda: sss.sss_sort(chars, offsets, n, perm, lcp, stream)
     for _ in range(max(2, args.warmup)):
         fn()
     ms = _timed(torch, stream, dev, fn, args.steps, dist)
     st = sss.sss_get_last_stats()
-    o.graph = 0
+    o.graph = saved
     sss.sss_set_options(o)
     return {"value": n * world / (ms * 1e-3), "unit": "strings/s", "ms_per_step": ms, "steps": args.steps,
             "gpu_launches_per_step": int(st.launches), "rounds": int(st.rounds)}
@@ -334,6 +337,44 @@ def leg_learned(sss, torch, stream, dev, args, world, dist):
                       "fit_ms": prof.get("learned", {}).get("ms"),
                       "cdf_segments": int(o.cdf_segments), "cdf_steps": int(o.cdf_steps)})
         out[name] = r
+    sss.sss_set_options(saved)
+    del chars, offsets, perm, lcp
+    torch.cuda.empty_cache()
+    return out
+
+
+def leg_alphabet(sss, torch, stream, dev, args, world, dist):
+    """Alphabet compression (App. A.2) on the 20M-string DNA workload: graph
+    form with the strings rewritten 3 characters per byte (sigma' = 4) beside
+    the same sort on the plain strings."""
+    s = gen.workload("dna-20m")
+    n = s.n
+    chars = torch.from_numpy(s.chars).to(dev)
+    offsets = torch.from_numpy(s.offsets.view(np.int64)).to(dev)
+    perm = torch.empty(n, dtype=torch.int32, device=dev)
+    lcp = torch.empty(n, dtype=torch.int32, device=dev)
+    saved = sss.sss_get_options()
+    o = sss.sss_options.from_buffer_copy(saved)
+    steps = max(3, args.steps // 4)
+    out = {"workload": WORKLOAD_TEXT["dna-20m"], "n": n, "chars_bytes": int(s.total)}
+    fn = lambda: sss.sss_sort(chars, offsets, n, perm, lcp, stream)
+    for name, alpha in (("plain", 0), ("compressed", 1)):
+        o.graph, o.profile, o.alphabet = 1, 0, alpha
+        sss.sss_set_options(o)
+        for _ in range(max(2, args.warmup)):
+            fn()
+        ms = _timed(torch, stream, dev, fn, steps, dist)
+        st = sss.sss_get_last_stats()
+        # per-kernel split of one profiled (host-driven) run
+        o.graph, o.profile = 0, 1
+        sss.sss_set_options(o)
+        fn()
+        torch.cuda.synchronize(dev)
+        prof = sss.sss_get_last_stats().as_dict()["profile"] or {}
+        out[name] = {"value": n * world / (ms * 1e-3), "unit": "strings/s", "ms_per_step": ms, "steps": steps,
+                     "rounds": int(st.rounds), "gpu_launches_per_step": int(st.launches),
+                     "alphabet_symbols": int(st.alphabet_symbols), "chars_per_byte": max(1, int(st.alphabet_group)),
+                     "profiled_ms": {k: round(v["ms"], 4) for k, v in prof.items() if v["launches"]}}
     sss.sss_set_options(saved)
     del chars, offsets, perm, lcp
     torch.cuda.empty_cache()
@@ -426,20 +467,16 @@ def main():
     stream = torch.cuda.current_stream(dev)
     sort_fn = sss.sss_sort_learned if args.mode == "learned" else sss.sss_sort
 
+    # the headline form: each sort is one launch of the library's cached CUDA
+    # graph (device-side round loop, no host round-trip per round)
     opts = sss.sss_get_options()
-    opts.profile = 0
+    opts.profile, opts.graph = 0, 1
     sss.sss_set_options(opts)
     for _ in range(args.warmup):
         sort_fn(chars, offsets, n, perm, lcp, stream)
     torch.cuda.synchronize(dev)
 
-    # timed region: library kernel timing on (CUDA events on the sort's stream)
-    opts.profile = 1
-    sss.sss_set_options(opts)
-    prof_ms = np.zeros(len(sss.K_CLASSES))
-    prof_launches = np.zeros(len(sss.K_CLASSES), dtype=np.int64)
     launches = 0
-    large_strings = large_refills = medium_strings = medium_refills = base_strings = 0
     clocks = ClockSampler(visible_gpu(local_rank))
     if dist:
         dist.barrier()
@@ -451,8 +488,33 @@ def main():
     t_start.record(stream)
     for _ in range(args.steps):
         sort_fn(chars, offsets, n, perm, lcp, stream)
+        launches += sss.sss_get_last_stats().launches
+    t_end.record(stream)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    ms = t_start.elapsed_time(t_end) / args.steps
+    if dist:
+        tt = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+
+    # second timed region, per-kernel times: the same sorts with the rounds
+    # driven from the host and CUDA events around every kernel launch on the
+    # stream it runs on (the roofline and the kernel split come from here)
+    opts.graph, opts.profile = 0, 1
+    sss.sss_set_options(opts)
+    prof_ms = np.zeros(len(sss.K_CLASSES))
+    prof_launches = np.zeros(len(sss.K_CLASSES), dtype=np.int64)
+    large_strings = large_refills = medium_strings = medium_refills = base_strings = 0
+    sort_fn(chars, offsets, n, perm, lcp, stream)  # warm the host-driven form
+    torch.cuda.synchronize(dev)
+    p_start = torch.cuda.Event(enable_timing=True)
+    p_end = torch.cuda.Event(enable_timing=True)
+    p_start.record(stream)
+    for _ in range(args.steps):
+        sort_fn(chars, offsets, n, perm, lcp, stream)
         st = sss.sss_get_last_stats()
-        launches += st.launches
         prof_ms += np.array(list(st.prof_ms))
         prof_launches += np.array(list(st.prof_launches))
         large_strings += st.round_strings - st.medium_strings
@@ -461,16 +523,10 @@ def main():
         medium_refills += st.medium_refilled_strings
         base_strings += st.base_strings
         last_stats = st.as_dict()
-    t_end.record(stream)
+    p_end.record(stream)
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
-    if dist:
-        dist.barrier()
-    ms = t_start.elapsed_time(t_end) / args.steps
-    if dist:
-        tt = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms_profiled = p_start.elapsed_time(p_end) / args.steps
     opts.profile = 0
     sss.sss_set_options(opts)
 
@@ -497,8 +553,9 @@ def main():
 
     legs = set(x for x in args.legs.split(",") if x and x != "none")
     extra = {}
-    if "graph" in legs:
-        extra["graph_form"] = leg_graph(sss, torch, chars, offsets, perm, lcp, n, stream, dev, args, world, dist)
+    if "host" in legs:
+        extra["host_driven_form"] = leg_host(sss, torch, chars, offsets, perm, lcp, n, stream, dev, args, world,
+                                             dist)
     if "keys8" in legs:
         extra["graph_form_keys8"] = leg_keys8(sss, torch, chars, offsets, perm, lcp, n, stream, dev, args, world,
                                               dist)
@@ -509,6 +566,8 @@ def main():
         extra["learned"] = leg_learned(sss, torch, stream, dev, args, world, dist)
     if "batched" in legs:
         extra["batched"] = leg_batched(sss, torch, stream, dev, args, world, dist)
+    if "alphabet" in legs:
+        extra["alphabet"] = leg_alphabet(sss, torch, stream, dev, args, world, dist)
 
     if rank != 0:
         if dist:
@@ -571,7 +630,7 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": args.workload, "description": WORKLOAD_TEXT.get(args.workload, ""),
-                   "mode": args.mode, "key_bytes": int(opts.key_bytes), "n": n, "chars_bytes": int(s.total),
+                   "mode": args.mode, "form": "graph", "key_bytes": int(opts.key_bytes), "n": n, "chars_bytes": int(s.total),
                    "D": D, "D_over_N": (D / s.total) if D else None,
                    "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
         "d_bytes_per_s": (D * world / (ms * 1e-3)) if D else None,
@@ -584,6 +643,8 @@ def main():
         "clocks": clk,
         "gpu_launches": int(launches),
         "kernels": kernel_share,
+        "profiled_pass": {"form": "host-driven rounds, CUDA events around every launch", "steps": args.steps,
+                          "ms_per_step": ms_profiled},
         "sort_stats": {k: last_stats[k] for k in ("rounds", "base_tiles", "round_strings", "medium_strings",
                                                   "base_strings", "refilled_strings", "medium_refilled_strings",
                                                   "learned_keys", "learned_misses")},

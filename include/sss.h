@@ -88,7 +88,16 @@ typedef struct sss_options {
                                 equality test at every node with early exit (both
                                 Sec. 3.1).  The learned proposal always uses 0.  The
                                 output does not depend on it. */
-    uint32_t pad;
+    uint32_t alphabet;       /* 1: alphabet compression (App. A.2, "Practical Refinements"):
+                                when only sigma' <= 15 distinct characters occur, each
+                                string is first rewritten with g = floor(log_{sigma'+1}
+                                256) characters per byte, as base-(sigma'+1) digits in
+                                rank order (the terminator is digit 0), the rewritten
+                                strings are sorted, and the LCP array is converted back
+                                to characters.  DNA (sigma' = 4) gets g = 3.  Uses
+                                library-managed memory: sss_sort_ws and
+                                sss_sort_noalloc ignore it.  0: off.  The output does
+                                not depend on it. */
 } sss_options;
 
 #define SSS_MAX_ROUNDS_LOGGED 64
@@ -106,7 +115,8 @@ enum {
     SSS_K_FIXUP = 8,    /* LCP at bucket boundaries, batched index rebasing */
     SSS_K_LEARNED = 9,  /* learned CDF fit and proposal */
     SSS_K_MEDIUM = 10,  /* one CTA per medium bucket: a whole round in shared memory */
-    SSS_K_CLASSES = 11
+    SSS_K_ALPHABET = 11, /* alphabet compression: character scan, packing, LCP conversion */
+    SSS_K_CLASSES = 12
 };
 
 /* Statistics of the last successful sort call. */
@@ -129,6 +139,11 @@ typedef struct sss_stats {
     double prof_ms[SSS_K_CLASSES];   /* summed device time per kernel class (ms) */
     uint32_t round_segments[SSS_MAX_ROUNDS_LOGGED]; /* large + medium segments per round */
     uint32_t round_active[SSS_MAX_ROUNDS_LOGGED];   /* strings distributed per round */
+    uint32_t alphabet_symbols;       /* sigma': distinct non-terminator characters seen
+                                        (alphabet option on), else 0 */
+    uint32_t alphabet_group;         /* characters packed per byte: g >= 2 when the strings
+                                        were rewritten, 1 when the alphabet was too large,
+                                        0 when the option is off */
 } sss_stats;
 
 /* ---------------------------------------------------------------- sort */

@@ -31,7 +31,7 @@ STATUS = {0: "SSS_OK", -1: "SSS_ERR_INVALID", -2: "SSS_ERR_NOMEM", -3: "SSS_ERR_
           -4: "SSS_ERR_TIMEOUT", -5: "SSS_ERR_TOO_LARGE", -6: "SSS_ERR_INTERNAL"}
 MAX_ROUNDS_LOGGED = 64
 K_CLASSES = ["init", "sample", "classify", "scan", "scatter", "plan", "base", "runs", "fixup", "learned",
-             "medium"]
+             "medium", "alphabet"]
 
 
 class SSSError(RuntimeError):
@@ -45,7 +45,7 @@ class sss_options(ctypes.Structure):
                 ("medium_threshold", ctypes.c_uint32), ("chunk", ctypes.c_uint32),
                 ("seed", ctypes.c_uint64), ("cdf_segments", ctypes.c_uint32), ("cdf_steps", ctypes.c_uint32),
                 ("cdf_lr", ctypes.c_float), ("profile", ctypes.c_uint32), ("graph", ctypes.c_uint32),
-                ("key_bytes", ctypes.c_uint32), ("classifier", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
+                ("key_bytes", ctypes.c_uint32), ("classifier", ctypes.c_uint32), ("alphabet", ctypes.c_uint32)]
 
 
 class sss_stats(ctypes.Structure):
@@ -60,7 +60,8 @@ class sss_stats(ctypes.Structure):
                 ("prof_launches", ctypes.c_uint32 * len(K_CLASSES)),
                 ("prof_ms", ctypes.c_double * len(K_CLASSES)),
                 ("round_segments", ctypes.c_uint32 * MAX_ROUNDS_LOGGED),
-                ("round_active", ctypes.c_uint32 * MAX_ROUNDS_LOGGED)]
+                ("round_active", ctypes.c_uint32 * MAX_ROUNDS_LOGGED),
+                ("alphabet_symbols", ctypes.c_uint32), ("alphabet_group", ctypes.c_uint32)]
 
     def as_dict(self):
         r = self.rounds
@@ -74,7 +75,8 @@ class sss_stats(ctypes.Structure):
                 "profile": ({K_CLASSES[i]: {"launches": self.prof_launches[i], "ms": self.prof_ms[i]}
                              for i in range(len(K_CLASSES))} if self.profiled else None),
                 "round_segments": list(self.round_segments)[:min(r, MAX_ROUNDS_LOGGED)],
-                "round_active": list(self.round_active)[:min(r, MAX_ROUNDS_LOGGED)]}
+                "round_active": list(self.round_active)[:min(r, MAX_ROUNDS_LOGGED)],
+                "alphabet_symbols": self.alphabet_symbols, "alphabet_group": self.alphabet_group}
 
 
 _lib = None

@@ -25,7 +25,7 @@ using namespace sss;
 namespace {
 
 std::mutex g_mu;
-sss_options g_opt = {10, 128u, 2048u, 32768u, 0x5eedull, 4096u, 16u, 0.05f, 0u, 0u, 16u, 0u};
+sss_options g_opt = {10, 128u, 2048u, 32768u, 0x5eedull, 4096u, 16u, 0.05f, 0u, 0u, 16u, 0u, 0u};
 sss_stats g_stats;
 Prof g_prof;
 std::vector<int> g_tl_cls;       // timeline of the last profiled host-driven call
@@ -40,6 +40,11 @@ struct DevPool {
     Hdr* hh = nullptr;  // pinned host copy of the device header
     void* io = nullptr; // device buffers of sss_sort_host
     size_t io_bytes = 0;
+    void* alpha_scan = nullptr;  // alphabet compression: header + string lengths
+    size_t alpha_scan_bytes = 0;
+    void* alpha_pack = nullptr;  // alphabet compression: packed offsets + packed strings
+    size_t alpha_pack_bytes = 0;
+    AlphaHdr* ah_host = nullptr; // pinned host copy of the alphabet header
 };
 DevPool g_pool[kMaxDevices];
 Branches g_branches[kMaxDevices];  // concurrent round-body branches, created on first use
@@ -217,6 +222,7 @@ int check_options(const sss_options& o) {
         return fail(SSS_ERR_INVALID, "cdf_segments must be a power of two in 16..4096");
     if (o.key_bytes != 8 && o.key_bytes != 16) return fail(SSS_ERR_INVALID, "key_bytes must be 8 or 16");
     if (o.classifier > 1) return fail(SSS_ERR_INVALID, "classifier must be 0 (unroll) or 1 (equal)");
+    if (o.alphabet > 1) return fail(SSS_ERR_INVALID, "alphabet must be 0 (off) or 1 (compress small alphabets)");
     return SSS_OK;
 }
 
@@ -242,6 +248,116 @@ int pool_reserve(DevPool& P, size_t bytes) {
     return SSS_OK;
 }
 
+// Grow-only device buffer.
+int grow_buffer(void** buf, size_t* have, size_t need, const char* what) {
+    if (*have >= need) return SSS_OK;
+    if (*buf) { cudaFree(*buf); *buf = nullptr; *have = 0; }
+    cudaError_t e = cudaMalloc(buf, need);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SSS_ERR_NOMEM, "cudaMalloc of %zu %s bytes failed: %s", need, what, cudaGetErrorString(e));
+    }
+    *have = need;
+    return SSS_OK;
+}
+
+// Alphabet compression of one call (App. A.2): the alphabet from a sample
+// of the strings, the packed copy the sort then runs on (when g >= 2), and
+// the exact scan over all strings only when the packing pass finds a
+// character the sample missed or outgrows the estimated buffer.
+struct AlphaRun {
+    bool on = false;
+    uint32_t sigma = 0, g = 0, launches = 0;
+    const uint8_t* chars = nullptr;
+    const uint64_t* off = nullptr;
+    const uint32_t* len = nullptr;
+    AlphaHdr* ah = nullptr;
+};
+
+constexpr uint32_t kAlphaSample = 16384;  // strings of the sampled scan
+
+int alpha_readback(DevPool& P, AlphaHdr* ah, cudaStream_t st) {
+    CK(cudaMemcpyAsync(P.ah_host, ah, sizeof(AlphaHdr), cudaMemcpyDeviceToHost, st), "alphabet readback");
+    CK(cudaStreamSynchronize(st), "alphabet pass");
+    return SSS_OK;
+}
+
+uint32_t alpha_sigma(const AlphaHdr& h) {
+    uint32_t sigma = 0;
+    for (int j = 0; j < 8; j++) sigma += (uint32_t)__builtin_popcount(h.present[j]);
+    return sigma;
+}
+
+// Packs with ah->present as the alphabet into a buffer of `capacity` bytes;
+// *flags: the pass's kAlphaMiss / kAlphaFull.
+int alpha_pack(DevPool& P, const uint8_t* chars, const uint64_t* offsets, uint32_t n, uint32_t g, uint32_t sigma,
+               uint64_t capacity, Prof* pf, cudaStream_t st, AlphaRun* ar, uint32_t* flags) {
+    const size_t b_off = align_up(8ull * n, 256);
+    // 64 bytes of slack after the last string for the 8-byte key-word reads
+    int rc = grow_buffer(&P.alpha_pack, &P.alpha_pack_bytes, b_off + align_up(capacity + 64, 256), "alphabet pack");
+    if (rc) return rc;
+    uint64_t* off2 = (uint64_t*)P.alpha_pack;
+    uint8_t* chars2 = (uint8_t*)P.alpha_pack + b_off;
+    CK(cudaMemsetAsync(&ar->ah->flags, 0, sizeof(uint32_t), st), "alphabet flags reset");
+    CK(cudaMemsetAsync(&ar->ah->cursor, 0, sizeof(unsigned long long), st), "alphabet cursor reset");
+    CK(launch_alpha_pack(chars, offsets, n, g, sigma, ar->ah, chars2, capacity, off2, (uint32_t*)ar->len, pf, st),
+       "alphabet pack");
+    ar->launches++;
+    rc = alpha_readback(P, ar->ah, st);
+    if (rc) return rc;
+    *flags = P.ah_host->flags;
+    ar->chars = chars2;
+    ar->off = off2;
+    return SSS_OK;
+}
+
+int alpha_prologue(DevPool& P, const uint8_t* chars, const uint64_t* offsets, uint32_t n, Prof* pf,
+                   cudaStream_t st, AlphaRun* ar) {
+    ar->on = true;
+    if (!P.ah_host) CK(cudaMallocHost((void**)&P.ah_host, sizeof(AlphaHdr)), "cudaMallocHost(alphabet header)");
+    const size_t b_hdr = align_up(sizeof(AlphaHdr), 256), b_len = align_up(4ull * n, 256);
+    int rc = grow_buffer(&P.alpha_scan, &P.alpha_scan_bytes, b_hdr + b_len, "alphabet scan");
+    if (rc) return rc;
+    ar->ah = (AlphaHdr*)P.alpha_scan;
+    ar->len = (const uint32_t*)((char*)P.alpha_scan + b_hdr);
+    // 1. the alphabet and mean length of a sample
+    const uint32_t step = n > kAlphaSample ? n / kAlphaSample : 1u;
+    CK(cudaMemsetAsync(ar->ah, 0, sizeof(AlphaHdr), st), "alphabet header reset");
+    CK(launch_alpha_scan(chars, offsets, n, step, ar->ah, pf, st), "alphabet scan");
+    ar->launches++;
+    rc = alpha_readback(P, ar->ah, st);
+    if (rc) return rc;
+    ar->sigma = alpha_sigma(*P.ah_host);
+    ar->g = alpha_group(ar->sigma);  // sigma' of the sample >= 16: so is the whole input's
+    if (ar->g < 2) return SSS_OK;
+    // 2. pack into a buffer sized from the sample's mean length
+    const double mean = P.ah_host->strings ? (double)P.ah_host->chars / P.ah_host->strings : 0.0;
+    const uint64_t per = (uint64_t)((1.25 * mean + 8.0) / ar->g) + 16u;
+    uint64_t capacity = (uint64_t)n * per;
+    const size_t b_off = align_up(8ull * n, 256);
+    if (P.alpha_pack_bytes > b_off + 320 && P.alpha_pack_bytes - b_off - 320 > capacity)
+        capacity = P.alpha_pack_bytes - b_off - 320;  // reuse a larger buffer as it is
+    uint32_t flags = 0;
+    rc = alpha_pack(P, chars, offsets, n, ar->g, ar->sigma, capacity, pf, st, ar, &flags);
+    if (rc || !flags) return rc;
+    // 3. the sample missed a character or the estimate was short: the exact
+    // alphabet and sizes of all strings, then pack again
+    CK(cudaMemsetAsync(ar->ah, 0, sizeof(AlphaHdr), st), "alphabet header reset");
+    CK(launch_alpha_scan(chars, offsets, n, 1u, ar->ah, pf, st), "alphabet scan");
+    ar->launches++;
+    rc = alpha_readback(P, ar->ah, st);
+    if (rc) return rc;
+    ar->sigma = alpha_sigma(*P.ah_host);
+    ar->g = alpha_group(ar->sigma);
+    ar->chars = nullptr;
+    ar->off = nullptr;
+    if (ar->g < 2) return SSS_OK;
+    rc = alpha_pack(P, chars, offsets, n, ar->g, ar->sigma, P.ah_host->total[ar->g - 1], pf, st, ar, &flags);
+    if (rc) return rc;
+    if (flags) return fail(SSS_ERR_INTERNAL, "alphabet packing failed after the exact scan (flags 0x%x)", flags);
+    return SSS_OK;
+}
+
 int read_hdr(Hdr* hh, const Work& w, cudaStream_t st) {
     CK(cudaMemcpyAsync(hh, w.hdr, sizeof(Hdr), cudaMemcpyDeviceToHost, st), "header readback");
     CK(cudaStreamSynchronize(st), "round");
@@ -255,12 +371,13 @@ int read_hdr(Hdr* hh, const Work& w, cudaStream_t st) {
 // device-wide round and the medium rounds as concurrent branches (br), or
 // one after the other on st (br null).
 int run_sort(const Work& w, const sss_options& o, const Seg* roots_dev, uint32_t num_roots, Hdr* hh,
-             cudaStream_t st, sss_stats* stats, bool learned = false, bool concurrent = true) {
+             cudaStream_t st, sss_stats* stats, bool learned = false, bool concurrent = true,
+             bool reset_prof = true) {
     Params p{learned ? 1 : 0, o.cdf_segments, o.cdf_steps, o.cdf_lr, o.k_max, o.base_threshold,
              o.medium_threshold, o.chunk, o.seed, device_sms(), learned ? 8u : o.key_bytes,
              learned ? 0u : o.classifier, 0u};
     Prof* pf = &g_prof;
-    pf->reset(o.profile != 0);
+    if (reset_prof) pf->reset(o.profile != 0);
     memset(stats, 0, sizeof(*stats));
     CK(prepare_kernels(o.cdf_segments), "kernel attributes");
     CK(launch_init(w, pf, st), "init");
@@ -326,8 +443,8 @@ int run_sort(const Work& w, const sss_options& o, const Seg* roots_dev, uint32_t
 // per device and reused while the call's buffers and options are unchanged.
 
 struct GraphKey {
-    const void *chars, *offsets, *perm, *lcp, *ws, *roots;
-    uint32_t n, num_roots;
+    const void *chars, *offsets, *perm, *lcp, *ws, *roots, *alpha_dig, *alpha_len;
+    uint32_t n, num_roots, alpha_g;
     sss_options opt;
     int learned;
     bool operator==(const GraphKey& o) const { return memcmp(this, &o, sizeof(GraphKey)) == 0; }
@@ -488,6 +605,16 @@ int sort_common(const uint8_t* chars, const uint64_t* offsets, uint32_t n, uint3
     DevPool* P = nullptr;
     rc = get_pool(&P);
     if (rc) return rc;
+    g_prof.reset(g_opt.profile != 0);
+    AlphaRun ar;
+    if (g_opt.alphabet && !ws_user) {
+        rc = alpha_prologue(*P, chars, offsets, n, &g_prof, st, &ar);
+        if (rc) return rc;
+        if (ar.g >= 2) {  // sort the packed copy instead
+            chars = ar.chars;
+            offsets = ar.off;
+        }
+    }
     const Layout L = layout_for(n, g_opt, num_sets, learned);
     char* ws;
     if (ws_user) {
@@ -501,6 +628,11 @@ int sort_common(const uint8_t* chars, const uint64_t* offsets, uint32_t n, uint3
         ws = (char*)P->ws;
     }
     Work w = make_work(L, ws, chars, offsets, n, perm, lcp);
+    if (ar.g >= 2) {  // LCP entries in characters of the original strings
+        w.alpha_g = ar.g;
+        w.alpha_dig = ar.ah->dig;
+        w.alpha_len = ar.len;
+    }
     Seg* roots_dev = nullptr;
     if (set_begin) {
         std::vector<Seg> roots(num_sets);
@@ -519,12 +651,18 @@ int sort_common(const uint8_t* chars, const uint64_t* offsets, uint32_t n, uint3
         memset(&key, 0, sizeof(key));
         key.chars = chars; key.offsets = offsets; key.perm = perm; key.lcp = lcp; key.ws = ws;
         key.roots = roots_dev; key.n = n; key.num_roots = num_sets; key.opt = g_opt; key.learned = learned;
+        key.alpha_g = w.alpha_g; key.alpha_dig = w.alpha_dig; key.alpha_len = w.alpha_len;
         key.opt.profile = 0;
         rc = run_sort_graph(w, g_opt, roots_dev, num_sets, P->hh, st, &stats, learned, key);
+        stats.launches += ar.launches;
     } else {
-        rc = run_sort(w, g_opt, roots_dev, num_sets, P->hh, st, &stats, learned);
+        rc = run_sort(w, g_opt, roots_dev, num_sets, P->hh, st, &stats, learned, true, false);
     }
     if (rc) return rc;
+    if (ar.on) {
+        stats.alphabet_symbols = ar.sigma;
+        stats.alphabet_group = ar.g >= 2 ? ar.g : 1u;
+    }
     g_stats = stats;
     return SSS_OK;
 }

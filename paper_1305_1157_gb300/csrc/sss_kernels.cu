@@ -1031,10 +1031,10 @@ __global__ void __launch_bounds__(kBaseThreads) k_base(Work w, Params p) {
                 const KT pk = base_key<KT>(sm.K[s - 1], sm.K2[s - 1]);
                 const KT ck = base_key<KT>(k, k2);
                 if (!keq(pk, ck)) {
-                    w.out_lcp[G] = dold + klcp(pk, ck);
+                    w.out_lcp[G] = lcp_of_keys(w, dold, pk, ck);
                 } else {
                     head = false;
-                    if (kends(ck)) w.out_lcp[G] = dold + kchars(ck);
+                    if (kends(ck)) w.out_lcp[G] = lcp_of_equal(w, dold + kchars(ck), id);
                 }
             }
         }
@@ -1170,10 +1170,10 @@ __global__ void __launch_bounds__(32 * kTinyWarps) k_tiny(Work w, Params p) {
             if (act && lane != rs) {
                 const KT pkk = base_key<KT>(pk, pk2);
                 if (!keq(pkk, ck)) {
-                    w.out_lcp[G] = d + klcp(pkk, ck);
+                    w.out_lcp[G] = lcp_of_keys(w, d, pkk, ck);
                 } else {
                     head = false;
-                    if (kends(ck)) w.out_lcp[G] = d + kchars(ck);
+                    if (kends(ck)) w.out_lcp[G] = lcp_of_equal(w, d + kchars(ck), id);
                 }
             }
             // groups of equal keys: [highest head <= lane, next head above lane)
@@ -1205,10 +1205,12 @@ __global__ void k_bigrun(Work w) {
     __shared__ uint32_t s_item;
     for (uint32_t r = first_item(); r < nrun; r = next_item(&w.hdr->q_bigrun, &s_item)) {
         const Seg g = w.bigrun[buf][r];
+        // equal strings: their common length
+        const uint32_t runlcp = lcp_of_equal(w, g.aux, w.rec[buf][g.begin].idx);
         for (uint32_t i = threadIdx.x; i < g.size; i += blockDim.x) {
             const uint32_t q = g.begin + i;
             w.out_perm[q] = w.rec[buf][q].idx;
-            if (i > 0) w.out_lcp[q] = g.aux;
+            if (i > 0) w.out_lcp[q] = runlcp;
         }
     }
 }
@@ -1234,7 +1236,7 @@ __global__ void k_fixup(Work w) {
             load_key2(w.chars, w.offsets[pa] + l, a.h, a.l);
             load_key2(w.chars, w.offsets[pb] + l, b.h, b.l);
             if (keq(a, b)) atomicOr(&w.hdr->err, kErrEqualBoundary);
-            w.out_lcp[q] = l + klcp(a, b);
+            w.out_lcp[q] = lcp_of_keys(w, l, a, b);
         }
     }
 }

@@ -70,6 +70,11 @@ def test_options_roundtrip_and_validation(lib):
     bad.classifier = 2  # pS5-Unroll (0) or pS5-Equal (1)
     with pytest.raises(sss.SSSError):
         sss.sss_set_options(bad)
+    assert o.alphabet == 0  # alphabet compression is off by default
+    bad = sss.sss_options.from_buffer_copy(o)
+    bad.alphabet = 2  # off (0) or on (1)
+    with pytest.raises(sss.SSSError):
+        sss.sss_set_options(bad)
     sss.sss_set_options(o)
     assert sss.sss_get_options().k_max == 10
 
