@@ -26,7 +26,7 @@
 // packs and checks every character against the sampled alphabet.  Only if a
 // character was missing from the sample (or the estimated buffer was too
 // small) does the host run the exact scan over all strings and pack again.
-#include "sss_internal.cuh"
+#include "sss_alphabet.cuh"
 
 namespace sss {
 

@@ -19,6 +19,7 @@
 
 #include "../../include/sss.h"
 #include "sss_internal.cuh"
+#include "sss_alphabet.cuh"
 
 using namespace sss;
 
