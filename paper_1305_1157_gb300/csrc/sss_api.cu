@@ -129,7 +129,7 @@ Layout layout_for(uint32_t n, const sss_options& o, uint32_t num_roots, bool lea
     // threshold allows any), warp-form ones at least 2
     const uint64_t smax = (T > kTinyMax ? nn / (kTinyMax + 1) : 0) + num_roots + 2;
     const uint64_t ymax = nn / 2 + num_roots + 2;
-    const uint64_t bmax = nn / (T + 1) + 2;
+    const uint64_t bmax = nn / (T + 1) + nn / kRunPiece + 2;  // runs > T strings, in pieces
     const uint64_t scan_tmp = scan_tmp_elems((uint32_t)(cmax > smax ? cmax : smax)) + 1;
     L.cmax = (uint32_t)cmax; L.tmax = (uint32_t)tmax; L.lmax = (uint32_t)lmax; L.chmax = (uint32_t)chmax;
     L.smax = (uint32_t)smax; L.ymax = (uint32_t)ymax; L.bmax = (uint32_t)bmax; L.scan_tmp_max = (uint32_t)scan_tmp;

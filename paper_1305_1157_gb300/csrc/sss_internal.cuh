@@ -19,6 +19,7 @@ constexpr int kSampleMax = 1 << (kKMax + 1);    // sample buffer, 2v + 1 keys pa
 constexpr uint32_t kBaseCap = 256;              // slots of one base-case tile
 constexpr uint32_t kBaseMax = kBaseCap / 2;     // largest base-case bucket (128)
 constexpr uint32_t kTinyMax = 32;               // base-case buckets this small get one warp each
+constexpr uint32_t kRunPiece = 2048;            // strings per work item of a large run of equal strings
 constexpr uint32_t kMedMax = 8192;              // largest bucket one CTA distributes alone
 constexpr int kMedKMax = 9;                     // its deepest tree: choose_k(8192) = 9
 constexpr int kMedNB = (2 << kMedKMax) - 1;     // 1023 buckets
@@ -152,7 +153,7 @@ struct Work {
     Seg* small[2];           // [smax] children for the base case (tile form)
     Seg* tiny[2];            // [ymax] children of at most kTinyMax strings (warp form)
     uint32_t* small_size[2]; // [smax] their sizes
-    Seg* bigrun[2];          // [bmax] large runs of equal strings
+    Seg* bigrun[2];          // [bmax] pieces of large runs of equal strings
     uint32_t* small_off;     // [smax + 1] packed start of each small segment
     uint32_t* tile_first;    // [n / base_threshold + 2] first small segment packed into each base-case tile
     uint32_t* scan_tmp;      // [scan_tmp_max] scan scratch of the distribution rounds

@@ -81,9 +81,16 @@ __device__ __forceinline__ void append_child(const Work& w, const Params& p, int
     Hdr* h = w.hdr;
     if (size <= 1) return;
     if (isrun && size > p.base_threshold) {
-        uint32_t s = atomicAdd(&h->n_bigrun, 1u);
-        if (s < w.bmax) w.bigrun[out][s] = Seg{start, size, cdepth, runlcp};
-        else atomicOr(&h->err, kErrRunOverflow);
+        // pieces of at most kRunPiece strings, so one large run spreads over
+        // many CTAs; depth holds the run's first position
+        const uint32_t np = (size + kRunPiece - 1u) / kRunPiece;
+        const uint32_t s = atomicAdd(&h->n_bigrun, np);
+        if (s + np <= w.bmax) {
+            for (uint32_t j = 0; j < np; j++)
+                w.bigrun[out][s + j] = Seg{start + j * kRunPiece, min(kRunPiece, size - j * kRunPiece), start, runlcp};
+        } else {
+            atomicOr(&h->err, kErrRunOverflow);
+        }
     } else if (size <= min(p.base_threshold, kTinyMax)) {
         uint32_t s = atomicAdd(&h->n_tiny, 1u);
         if (s < w.ymax) {
@@ -1198,7 +1205,8 @@ __global__ void __launch_bounds__(32 * kTinyWarps) k_tiny(Work w, Params p) {
     if (threadIdx.x == 0 && s_iters) atomicAdd(&w.hdr->base_iters, s_iters);
 }
 
-// Buckets too large for the base case whose strings are all equal.
+// Buckets too large for the base case whose strings are all equal, in
+// pieces of at most kRunPiece strings (g.depth: the run's first position).
 __global__ void k_bigrun(Work w) {
     const int buf = w.hdr->round & 1u;
     const uint32_t nrun = w.hdr->n_bigrun_snap;
@@ -1207,10 +1215,11 @@ __global__ void k_bigrun(Work w) {
         const Seg g = w.bigrun[buf][r];
         // equal strings: their common length
         const uint32_t runlcp = lcp_of_equal(w, g.aux, w.rec[buf][g.begin].idx);
+#pragma unroll 4
         for (uint32_t i = threadIdx.x; i < g.size; i += blockDim.x) {
             const uint32_t q = g.begin + i;
             w.out_perm[q] = w.rec[buf][q].idx;
-            if (i > 0) w.out_lcp[q] = runlcp;
+            if (q > g.depth) w.out_lcp[q] = runlcp;
         }
     }
 }
