@@ -43,9 +43,10 @@ WORKLOAD_TEXT = {
     "uniform-100k": "100k strings, lengths uniform 8-20, bytes uniform a-z",
     "url-64m": "64M URL-like strings as url-16m (about 3.9 GB of characters)",
 }
-SCATTER_BYTES_PER_STRING = 24   # read key 8 + index 4, write key 8 + index 4
+SCATTER_BYTES_PER_STRING = 26   # read bucket id 2 + key 8 + index 4, write key 8 + index 4
+MEDIUM_BYTES_PER_STRING = 24    # read key 8 + index 4, write key 8 + index 4 (bucket ids in shared memory)
 REFILL_BYTES = 16               # offset 8 + key word 8, per key word gathered again
-CLASSIFY_BYTES_PER_STRING = 8   # read key 8
+CLASSIFY_BYTES_PER_STRING = 10  # read key 8, write bucket id 2
 BASE_BYTES_PER_STRING = 20      # read key 8 + index 4, write perm 4 + lcp 4
 
 
@@ -585,7 +586,7 @@ def main():
     # k_scatter) see the large segments' strings, k_med_round the medium ones
     algo = {"scatter": SCATTER_BYTES_PER_STRING * large_strings + REFILL_BYTES * large_refills,
             "classify": CLASSIFY_BYTES_PER_STRING * large_strings,
-            "medium": SCATTER_BYTES_PER_STRING * medium_strings + REFILL_BYTES * medium_refills,
+            "medium": MEDIUM_BYTES_PER_STRING * medium_strings + REFILL_BYTES * medium_refills,
             "base": BASE_BYTES_PER_STRING * base_strings}
     units = {"scatter": large_strings, "classify": large_strings, "medium": medium_strings,
              "base": base_strings}

@@ -86,7 +86,7 @@ struct Layout {
     size_t total = 0;
     size_t o_rec0, o_rec1, o_counts, o_counts_scan, o_tlvl, o_tino, o_plans, o_chunk_seg,
         o_large, o_med0, o_med1, o_small0, o_small1, o_tiny0, o_tiny1, o_small_size0, o_small_size1, o_small_off, o_tile_first,
-        o_bigrun0, o_bigrun1, o_scan_tmp, o_scan_tmp2, o_hdr, o_roots,
+        o_bigrun0, o_bigrun1, o_bids, o_scan_tmp, o_scan_tmp2, o_hdr, o_roots,
         o_cdf_samp, o_cdf_tab, o_cdf_kmin, o_cdf_scale;
     uint32_t cmax, tmax, lmax, chmax, smax, ymax, bmax, scan_tmp_max, mmax;
 };
@@ -157,6 +157,7 @@ Layout layout_for(uint32_t n, const sss_options& o, uint32_t num_roots, bool lea
     L.o_tile_first = take(4 * (nn / T + 2));
     L.o_bigrun0 = take(sizeof(Seg) * bmax);
     L.o_bigrun1 = take(sizeof(Seg) * bmax);
+    L.o_bids = take(sizeof(uint16_t) * nn);
     L.o_scan_tmp = take(4 * scan_tmp);
     L.o_scan_tmp2 = take(4 * scan_tmp);
     L.o_hdr = take(sizeof(Hdr));
@@ -198,6 +199,7 @@ Work make_work(const Layout& L, char* ws, const uint8_t* chars, const uint64_t* 
     w.tile_first = (uint32_t*)(ws + L.o_tile_first);
     w.bigrun[0] = (Seg*)(ws + L.o_bigrun0);
     w.bigrun[1] = (Seg*)(ws + L.o_bigrun1);
+    w.bids = (uint16_t*)(ws + L.o_bids);
     w.scan_tmp = (uint32_t*)(ws + L.o_scan_tmp);
     w.scan_tmp2 = (uint32_t*)(ws + L.o_scan_tmp2);
     w.hdr = (Hdr*)(ws + L.o_hdr);

@@ -474,7 +474,7 @@ __device__ __forceinline__ void classify_range(const Rec* __restrict__ recs, uin
 __device__ __forceinline__ void classify_range_learned(const Rec* __restrict__ recs, uint32_t lo, uint32_t hi,
                                                        const uint64_t* t, const uint64_t* ino, int k, uint32_t nb,
                                                        uint32_t* hist, const float* C, uint32_t M, uint64_t kmin,
-                                                       float scale, uint32_t& misses) {
+                                                       float scale, uint32_t& misses, uint16_t* bid) {
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t v = (1u << k) - 1u;
     for (uint32_t base = lo; base < hi; base += blockDim.x * kClassifyUnroll) {
@@ -492,6 +492,7 @@ __device__ __forceinline__ void classify_range_learned(const Rec* __restrict__ r
                 b = classify_key(kk[u], t, ino, k);
                 misses++;
             }
+            if (e < hi) bid[e - lo] = (uint16_t)b;
             const uint32_t peers = __match_any_sync(FULL_MASK, b);
             if (lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&hist[b], (uint32_t)__popc(peers));
         }
@@ -534,16 +535,16 @@ __global__ void __launch_bounds__(kClassifyThreads) k_classify(Work w, Params p)
                 __syncthreads();
                 uint32_t misses = 0;
                 classify_range_learned(w.rec[cur], lo, hi, t.view(), ino, k, nb, hist, C, p.cdf_M, w.cdf_kmin[s],
-                                       w.cdf_scale[s], misses);
+                                       w.cdf_scale[s], misses, w.bids + lo);
                 misses = __reduce_add_sync(FULL_MASK, misses);
                 if ((threadIdx.x & 31u) == 0 && misses)
                     atomicAdd(&w.hdr->learned_misses, (unsigned long long)misses);
                 if (threadIdx.x == 0) atomicAdd(&w.hdr->learned_keys, (unsigned long long)(hi - lo));
             } else {
-                classify_range(w.rec[cur], lo, hi, t.view(), ino, k, nb, hist, (uint16_t*)nullptr, p.equal_test != 0);
+                classify_range(w.rec[cur], lo, hi, t.view(), ino, k, nb, hist, w.bids + lo, p.equal_test != 0);
             }
         } else {
-            classify_range(w.rec[cur], lo, hi, t.view(), ino, k, nb, hist, (uint16_t*)nullptr, p.equal_test != 0);
+            classify_range(w.rec[cur], lo, hi, t.view(), ino, k, nb, hist, w.bids + lo, p.equal_test != 0);
         }
         __syncthreads();
         for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x)
@@ -620,14 +621,16 @@ __device__ uint32_t scatter_range(const Work& w, int cur, uint32_t lo, uint32_t 
                 proposed = true;
             }
         }
-        if (!kFromBid && !proposed) {
-            KT kk[ITEMS];
+        if constexpr (!kFromBid) {
+            if (!proposed) {
+                KT kk[ITEMS];
 #pragma unroll
-            for (int j = 0; j < ITEMS; j++) kk[j] = KeyTraits<KT>::of(rr[j]);
-            classify_keys_by<ITEMS>(equal_test, kk, bb, t, ino, k);
+                for (int j = 0; j < ITEMS; j++) kk[j] = KeyTraits<KT>::of(rr[j]);
+                classify_keys_by<ITEMS>(equal_test, kk, bb, t, ino, k);
 #pragma unroll
-            for (int j = 0; j < ITEMS; j++)
-                if (wbase + j * 32u >= hi) bb[j] = nb;
+                for (int j = 0; j < ITEMS; j++)
+                    if (wbase + j * 32u >= hi) bb[j] = nb;
+            }
         }
         // next key words of strings whose bucket moves deeper: all gathers are
         // issued here, before any store, and complete during the ranking
@@ -689,17 +692,14 @@ __device__ __forceinline__ void add_refills(unsigned long long* counter, uint32_
 
 template <class KT>
 struct ScatterSmem {
-    LevelTree<KT, kVMax + 1> t;
     KT ino[kVMax];
     ScatterState<kNBMax> ss;
-    float C[KeyTraits<KT>::kBytes == 8 ? kCdfMMax + 1 : 1];  // learned model knots (learned mode only)
 };
 
 template <class KT>
 __global__ void __launch_bounds__(kScatterThreads, SSS_SCATTER_MIN_BLOCKS) k_scatter(Work w, Params p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ScatterSmem<KT>& sm = *reinterpret_cast<ScatterSmem<KT>*>(smem_raw);
-    const KT* tree_lvl = reinterpret_cast<const KT*>(w.tree_lvl);
     const KT* tree_ino = reinterpret_cast<const KT*>(w.tree_ino);
     const int cur = w.hdr->round & 1u;
     const int med_out = cur ^ 1;
@@ -712,10 +712,7 @@ __global__ void __launch_bounds__(kScatterThreads, SSS_SCATTER_MIN_BLOCKS) k_sca
         const uint32_t ci = c - P.chunk_base;
         const int k = (int)P.k;
         const uint32_t v = (1u << k) - 1u, nb = 2u * v + 1u;
-        for (uint32_t i = threadIdx.x; i < v; i += blockDim.x) {
-            sm.t.set(i + 1, tree_lvl[P.tree_base + i]);
-            sm.ino[i] = tree_ino[P.tree_base + i];
-        }
+        for (uint32_t i = threadIdx.x; i < v; i += blockDim.x) sm.ino[i] = tree_ino[P.tree_base + i];
         __syncthreads();
         const uint32_t* S = w.counts_scan + P.count_base;
         const uint32_t seg_end = P.begin + P.size;
@@ -751,18 +748,9 @@ __global__ void __launch_bounds__(kScatterThreads, SSS_SCATTER_MIN_BLOCKS) k_sca
         __syncthreads();
         const uint32_t lo = P.begin + ci * P.chunk;
         const uint32_t hi = min(lo + P.chunk, seg_end);
-        const float* C = nullptr;
-        const bool model = KeyTraits<KT>::kBytes == 8 && p.learned && P.size >= kLearnedMinSize;
-        if (model) {
-            const float* tab = w.cdf_tab + (size_t)s * (p.cdf_M + 1);
-            for (uint32_t j = threadIdx.x; j <= p.cdf_M; j += blockDim.x) sm.C[j] = tab[j];
-            __syncthreads();
-            C = sm.C;
-        }
-        const uint32_t nref = scatter_range<kNBMax, false, KT>(w, cur, lo, hi, nb, sm.ss, sm.t.view(), sm.ino, k, nullptr, seg_end,
-                                                           P.depth, p.equal_test != 0, C, p.cdf_M,
-                                                           model ? w.cdf_kmin[s] : 0ull,
-                                                           model ? w.cdf_scale[s] : 0.0f);
+        // buckets as k_classify found them (tree or learned proposal)
+        const uint32_t nref = scatter_range<kNBMax, true, KT>(w, cur, lo, hi, nb, sm.ss, (const KT*)sm.ino, sm.ino, k,
+                                                          w.bids + lo, seg_end, P.depth, p.equal_test != 0);
         add_refills(&w.hdr->refills, nref);
         __syncthreads();
     }
