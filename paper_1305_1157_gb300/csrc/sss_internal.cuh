@@ -641,7 +641,7 @@ cudaError_t launch_plan(const Work& w, const Params& p, Prof* pf, cudaStream_t s
 // the device-wide round and the medium round of one round body concurrently
 // (forked from and joined back into the caller's stream).  Stream
 // priorities: the device-wide round (the chain the next round waits on)
-// highest, the base case next, the medium round lowest; the lower branches
+// highest, the medium rounds next, the base case lowest; the lower branches
 // fill the SMs around the higher.
 struct Branches {
     cudaStream_t large = nullptr, base = nullptr, medium = nullptr, tiny = nullptr;

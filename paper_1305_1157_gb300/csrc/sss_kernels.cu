@@ -1443,22 +1443,23 @@ static cudaError_t launch_medium_t(const Work& w, const Params& p, const Hdr* hc
 #endif
 
 cudaError_t branches_create(Branches& b) {
-    // priorities: the device-wide round first, then the base case (short
-    // kernels that would otherwise queue behind the medium round's CTAs), the
-    // medium round fills what is left
+    // priorities: the device-wide round first (the chain every later round
+    // waits on), then the medium rounds (whose children feed the next
+    // round), and the base case of finished buckets fills what is left
     int least = 0, greatest = 0;
     cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
     if (!SSS_BRANCH_PRIORITIES) greatest = least;
     const int middle = greatest < least ? greatest + 1 : greatest;
+    const int p_base = least, p_med = middle;
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b.large, cudaStreamNonBlocking, greatest);
-    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b.base, cudaStreamNonBlocking, middle);
-    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b.medium, cudaStreamNonBlocking, least);
-    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b.tiny, cudaStreamNonBlocking, middle);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b.base, cudaStreamNonBlocking, p_base);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b.medium, cudaStreamNonBlocking, p_med);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b.tiny, cudaStreamNonBlocking, p_base);
     // the same priorities as stream launch attributes, which stream capture
     // copies into the kernel nodes of a graph (optional: ignored if refused)
     if (e == cudaSuccess) {
         const cudaStream_t ss[4] = {b.large, b.base, b.medium, b.tiny};
-        const int pr[4] = {greatest, middle, least, middle};
+        const int pr[4] = {greatest, p_base, p_med, p_base};
         for (int i = 0; i < 4; i++) {
             cudaLaunchAttributeValue v;
             memset(&v, 0, sizeof(v));
