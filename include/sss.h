@@ -55,7 +55,7 @@ typedef enum {
 } sss_status;
 
 /* Tuning knobs.  Defaults: k_max 10, base_threshold 128, medium_threshold
- * 4096, chunk 32768, seed 0x5eed, cdf_segments 4096, cdf_steps 16,
+ * 8192, chunk 16384, seed 0x5eed, cdf_segments 4096, cdf_steps 16,
  * cdf_lr 0.05, profile 0, graph 0, key_bytes 16, classifier 0, alphabet 0. */
 typedef struct sss_options {
     int32_t k_max;             /* largest splitter tree depth k: v = 2^k - 1 splitters, 1..10 */

@@ -26,7 +26,7 @@ using namespace sss;
 namespace {
 
 std::mutex g_mu;
-sss_options g_opt = {10, 128u, 4096u, 32768u, 0x5eedull, 4096u, 16u, 0.05f, 0u, 0u, 16u, 0u, 0u};
+sss_options g_opt = {10, 128u, 8192u, 16384u, 0x5eedull, 4096u, 16u, 0.05f, 0u, 0u, 16u, 0u, 0u};
 sss_stats g_stats;
 Prof g_prof;
 std::vector<int> g_tl_cls;       // timeline of the last profiled host-driven call

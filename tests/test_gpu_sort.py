@@ -201,7 +201,7 @@ SMALL_OPTS = [
     dict(base_threshold=16, medium_threshold=8192, k_max=10, chunk=2048, key_bytes=16),
     dict(base_threshold=100, medium_threshold=300, k_max=5, chunk=4096, key_bytes=8),
     # defaults
-    dict(base_threshold=128, medium_threshold=8192, k_max=10, chunk=32768, key_bytes=16),
+    dict(base_threshold=128, medium_threshold=8192, k_max=10, chunk=16384, key_bytes=16),
     # as above with two-word keys and one-word keys
     dict(base_threshold=16, medium_threshold=16, k_max=2, chunk=2048, key_bytes=16),
     dict(base_threshold=16, medium_threshold=8192, k_max=10, chunk=2048, key_bytes=8),
