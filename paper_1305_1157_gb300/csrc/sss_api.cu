@@ -436,11 +436,12 @@ int run_sort(const Work& w, const sss_options& o, const Seg* roots_dev, uint32_t
 // ------------------------------------------------------------ graph form
 //
 // The same sort as one CUDA graph: prologue (init, roots, plan), a
-// conditional WHILE node whose body is one round (three concurrent branches:
-// base case of the previous round's small children, device-wide round,
-// medium rounds; then plan and advance) and whose last kernel decides on the
-// device whether another round is needed, then the epilogue (base case of
-// the last round's children, LCP fixup, index rebasing).
+// conditional WHILE node whose body is one round (four concurrent branches:
+// tile-form and warp-form base case of the previous round's small children,
+// device-wide round, medium rounds; then plan and advance) and whose last
+// kernel decides on the device whether another round is needed, then the
+// epilogue (base case of the last round's children, LCP fixup, index
+// rebasing).
 // Kernels take their work counts from the device header, so one launch runs
 // the whole sort without host round-trips.  Instantiated graphs are cached
 // per device and reused while the call's buffers and options are unchanged.
