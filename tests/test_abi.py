@@ -3,6 +3,8 @@ include/sss.h declares; host-side argument checks work without a GPU."""
 import ctypes
 import os
 import re
+import shutil
+import subprocess
 
 import pytest
 
@@ -98,3 +100,34 @@ def test_workspace_size_grows_with_n(lib):
     a, b = sss.sss_workspace_size(1000), sss.sss_workspace_size(1_000_000)
     assert 0 < a < b
     assert b >= 24 * 1_000_000  # two key and two index arrays at least
+
+
+def _c_layout(struct, fields, tmp_path):
+    """sizeof and offsetof of a struct of include/sss.h, from a C program
+    compiled with the host compiler."""
+    src = tmp_path / "layout.c"
+    body = "\n".join(f'    printf("{f} %zu\\n", offsetof({struct}, {f}));' for f in fields)
+    src.write_text(f"""#include <stdio.h>
+#include <stddef.h>
+#include "sss.h"
+int main(void) {{
+    printf("sizeof %zu\\n", sizeof({struct}));
+{body}
+    return 0;
+}}
+""")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    return {k: int(v) for k, v in (line.split() for line in out.splitlines())}
+
+
+@pytest.mark.parametrize("cls", [sss.sss_options, sss.sss_stats])
+def test_binding_structs_match_the_header_layout(cls, tmp_path):
+    if shutil.which("gcc") is None:
+        pytest.skip("no host C compiler")
+    fields = [f for f, _ in cls._fields_]
+    c = _c_layout(cls.__name__, fields, tmp_path)
+    assert c["sizeof"] == ctypes.sizeof(cls)
+    for f in fields:
+        assert c[f] == getattr(cls, f).offset, f
