@@ -223,6 +223,18 @@ def run_reference(args, rank):
 
 # ------------------------------------------------------------------ extra legs
 
+def reduce_max(value: float, dist, device) -> float:
+    """The largest of each rank's value (the slowest rank's time); the value
+    itself without a process group.  device: where the collective's tensor
+    lives (the rank's GPU under NCCL, the CPU under gloo)."""
+    if not dist:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _timed(torch, stream, dev, fn, steps, dist):
     """Mean ms per call of fn over `steps` calls (CUDA events on stream), max over ranks."""
     if dist:
@@ -235,12 +247,7 @@ def _timed(torch, stream, dev, fn, steps, dist):
         fn()
     b.record(stream)
     torch.cuda.synchronize(dev)
-    ms = a.elapsed_time(b) / max(1, steps)
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    return ms
+    return reduce_max(a.elapsed_time(b) / max(1, steps), dist, dev)
 
 
 def leg_host(sss, torch, chars, offsets, perm, lcp, n, stream, dev, args, world, dist):
@@ -494,11 +501,7 @@ def main():
     torch.cuda.synchronize(dev)
     if dist:
         dist.barrier()
-    ms = t_start.elapsed_time(t_end) / args.steps
-    if dist:
-        tt = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = reduce_max(t_start.elapsed_time(t_end) / args.steps, dist, dev)
 
     # second timed region, per-kernel times: the same sorts with the rounds
     # driven from the host and CUDA events around every kernel launch on the
@@ -544,11 +547,7 @@ def main():
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             sss.sss_sort_host(h_chars, len(s.chars), h_off, n, h_perm, h_lcp)
-        te = (time.perf_counter() - t0) / args.e2e_steps
-        if dist:
-            tt = torch.tensor([te], dtype=torch.float64, device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te = float(tt.item())
+        te = reduce_max((time.perf_counter() - t0) / args.e2e_steps, dist, dev)
         e2e = {"value": n * world / te, "unit": "strings/s", "h2d_bytes_per_step": int(len(s.chars) + 8 * n),
                "d2h_bytes_per_step": int(8 * n), "ms_per_step": te * 1e3}
 

@@ -42,3 +42,33 @@ def test_scatter_traffic_is_read_only_for_the_captured_source(monkeypatch):
     monkeypatch.setattr(bench, "kernel_source_sha", lambda: "0" * 16)
     assert bench.ncu_traffic("k_scatter", "url-16m") is None
     assert bench.ncu_traffic("k_scatter", "no-such-workload") is None
+
+
+def _free_port():
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _torchrun(script_args, nproc=2):
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes", "1", "--nproc-per-node", str(nproc),
+           "--master-addr", "127.0.0.1", "--master-port", str(_free_port()), *script_args]
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    return subprocess.run(cmd, capture_output=True, text=True, cwd=ROOT, timeout=600, env=env)
+
+
+def test_times_reduce_to_the_slowest_rank_over_gloo():
+    r = _torchrun([os.path.join(ROOT, "tests", "dist_reduce_helper.py")])
+    assert r.returncode == 0, r.stderr[-2000:]
+    got = sorted(line for line in r.stdout.splitlines() if line.startswith("rank "))
+    assert got == ["rank 0 max 2.0", "rank 1 max 2.0"]
+
+
+def test_reference_arm_under_two_ranks_prints_one_line():
+    r = _torchrun([os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1", "--warmup", "0",
+                   "--cpu-sample", "3000"])
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    assert json.loads(lines[0])["impl"] == "reference"
