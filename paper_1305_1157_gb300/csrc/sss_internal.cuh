@@ -73,7 +73,10 @@ struct SegPlan {
     uint32_t begin, size, depth, k;     // v = 2^k - 1 splitters, 2^(k+1) - 1 buckets
     uint32_t chunks, chunk_base;        // work items of this segment
     uint32_t count_base, tree_base;     // offsets into the count matrix and the trees
-    uint32_t chunk, pad0, pad1, pad2;   // strings per work item in this round
+    uint32_t chunk;                     // strings per work item in this round
+    uint32_t kp;                        // k as planned (sizes the count rows and the sample);
+                                        // k_sample may lower k to the levels its splitters use
+    uint32_t pad1, pad2;
 };
 
 // Device header: live append counters and the snapshot the host reads back.

@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(1024) k_plan(Work w, Params p) {
             const Seg g = w.large[s];
             const int k = choose_k(g.size, p.k_max);
             const uint32_t ch = (g.size + chunk - 1) / chunk;
-            w.plans[s] = SegPlan{g.begin, g.size, g.depth, (uint32_t)k, ch, bc, bn, bt, chunk, 0u, 0u, 0u};
+            w.plans[s] = SegPlan{g.begin, g.size, g.depth, (uint32_t)k, ch, bc, bn, bt, chunk, (uint32_t)k, 0u, 0u};
             for (uint32_t c = 0; c < ch; c++) w.chunk_seg[bc + c] = s;
             bc += ch;
             bn += ((2u << k) - 1u) * ch;
@@ -316,10 +316,20 @@ __device__ __forceinline__ uint32_t upper_bound_k(const KT* s, uint32_t n, const
 // where b' and a' skip every sample equal to x.  A node whose range is empty
 // repeats its parent's splitter.  Level by level, one thread per node.
 // lvl[1..v] receives the level-order tree; ra/rb: shared scratch [v+1].
+// depth_used (shared, optional): the number of levels holding a node with a
+// non-empty range.  Below them every node repeats its parent's splitter, so
+// the tree cut to those levels has the same non-empty buckets (the paper's
+// "inspect the sample" adaptivity, App. A.2: samples with many equal keys
+// get smaller trees).
 template <class KT>
-__device__ void select_splitters(const KT* s, uint32_t cnt, int k, KT* lvl, int32_t* ra, int32_t* rb) {
+__device__ void select_splitters(const KT* s, uint32_t cnt, int k, KT* lvl, int32_t* ra, int32_t* rb,
+                                 int* depth_used = nullptr) {
     const uint32_t v = (1u << k) - 1u;
-    if (threadIdx.x == 0) { ra[1] = 0; rb[1] = (int32_t)cnt - 1; }
+    if (threadIdx.x == 0) {
+        ra[1] = 0;
+        rb[1] = (int32_t)cnt - 1;
+        if (depth_used) *depth_used = 0;
+    }
     __syncthreads();
     for (int l = 0; l < k; l++) {
         const uint32_t first = 1u << l;
@@ -328,6 +338,7 @@ __device__ void select_splitters(const KT* s, uint32_t cnt, int k, KT* lvl, int3
             KT x;
             int32_t bl, ar;
             if (a <= b) {
+                if (depth_used) atomicMax(depth_used, l + 1);
                 int32_t m = a + (b - a) / 2;
                 x = s[m];
                 int32_t first_eq = (int32_t)lower_bound_k(s, cnt, x);
@@ -398,13 +409,14 @@ __global__ void __launch_bounds__(1024) k_sample(Work w, Params p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SampleSmem<KT>& sm = *reinterpret_cast<SampleSmem<KT>*>(smem_raw);
     __shared__ uint32_t s_item;
+    __shared__ int s_depth;
     const Rec* recs = w.rec[w.hdr->round & 1u];
     const uint32_t L = w.hdr->L;
     KT* tree_lvl = reinterpret_cast<KT*>(w.tree_lvl);
     KT* tree_ino = reinterpret_cast<KT*>(w.tree_ino);
     for (uint32_t seg = first_item(); seg < L; seg = next_item(&w.hdr->q_sample, &s_item)) {
         const SegPlan P = w.plans[seg];
-        const int k = (int)P.k;
+        const int k = (int)P.kp;
         const uint32_t pw = 2u << k;
         const uint32_t cnt = pw - 1u;  // alpha (v + 1) - 1 with alpha = 2
         for (uint32_t j = threadIdx.x; j < pw; j += blockDim.x)
@@ -416,8 +428,11 @@ __global__ void __launch_bounds__(1024) k_sample(Work w, Params p) {
             uint64_t* out = w.cdf_samp + (size_t)seg * kSampleMax;
             for (uint32_t j = threadIdx.x; j < cnt; j += blockDim.x) out[j] = KeyTraits<KT>::word(sm.samp[j]);
         }
-        select_splitters(sm.samp, cnt, k, sm.lvl, sm.ra, sm.rb);
-        emit_tree(sm.lvl, k, tree_lvl + P.tree_base, tree_ino + P.tree_base);
+        // the learned model fits the planned sample and tree: no cut there
+        select_splitters(sm.samp, cnt, k, sm.lvl, sm.ra, sm.rb, p.learned ? nullptr : &s_depth);
+        const int kt = p.learned ? k : max(1, s_depth);
+        if (threadIdx.x == 0 && kt != k) w.plans[seg].k = (uint32_t)kt;
+        emit_tree(sm.lvl, kt, tree_lvl + P.tree_base, tree_ino + P.tree_base);
     }
 }
 
@@ -547,8 +562,11 @@ __global__ void __launch_bounds__(kClassifyThreads) k_classify(Work w, Params p)
             classify_range(w.rec[cur], lo, hi, t.view(), ino, k, nb, hist, w.bids + lo, p.equal_test != 0);
         }
         __syncthreads();
-        for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x)
-            w.counts[P.count_base + b * P.chunks + ci] = hist[b];
+        // the count rows were planned for 2^(kp+1) - 1 buckets: the rows a
+        // smaller tree leaves unused are zero
+        const uint32_t nbp = (2u << P.kp) - 1u;
+        for (uint32_t b = threadIdx.x; b < nbp; b += blockDim.x)
+            w.counts[P.count_base + b * P.chunks + ci] = b < nb ? hist[b] : 0u;
         __syncthreads();
     }
 }
@@ -798,22 +816,27 @@ __global__ void __launch_bounds__(kScatterThreads, SSS_MED_MIN_BLOCKS) k_med_rou
     const int med_in = cur, med_out = cur ^ 1;
     const uint32_t n_med = w.hdr->n_med_snap;
     __shared__ uint32_t s_item;
+    __shared__ int s_depth;  // levels the splitters use (select_splitters)
     for (uint32_t mi = first_item(); mi < n_med; mi = next_item(&w.hdr->q_med, &s_item)) {
         Seg g = w.med[med_in][mi];
         const uint32_t m = g.size;
-        const int k = choose_k(m, min(p.k_max, kMedKMax));
-        const uint32_t v = (1u << k) - 1u, nb = 2u * v + 1u;
-        const uint32_t pw = 2u << k, cnt = pw - 1u;
+        const int kp = choose_k(m, min(p.k_max, kMedKMax));
+        const uint32_t nbp = (2u << kp) - 1u;
+        const uint32_t pw = 2u << kp, cnt = pw - 1u;
+        int k = kp;          // the tree's levels this pass (cut to the levels its splitters use)
+        uint32_t nb = nbp;
         Rec* recs = w.rec[cur];
         for (uint32_t level = 0;; level++) {
             for (uint32_t j = threadIdx.x; j < pw; j += blockDim.x)
                 sm.sel.samp[j] = j < cnt ? KeyTraits<KT>::load(recs + g.begin + sample_pos(p.seed, g.begin, m, j))
                                          : KeyTraits<KT>::top();
-            for (uint32_t b = threadIdx.x; b <= nb; b += blockDim.x) sm.hist[b] = 0;
+            for (uint32_t b = threadIdx.x; b <= nbp; b += blockDim.x) sm.hist[b] = 0;
             if (threadIdx.x == 0) sm.full = kNoRefill;
             __syncthreads();
             bitonic_sort(sm.sel.samp, pw);
-            select_splitters(sm.sel.samp, cnt, k, sm.sel.lvl, sm.sel.ra, sm.sel.rb);
+            select_splitters(sm.sel.samp, cnt, kp, sm.sel.lvl, sm.sel.ra, sm.sel.rb, &s_depth);
+            k = max(1, s_depth);
+            nb = (2u << k) - 1u;
             emit_tree_smem(sm.sel.lvl, k, sm.t, sm.ino);
             // the splitter-choice scratch is dead: the move state takes its place
             for (uint32_t b = threadIdx.x; b <= nb; b += blockDim.x) sm.mv.ss.wcnt[b] = 0ull;
