@@ -271,3 +271,51 @@ def test_cdf_gradient_matches_finite_differences():
         tm = theta.copy(); tm[j] -= h
         fd[j] = (oracle.cdf_loss(tp, u, y) - oracle.cdf_loss(tm, u, y)) / (2 * h)
     assert np.allclose(g, fd, rtol=1e-5, atol=1e-9)
+
+
+def _cut_depth(level):
+    """Levels of a level-order tree that hold a node differing from its
+    parent (a node repeats its parent's splitter exactly when its sample
+    range was empty; a chosen splitter never equals its parent's, whose
+    equal samples the child ranges skip)."""
+    d = 1
+    for i in range(2, len(level) + 1):
+        if int(level[i - 1]) != int(level[(i >> 1) - 1]):
+            d = max(d, i.bit_length())
+    return d
+
+
+def _in_order(level, d):
+    """In-order sequence of the top d levels of a level-order tree."""
+    out = [0] * (2 ** d - 1)
+    for i in range(1, 2 ** d):
+        lv = i.bit_length() - 1
+        q = i - (1 << lv)
+        out[(2 * q + 1) * (1 << (d - 1 - lv)) - 1] = int(level[i - 1])
+    return out
+
+
+def test_cut_tree_keeps_the_nonempty_buckets():
+    # the splitter tree cut to the levels whose nodes still choose a new
+    # splitter (the sample-driven tree depth) puts every key with the same
+    # other keys, and in an equality bucket exactly when the full tree does
+    rng = random.Random(9)
+    for trial in range(300):
+        k = rng.randint(2, 8)
+        cnt = 2 ** (k + 1) - 1
+        distinct = rng.choice([1, 2, 3, 5, 9, 17, 40, 1000])
+        vals = [rng.randrange(1, 10 ** 6) for _ in range(distinct)]
+        weights = [rng.random() ** 3 for _ in vals]
+        s = np.array(sorted(rng.choices(vals, weights, k=cnt)), dtype=np.uint64)
+        level, ino = oracle.select_splitters(s, k)
+        d = _cut_depth(level)
+        assert 1 <= d <= k
+        cut = _in_order(level, d)
+        assert cut == sorted(cut)
+        assert set(cut) == set(map(int, ino))  # the same splitters, fewer repeats
+        keys = sorted(set(vals) | {v + 1 for v in vals} | {v - 1 for v in vals} | {0, 2 ** 63})
+        full_b = [oracle.classify(q, ino) for q in keys]
+        cut_b = [oracle.classify(q, cut) for q in keys]
+        for i in range(len(keys) - 1):
+            assert (full_b[i] == full_b[i + 1]) == (cut_b[i] == cut_b[i + 1])
+        assert [b & 1 for b in full_b] == [b & 1 for b in cut_b]
