@@ -856,11 +856,14 @@ int sss_release(void) {
             cudaSetDevice(d);
             branches_destroy(g_branches[d]);
         }
-        if (!P.ws && !P.io && !P.hh) continue;
+        if (!P.ws && !P.io && !P.hh && !P.alpha_scan && !P.alpha_pack && !P.ah_host) continue;
         cudaSetDevice(d);
         if (P.ws) cudaFree(P.ws);
         if (P.io) cudaFree(P.io);
+        if (P.alpha_scan) cudaFree(P.alpha_scan);
+        if (P.alpha_pack) cudaFree(P.alpha_pack);
         if (P.hh) cudaFreeHost(P.hh);
+        if (P.ah_host) cudaFreeHost(P.ah_host);
         P = DevPool();
     }
     cudaSetDevice(cur);

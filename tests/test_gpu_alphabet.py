@@ -223,3 +223,17 @@ def test_full_size_dna_20m_verified():
     assert code == 0, (oracle.VERIFY_CODES[code], bad)
     st = sss.sss_get_last_stats()
     assert st.alphabet_group == 3
+
+
+def test_release_frees_and_sorting_resumes():
+    # sss_release drops the workspace, the graph cache and the alphabet
+    # buffers; the next calls allocate again and still sort correctly
+    s = gen.generate(3, 30_000, 75)
+    for graph in (0, 1):
+        sss.sss_set_options(alphabet=1, graph=graph)
+        perm, lcp = gpu_sort(s)
+        assert_same(s, perm, lcp)
+        sss.sss_release()
+        perm, lcp = gpu_sort(s)
+        assert_same(s, perm, lcp)
+        assert sss.sss_get_last_stats().alphabet_group == 3
