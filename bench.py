@@ -2,14 +2,19 @@
 """Benchmark of the GB300 string sample sort.
 
 One step = one complete sort (every distribution round, base case and LCP
-pass) of one workload that is already resident in device memory.  The
-default workload is 16M URL-like strings (about 0.97 GB of characters,
-larger than the 129 MB L2, so no flush is needed between steps).
+pass) of one workload that is already resident in device memory, run as
+one launch of the library's CUDA graph (options.graph = 1).  The default
+workload is 16M URL-like strings (about 0.97 GB of characters, larger than
+the 129 MB L2, so no flush is needed between steps).
 
 Prints one JSON line: sorted strings/s over all ranks, plus
   roofline      the dominant kernel's algorithmic bytes / its average launch
-                time (CUDA events recorded by the library on its stream during
-                the timed steps) against the measured HBM copy bandwidth
+                time against the measured HBM copy bandwidth; the launch
+                times come from a second timed region of the same sorts with
+                the rounds driven from the host and CUDA events recorded by
+                the library around every launch on its stream
+                (profiled_pass); traffic = the committed ncu DRAM bytes per
+                string for the current kernel source, else null
   cpu_baseline  the CPU oracle timed on this host (single thread)
   e2e           the same metric through sss_sort_host: pinned host buffers,
                 copies to and from the device inside the timed region
