@@ -11,6 +11,8 @@ import bench  # noqa: E402
 
 dist.init_process_group("gloo")
 rank = dist.get_rank()
-print(f"rank {rank} max {bench.reduce_max(1.0 + rank, dist, 'cpu')}", flush=True)
+# one write per line: the two ranks share the pipe
+sys.stdout.write(f"rank {rank} max {bench.reduce_max(1.0 + rank, dist, 'cpu')}\n")
+sys.stdout.flush()
 dist.barrier()
 dist.destroy_process_group()

@@ -2,6 +2,7 @@
 the reading of the committed ncu summary that feeds roofline.traffic."""
 import json
 import os
+import re
 import subprocess
 import sys
 
@@ -61,8 +62,8 @@ def _torchrun(script_args, nproc=2):
 def test_times_reduce_to_the_slowest_rank_over_gloo():
     r = _torchrun([os.path.join(ROOT, "tests", "dist_reduce_helper.py")])
     assert r.returncode == 0, r.stderr[-2000:]
-    got = sorted(line for line in r.stdout.splitlines() if line.startswith("rank "))
-    assert got == ["rank 0 max 2.0", "rank 1 max 2.0"]
+    got = sorted(re.findall(r"rank (\d+) max ([0-9.]+)", r.stdout))
+    assert got == [("0", "2.0"), ("1", "2.0")]
 
 
 def test_reference_arm_under_two_ranks_prints_one_line():
