@@ -224,9 +224,14 @@ def sss_cdf_loss_grad(theta, M, u, y, S, out_loss, out_grad, stream=None):
 
 
 def sss_set_options(opt: sss_options = None, **kw):
+    """Set the library options: opt (or the current options) with the
+    fields named in kw replaced; unknown field names raise TypeError."""
     if opt is None:
         opt = sss_get_options()
+    names = {f for f, _ in sss_options._fields_}
     for k, v in kw.items():
+        if k not in names:
+            raise TypeError(f"sss_options has no field {k!r}")
         setattr(opt, k, v)
     _check(load().sss_set_options(ctypes.byref(opt)))
 

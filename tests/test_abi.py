@@ -79,6 +79,9 @@ def test_options_roundtrip_and_validation(lib):
         sss.sss_set_options(bad)
     sss.sss_set_options(o)
     assert sss.sss_get_options().k_max == 10
+    with pytest.raises(TypeError):
+        sss.sss_set_options(medium_threshhold=4096)  # misspelt field: rejected, not ignored
+    assert sss.sss_get_options().medium_threshold == o.medium_threshold
 
 
 def test_empty_input_is_a_noop(lib):
