@@ -69,17 +69,25 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle child (no D, no cpu_baseline)")
     ap.add_argument("--n", type=int, default=None,
                     help="sort only the first n strings of the workload's generator (profiling runs)")
-    ap.add_argument("--legs", default="host,keys8,equal,learned,batched,alphabet",
-                    help="extra measurements beside the headline: host,keys8,equal,learned,batched,alphabet "
-                         "(or none)")
+    ap.add_argument("--legs", default="host,keys8,equal,learned,batched,alphabet,uniform,literal",
+                    help="extra measurements beside the headline: host,keys8,equal,learned,batched,alphabet,"
+                         "uniform,literal (or none)")
     return ap.parse_args()
 
 
 # ------------------------------------------------------------------ oracle child
 
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
 def _oracle_child(workload: str, sample: int, n, q):
-    """Runs in a spawned process: D of the whole workload and the oracle's
-    time on a bounded sample of it."""
+    """Runs in a spawned process: D of the whole workload, and the oracle's
+    time on a bounded sample of it, single-threaded and on every host core
+    (sample-cut ranges sorted on threads of their own)."""
     import oracle
     try:
         s = gen.workload(workload, n=n)
@@ -88,10 +96,15 @@ def _oracle_child(workload: str, sample: int, n, q):
         t0 = time.perf_counter()
         perm, lcp = oracle.sort(sub.chars, sub.offsets)
         t = time.perf_counter() - t0
+        cores = host_cores()
+        t0 = time.perf_counter()
+        oracle.sort_parallel(sub.chars, sub.offsets, cores)
+        tp = time.perf_counter() - t0
         if m < s.n:
-            perm, lcp = oracle.sort(s.chars, s.offsets)
+            perm, lcp = oracle.sort_parallel(s.chars, s.offsets, cores)
         D = oracle.dist_prefix(s.chars, s.offsets, perm, lcp)
-        q.put({"D": int(D), "N": int(s.total), "cpu_s": t, "cpu_n": m, "n": s.n})
+        q.put({"D": int(D), "N": int(s.total), "cpu_s": t, "cpu_par_s": tp, "cpu_cores": cores, "cpu_n": m,
+               "n": s.n})
     except Exception as e:  # reported, never fatal to the GPU measurement
         q.put({"error": repr(e)})
 
@@ -199,28 +212,34 @@ def ncu_traffic(kernel: str, workload: str):
 # ------------------------------------------------------------------ reference arm
 
 def run_reference(args, rank):
+    """The CPU oracle as it stands, on every host core of rank 0's machine
+    (sample-cut ranges, each sorted by the multikey quicksort on a thread of
+    its own, then the LCP scan), on a bounded sample of the workload; each
+    step sorts the sample once, and the line reports the median step."""
     if rank != 0:
         return 0
     import oracle
-    s = gen.workload(args.workload)
-    m = min(args.cpu_sample, s.n)
-    sub = gen.workload(args.workload, n=m) if m < s.n else s
-    for _ in range(max(0, args.warmup)):
-        oracle.sort(sub.chars, sub.offsets)
+    m = min(args.cpu_sample, gen.WORKLOADS[args.workload]["n"])
+    sub = gen.workload(args.workload, n=m)
+    cores = host_cores()
+    steps = max(1, args.steps)
+    for _ in range(max(0, min(args.warmup, 3))):
+        oracle.sort_parallel(sub.chars, sub.offsets, cores)
     times = []
-    for _ in range(args.steps):
+    for _ in range(steps):
         t0 = time.perf_counter()
-        oracle.sort(sub.chars, sub.offsets)
+        oracle.sort_parallel(sub.chars, sub.offsets, cores)
         times.append(time.perf_counter() - t0)
-    t = sum(times) / len(times)
+    t = statistics.median(times)
     v = m / t
-    sample = f"first {m} strings of the {args.workload} workload per step (same generator and seed)"
+    sample = (f"first {m} strings of the {args.workload} workload per step (same generator and seed), "
+              f"{cores} host threads")
     line = {"impl": "reference", "metric": "sorted strings/s", "value": v, "unit": "strings/s", "n_gpus": 0,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": {"workload": args.workload, "description": WORKLOAD_TEXT.get(args.workload, ""),
                        "n": m},
-            "cpu_baseline": {"value": v, "unit": "strings/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": v, "unit": "strings/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "strings/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -240,19 +259,31 @@ def reduce_max(value: float, dist, device) -> float:
     return float(t.item())
 
 
-def _timed(torch, stream, dev, fn, steps, dist):
-    """Mean ms per call of fn over `steps` calls (CUDA events on stream), max over ranks."""
+def _step_times(torch, stream, dev, fn, steps, dist, after=None):
+    """ms of each of `steps` calls of fn (a CUDA event pair around each call
+    on stream), bracketed by a barrier and a synchronize on both sides.
+    after(i), if given, runs on the host after call i (not between its
+    events' records on the device, which the host does not wait for)."""
     if dist:
         dist.barrier()
     torch.cuda.synchronize(dev)
-    a = torch.cuda.Event(enable_timing=True)
-    b = torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    for _ in range(steps):
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        ev[i][0].record(stream)
         fn()
-    b.record(stream)
+        ev[i][1].record(stream)
+        if after:
+            after(i)
     torch.cuda.synchronize(dev)
-    return reduce_max(a.elapsed_time(b) / max(1, steps), dist, dev)
+    if dist:
+        dist.barrier()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def _timed(torch, stream, dev, fn, steps, dist):
+    """Median ms per call of fn over `steps` calls, max over ranks."""
+    t = _step_times(torch, stream, dev, fn, max(1, steps), dist)
+    return reduce_max(statistics.median(t), dist, dev)
 
 
 def leg_host(sss, torch, chars, offsets, perm, lcp, n, stream, dev, args, world, dist):
@@ -328,6 +359,19 @@ def leg_learned(sss, torch, stream, dev, args, world, dist):
     sss.sss_set_options(o)
     steps = max(3, args.steps // 6)
     out = {"workload": WORKLOAD_TEXT["url-64m"], "n": n, "chars_bytes": int(s.total)}
+    # the plain sort in its headline form (graph, default key width) on the same input
+    g = sss.sss_options.from_buffer_copy(saved)
+    g.graph, g.profile = 1, 0
+    sss.sss_set_options(g)
+    fn = lambda: sss.sss_sort(chars, offsets, n, perm, lcp, stream)
+    for _ in range(max(2, args.warmup)):
+        fn()
+    ms = _timed(torch, stream, dev, fn, steps, dist)
+    st = sss.sss_get_last_stats()
+    out["graph_form"] = {"value": n * world / (ms * 1e-3), "unit": "strings/s", "ms_per_step": ms, "steps": steps,
+                         "key_bytes": int(g.key_bytes), "rounds": int(st.rounds),
+                         "gpu_launches_per_step": int(st.launches)}
+    sss.sss_set_options(o)
     for name, fn in (("tree", lambda: sss.sss_sort(chars, offsets, n, perm, lcp, stream)),
                      ("learned", lambda: sss.sss_sort_learned(chars, offsets, n, perm, lcp, stream))):
         for _ in range(max(2, args.warmup)):
@@ -346,6 +390,7 @@ def leg_learned(sss, torch, stream, dev, args, world, dist):
              "classify_ms": prof.get("classify", {}).get("ms"), "scatter_ms": prof.get("scatter", {}).get("ms")}
         if name == "learned":
             r.update({"proposals": int(st.learned_keys), "misses": int(st.learned_misses),
+                      "models": int(st.learned_models),
                       "miss_rate": (st.learned_misses / st.learned_keys) if st.learned_keys else None,
                       "fit_ms": prof.get("learned", {}).get("ms"),
                       "cdf_segments": int(o.cdf_segments), "cdf_steps": int(o.cdf_steps)})
@@ -444,6 +489,88 @@ def leg_batched(sss, torch, stream, dev, args, world, dist):
                       "tuning_ms": tune_ms}}
 
 
+def leg_uniform(sss, torch, stream, dev, args, world, dist):
+    """The small configured workload (100k strings of 8-20 letters, 1.5 MB:
+    it lives in L2 and the sort is bound by launch and round latency, so it
+    is reported, not judged), graph form."""
+    s = gen.workload("uniform-100k")
+    n = s.n
+    chars = torch.from_numpy(s.chars).to(dev)
+    offsets = torch.from_numpy(s.offsets.view(np.int64)).to(dev)
+    perm = torch.empty(n, dtype=torch.int32, device=dev)
+    lcp = torch.empty(n, dtype=torch.int32, device=dev)
+    saved = sss.sss_get_options()
+    o = sss.sss_options.from_buffer_copy(saved)
+    o.graph, o.profile = 1, 0
+    sss.sss_set_options(o)
+    fn = lambda: sss.sss_sort(chars, offsets, n, perm, lcp, stream)
+    for _ in range(max(3, args.warmup)):
+        fn()
+    steps = max(5, args.steps)
+    ms = _timed(torch, stream, dev, fn, steps, dist)
+    st = sss.sss_get_last_stats()
+    sss.sss_set_options(saved)
+    return {"workload": WORKLOAD_TEXT["uniform-100k"], "n": n, "chars_bytes": int(s.total),
+            "value": n * world / (ms * 1e-3), "unit": "strings/s", "ms_per_step": ms, "steps": steps,
+            "rounds": int(st.rounds), "gpu_launches_per_step": int(st.launches),
+            "l2": "inputs fit in L2 (no flush): reported, not judged"}
+
+
+def leg_literal(sss, torch, stream, dev, args, world, dist):
+    """The batch as configured: 10,000 sets, sizes log-uniform in [100, 1M]
+    (1.09 G strings, about 51 GB of characters), one graph launch with the
+    default options, against one sss_sort call per set (host-driven rounds),
+    all sets once."""
+    w = gen.BATCH_WORKLOADS["sets-literal"]
+    sizes, _ = gen.batch_sizes(w["num_sets"], w["lo"], w["hi"], w["seed"])
+    n = int(sizes.sum())
+    torch.cuda.empty_cache()
+    sss.sss_release()
+    free, _ = torch.cuda.mem_get_info(dev)
+    need = 52e9 + 16 * n + sss.sss_workspace_size(n)
+    if free < need:
+        return {"skipped": f"needs about {need / 1e9:.0f} GB of device memory, {free / 1e9:.0f} GB free"}
+    t0 = time.perf_counter()
+    b = gen.generate_batch(w["num_sets"], w["lo"], w["hi"], w["seed"])
+    gen_s = time.perf_counter() - t0
+    s = b.strings
+    chars = torch.from_numpy(s.chars).to(dev)
+    off = torch.from_numpy(s.offsets.view(np.int64)).to(dev)
+    perm = torch.empty(n, dtype=torch.int32, device=dev)
+    lcp = torch.empty(n, dtype=torch.int32, device=dev)
+    saved = sss.sss_get_options()
+    o = sss.sss_options.from_buffer_copy(saved)
+    o.profile = 0
+    sss.sss_set_options(o)
+    fn = lambda: sss.sss_sort_batched(chars, off, n, b.set_begin, w["num_sets"], perm, lcp, stream)
+    fn()
+    steps = max(3, min(5, args.steps))
+    ms = _timed(torch, stream, dev, fn, steps, dist)
+    st = sss.sss_get_last_stats()
+    sb = b.set_begin.astype(np.int64)
+
+    def per_set():
+        for j in range(w["num_sets"]):
+            lo, hi = int(sb[j]), int(sb[j + 1])
+            sss.sss_sort(chars, off[lo:], hi - lo, perm[lo:], lcp[lo:], stream)
+
+    o.graph = 0
+    sss.sss_set_options(o)
+    ms_ps = _timed(torch, stream, dev, per_set, 1, dist)
+    sss.sss_set_options(saved)
+    out = {"workload": "sets-literal: 10,000 sets, sizes log-uniform 100-1,000,000, kinds uniform over "
+                       "uniform/url/dna, seed 5", "n": n, "chars_bytes": int(s.total),
+           "largest_set": int(sizes.max()), "generate_s": gen_s,
+           "value": n * world / (ms * 1e-3), "unit": "strings/s", "ms_per_step": ms, "steps": steps,
+           "graph_launches_per_step": 1, "kernel_launches_per_step": int(st.launches), "rounds": int(st.rounds),
+           "options": "defaults (no autotuning: a tuning batch of this size would be another 51 GB)",
+           "per_set_value": n * world / (ms_ps * 1e-3), "per_set_ms": ms_ps, "speedup_vs_per_set": ms_ps / ms}
+    del chars, off, perm, lcp, b
+    torch.cuda.empty_cache()
+    sss.sss_release()
+    return out
+
+
 # ------------------------------------------------------------------ gpu arm
 
 def main():
@@ -489,24 +616,22 @@ def main():
         sort_fn(chars, offsets, n, perm, lcp, stream)
     torch.cuda.synchronize(dev)
 
-    launches = 0
+    launches = [0]
     clocks = ClockSampler(visible_gpu(local_rank))
     if dist:
         dist.barrier()
     torch.cuda.synchronize(dev)
     clocks.start()
     time.sleep(0.2)
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
-    t_start.record(stream)
-    for _ in range(args.steps):
-        sort_fn(chars, offsets, n, perm, lcp, stream)
-        launches += sss.sss_get_last_stats().launches
-    t_end.record(stream)
-    torch.cuda.synchronize(dev)
-    if dist:
-        dist.barrier()
-    ms = reduce_max(t_start.elapsed_time(t_end) / args.steps, dist, dev)
+
+    def count_launches(_i):
+        launches[0] += sss.sss_get_last_stats().launches
+
+    step_ms = _step_times(torch, stream, dev, lambda: sort_fn(chars, offsets, n, perm, lcp, stream), args.steps,
+                          dist, after=count_launches)
+    # the median step (max over ranks) is the headline; the mean beside it
+    ms = reduce_max(statistics.median(step_ms), dist, dev)
+    ms_mean = reduce_max(sum(step_ms) / len(step_ms), dist, dev)
 
     # second timed region, per-kernel times: the same sorts with the rounds
     # driven from the host and CUDA events around every kernel launch on the
@@ -573,6 +698,11 @@ def main():
         extra["batched"] = leg_batched(sss, torch, stream, dev, args, world, dist)
     if "alphabet" in legs:
         extra["alphabet"] = leg_alphabet(sss, torch, stream, dev, args, world, dist)
+    if "uniform" in legs:
+        extra["uniform_100k"] = leg_uniform(sss, torch, stream, dev, args, world, dist)
+    if "literal" in legs:
+        del chars, offsets, perm, lcp
+        extra["batched_literal"] = leg_literal(sss, torch, stream, dev, args, world, dist)
 
     if rank != 0:
         if dist:
@@ -626,13 +756,18 @@ def main():
     if oracle_info and "error" not in oracle_info:
         D = oracle_info["D"]
         cpu = {"value": oracle_info["cpu_n"] / oracle_info["cpu_s"], "unit": "strings/s", "cores": 1,
-               "kind": "oracle",
+               "host_cores": oracle_info["cpu_cores"], "kind": "oracle",
                "sample": (f"first {oracle_info['cpu_n']} strings of the {args.workload} workload "
-                          f"(same generator and seed), one sort, single thread")}
+                          f"(same generator and seed), one sort, single thread"),
+               "parallel": {"value": oracle_info["cpu_n"] / oracle_info["cpu_par_s"], "unit": "strings/s",
+                            "cores": oracle_info["cpu_cores"], "kind": "oracle",
+                            "sample": "the same strings, sample-cut ranges sorted on one thread per host core"}}
     value = n * world / (ms * 1e-3)
     line = {
         "metric": "sorted strings/s", "value": value, "unit": "strings/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "ms_per_step_mean": ms_mean,
+        "timing": "median of the per-step CUDA-event times (each step one sort), max over ranks",
+        "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": args.workload, "description": WORKLOAD_TEXT.get(args.workload, ""),
                    "mode": args.mode, "form": "graph", "key_bytes": int(opts.key_bytes), "n": n, "chars_bytes": int(s.total),
@@ -646,7 +781,7 @@ def main():
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clk,
-        "gpu_launches": int(launches),
+        "gpu_launches": int(launches[0]),
         "kernels": kernel_share,
         "profiled_pass": {"form": "host-driven rounds, CUDA events around every launch", "steps": args.steps,
                           "ms_per_step": ms_profiled},

@@ -37,9 +37,13 @@ WORKLOADS = {
     "url-64m": dict(kind=2, n=64_000_000, seed=4),
 }
 
-# batched workload: 10,000 sets, sizes log-uniform in [100, 4000] (about 500M
-# characters in total), kinds uniform, seed 5
+# batched workloads, 10,000 sets each, kinds uniform, seed 5:
+#   sets-literal  sizes log-uniform in [100, 1,000,000] as configured
+#                 (1,092,616,105 strings, about 51 GB of characters)
+#   sets-10k      sizes log-uniform in [100, 4000], the reading that keeps the
+#                 configured total of about 500M characters
 BATCH_WORKLOADS = {
+    "sets-literal": dict(num_sets=10_000, lo=100, hi=1_000_000, seed=5),
     "sets-10k": dict(num_sets=10_000, lo=100, hi=4000, seed=5),
 }
 

@@ -144,7 +144,18 @@ typedef struct sss_stats {
     uint32_t alphabet_group;         /* characters packed per byte: g >= 2 when the strings
                                         were rewritten, 1 when the alphabet was too large,
                                         0 when the option is off */
+    uint32_t learned_models;         /* learned CDF models fitted (one per segment of a
+                                        device-wide round that got one) */
 } sss_stats;
+
+/* What the learned proposal did in the last sss_sort_learned call. */
+typedef struct sss_learned_stats {
+    uint64_t proposals;  /* keys the model proposed a bucket for */
+    uint64_t misses;     /* proposals the exact splitter check rejected (the tree decided) */
+    uint32_t models;     /* segment models fitted */
+    uint32_t pad;
+    double miss_rate;    /* misses / proposals, 0 without proposals */
+} sss_learned_stats;
 
 /* ---------------------------------------------------------------- sort */
 
@@ -178,9 +189,12 @@ int sss_sort_ws(const uint8_t* chars, const uint64_t* offsets, uint32_t n,
  * looks up the array's device address (cudaGetSymbolAddress); make that
  * first call before any stream capture on the device.  Every call shares the
  * one array and re-initialises what it reads, so calls that overlap on the
- * GPU (other streams, other threads bypassing the library mutex by sharing a
- * stream) race on it.  n above 65,536, or options whose scratch would exceed
- * the array, return SSS_ERR_TOO_LARGE. */
+ * GPU race on it.  The call returns only after its work on stream has
+ * finished (it reads each round's sizes back, and on an error it waits for
+ * the work it already queued), so two calls of this library never overlap;
+ * kernels a caller enqueues elsewhere that use the array's contents would.
+ * n above 65,536, or options whose scratch would exceed the array, return
+ * SSS_ERR_TOO_LARGE. */
 int sss_sort_noalloc(const uint8_t* chars, const uint64_t* offsets, uint32_t n,
                      uint32_t* out_perm, uint32_t* out_lcp, void* stream);
 
@@ -198,9 +212,12 @@ int sss_sort_host(const uint8_t* chars, uint64_t chars_bytes, const uint64_t* of
  * decided on the device, so the call makes one graph launch and one final
  * header readback (with options.profile = 1 the rounds are host-driven and
  * timed instead, as for sss_sort).  The instantiated graph is cached while the buffers,
- * sizes and options stay the same.  set_begin (host, num_sets + 1
- * entries, non-decreasing, set_begin[0] = 0, set_begin[num_sets] = n) gives
- * set j the strings with global index in [set_begin[j], set_begin[j+1]).
+ * sizes and options stay the same.  set_begin (host or device, num_sets + 1
+ * uint64 entries, non-decreasing, set_begin[0] = 0, set_begin[num_sets] = n)
+ * gives set j the strings with global index in [set_begin[j], set_begin[j+1]);
+ * a device array is read back once on stream (8 (num_sets + 1) bytes) before
+ * the sort.  n repeats the total so that the entries can be checked: a
+ * violation returns SSS_ERR_INVALID.
  * Outputs
  * are per set: for rank r inside set j (global position set_begin[j] + r),
  * out_perm holds the index relative to set_begin[j], and out_lcp is 0 at
@@ -236,10 +253,13 @@ int sss_autotune_batched(const uint8_t* chars, const uint64_t* offsets, uint32_t
  * GPU -- and classification first proposes a bucket from the model and
  * checks it exactly against the bounding splitters (and the neighbouring
  * intervals); only rejected proposals descend the splitter tree.  Output is
- * identical to sss_sort.  learned_keys and learned_misses of sss_stats
- * report the proposals and the rejected ones. */
+ * identical to sss_sort.  stats (host, nullable) receives the proposals,
+ * the rejected ones, their ratio and the number of models fitted (also in
+ * learned_keys, learned_misses and learned_models of sss_stats); it is
+ * written only on success. */
 int sss_sort_learned(const uint8_t* chars, const uint64_t* offsets, uint32_t n,
-                     uint32_t* out_perm, uint32_t* out_lcp, void* stream);
+                     uint32_t* out_perm, uint32_t* out_lcp, void* stream,
+                     sss_learned_stats* stats);
 
 /* ------------------------------------------------- single steps (testing) */
 

@@ -29,6 +29,13 @@
  *   oracle_select_splitters  the recursive duplicate-skipping splitter
  *                       choice of Sec. 3.1 "Implementation Details", laid
  *                       out as a perfect tree in level order plus in order.
+ *   oracle_sort_parallel  the same answer on several host threads: P - 1
+ *                       splitter strings from a regular sample cut the
+ *                       order into P independent ranges (a sample sort's
+ *                       top level, Sec. 2.3), each range is sorted by
+ *                       oracle_sort on its own thread, then the LCP scan.
+ *                       Only a timing baseline; its output is pinned to
+ *                       oracle_sort's.
  *   oracle_cdf_*        the monotone piecewise-linear CDF used to propose
  *                       buckets (an addition to the paper): forward, MSE
  *                       loss and its analytic gradient, in double.
@@ -39,6 +46,7 @@
 #include <stdlib.h>
 #include <string.h>
 #include <math.h>
+#include <pthread.h>
 
 /* ------------------------------------------------------ helpers */
 
@@ -134,6 +142,186 @@ int oracle_sort(const uint8_t *chars, const uint64_t *offsets, uint32_t n, uint3
     }
     free(st);
     return 0;
+}
+
+/* ------------------------------------------------------ parallel sort */
+
+void oracle_lcp_scan(const uint8_t *chars, const uint64_t *offsets, uint32_t n, const uint32_t *perm, uint32_t *lcp);
+static uint32_t lcp_pair(const uint8_t *chars, const uint64_t *offsets, uint32_t a, uint32_t b);
+
+/* unsigned-byte comparison of whole strings: <0, 0, >0 */
+static int str_cmp(const uint8_t *p, const uint8_t *q) {
+    for (;; p++, q++) {
+        if (*p != *q) return *p < *q ? -1 : 1;
+        if (*p == 0) return 0;
+    }
+}
+
+typedef struct {
+    const uint8_t *chars;
+    const uint64_t *offsets;
+    const uint32_t *members;  /* original indices, ascending, range by range */
+    const uint64_t *start;    /* [P + 1] first member of each range */
+    uint32_t *perm;           /* output: sorted original indices */
+    uint32_t P;
+    volatile int next;        /* next range to take (under mu) */
+    int err;
+    pthread_mutex_t mu;
+} par_job;
+
+static void *par_worker(void *arg) {
+    par_job *J = (par_job *)arg;
+    for (;;) {
+        pthread_mutex_lock(&J->mu);
+        int r = J->next < (int)J->P ? J->next++ : -1;
+        pthread_mutex_unlock(&J->mu);
+        if (r < 0) break;
+        uint64_t lo = J->start[r], m = J->start[r + 1] - lo;
+        if (m == 0) continue;
+        /* the range's strings as a set of their own: local index k is the
+         * k-th smallest original index, so oracle_sort's tie-break by local
+         * index is the tie-break by original index */
+        uint64_t *off = (uint64_t *)malloc(m * sizeof(uint64_t));
+        uint32_t *lp = (uint32_t *)malloc(m * sizeof(uint32_t));
+        if (!off || !lp) { free(off); free(lp); J->err = -2; continue; }
+        for (uint64_t k = 0; k < m; k++) off[k] = J->offsets[J->members[lo + k]];
+        if (oracle_sort(J->chars, off, (uint32_t)m, lp) != 0) J->err = -2;
+        for (uint64_t k = 0; k < m; k++) J->perm[lo + k] = J->members[lo + lp[k]];
+        free(off);
+        free(lp);
+    }
+    return NULL;
+}
+
+/* f(arg, t) for t = 0..threads-1, each on a thread of its own */
+typedef struct { void *(*f)(void *); void *arg; uint32_t t; } slice_t;
+static void *slice_main(void *p) {
+    slice_t *s = (slice_t *)p;
+    void *(*f)(void *) = s->f;
+    return f(s);
+}
+static int run_threads(int threads, void *(*f)(void *), void *arg) {
+    pthread_t *th = (pthread_t *)malloc((size_t)threads * sizeof(pthread_t));
+    slice_t *sl = (slice_t *)malloc((size_t)threads * sizeof(slice_t));
+    char *ok = (char *)calloc((size_t)threads, 1);
+    if (!th || !sl || !ok) { free(th); free(sl); free(ok); return -2; }
+    for (int t = 0; t < threads; t++) {
+        sl[t] = (slice_t){f, arg, (uint32_t)t};
+        ok[t] = pthread_create(&th[t], NULL, slice_main, &sl[t]) == 0;
+        if (!ok[t]) slice_main(&sl[t]);
+    }
+    for (int t = 0; t < threads; t++)
+        if (ok[t]) pthread_join(th[t], NULL);
+    free(th); free(sl); free(ok);
+    return 0;
+}
+
+/* contiguous slice t of [0, n) for `parts` slices */
+static void slice_bounds(uint32_t n, uint32_t parts, uint32_t t, uint32_t *lo, uint32_t *hi) {
+    *lo = (uint32_t)((uint64_t)n * t / parts);
+    *hi = (uint32_t)((uint64_t)n * (t + 1) / parts);
+}
+
+typedef struct {
+    const uint8_t *chars; const uint64_t *offsets; const uint8_t **x; uint32_t P;
+    uint32_t *part; uint32_t n, parts;
+} range_job;
+static void *range_worker(void *p) {
+    slice_t *s = (slice_t *)p;
+    range_job *R = (range_job *)s->arg;
+    uint32_t lo, hi;
+    slice_bounds(R->n, R->parts, s->t, &lo, &hi);
+    for (uint32_t i = lo; i < hi; i++) {
+        const uint8_t *sp = R->chars + R->offsets[i];
+        uint32_t a = 0, b = R->P - 1;
+        while (a < b) {
+            uint32_t mid = (a + b) / 2;
+            if (str_cmp(R->x[mid], sp) < 0) a = mid + 1; else b = mid;
+        }
+        R->part[i] = a;
+    }
+    return NULL;
+}
+
+typedef struct {
+    const uint8_t *chars; const uint64_t *offsets; const uint32_t *perm; uint32_t *lcp;
+    uint32_t n, parts;
+} lcp_job;
+static void *lcp_worker(void *p) {
+    slice_t *s = (slice_t *)p;
+    lcp_job *L = (lcp_job *)s->arg;
+    uint32_t lo, hi;
+    slice_bounds(L->n, L->parts, s->t, &lo, &hi);
+    for (uint32_t i = lo; i < hi; i++)
+        L->lcp[i] = i == 0 ? 0u : lcp_pair(L->chars, L->offsets, L->perm[i - 1], L->perm[i]);
+    return NULL;
+}
+
+/* perm and lcp as oracle_sort + oracle_lcp_scan give them, computed on
+ * `threads` host threads.  Range r holds the strings s with
+ * x_{r-1} < s <= x_r for sample strings x_0 <= ... <= x_{P-2}, so equal
+ * strings share a range and the ranges follow one another in the sorted
+ * order.  Returns 0, or -2 when memory runs out. */
+int oracle_sort_parallel(const uint8_t *chars, const uint64_t *offsets, uint32_t n, uint32_t *perm,
+                         uint32_t *lcp, int threads) {
+    if (threads < 1) threads = 1;
+    uint32_t P = (uint32_t)threads * 8u;
+    if (n < 4096u || threads == 1) {
+        if (oracle_sort(chars, offsets, n, perm) != 0) return -2;
+        oracle_lcp_scan(chars, offsets, n, perm, lcp);
+        return 0;
+    }
+    /* splitters: every (m/P)-th string of a sorted regular sample of m strings */
+    uint32_t m = P * 32u;
+    uint64_t *soff = (uint64_t *)malloc(m * sizeof(uint64_t));
+    uint32_t *sperm = (uint32_t *)malloc(m * sizeof(uint32_t));
+    const uint8_t **x = (const uint8_t **)malloc(P * sizeof(uint8_t *));
+    uint32_t *part = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+    uint64_t *start = (uint64_t *)calloc(P + 1, sizeof(uint64_t));
+    uint32_t *members = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+    int rc = -2;
+    if (!soff || !sperm || !x || !part || !start || !members) goto out;
+    for (uint32_t j = 0; j < m; j++) soff[j] = offsets[(uint64_t)j * n / m];
+    if (oracle_sort(chars, soff, m, sperm) != 0) goto out;
+    for (uint32_t r = 1; r < P; r++) x[r - 1] = chars + soff[sperm[(uint64_t)r * m / P]];
+    /* range of each string: the number of splitters below it */
+    {
+        range_job R = {chars, offsets, x, P, part, n, (uint32_t)threads};
+        if (run_threads(threads, range_worker, &R) != 0) goto out;
+    }
+    for (uint32_t i = 0; i < n; i++) start[part[i] + 1]++;
+    for (uint32_t r = 0; r < P; r++) start[r + 1] += start[r];
+    {
+        uint64_t *fill = (uint64_t *)malloc(P * sizeof(uint64_t));
+        if (!fill) goto out;
+        memcpy(fill, start, P * sizeof(uint64_t));
+        for (uint32_t i = 0; i < n; i++) members[fill[part[i]]++] = i;  /* ascending index per range */
+        free(fill);
+    }
+    {
+        par_job J;
+        J.chars = chars; J.offsets = offsets; J.members = members; J.start = start; J.perm = perm;
+        J.P = P; J.next = 0; J.err = 0;
+        pthread_mutex_init(&J.mu, NULL);
+        pthread_t *th = (pthread_t *)malloc((size_t)threads * sizeof(pthread_t));
+        if (!th) { pthread_mutex_destroy(&J.mu); goto out; }
+        int started = 0;
+        for (int t = 0; t < threads; t++)
+            if (pthread_create(&th[t], NULL, par_worker, &J) == 0) started++;
+        if (started == 0) par_worker(&J);
+        for (int t = 0; t < started; t++) pthread_join(th[t], NULL);
+        free(th);
+        pthread_mutex_destroy(&J.mu);
+        if (J.err) goto out;
+    }
+    {
+        lcp_job Lj = {chars, offsets, perm, lcp, n, (uint32_t)threads};
+        if (run_threads(threads, lcp_worker, &Lj) != 0) goto out;
+    }
+    rc = 0;
+out:
+    free(soff); free(sperm); free(x); free(part); free(start); free(members);
+    return rc;
 }
 
 /* ------------------------------------------------------ lcp */

@@ -24,7 +24,7 @@ __all__ = [
     "sss_cdf_loss_grad",
     "sss_set_options", "sss_get_options", "sss_get_last_stats", "sss_get_last_timeline", "sss_last_error",
     "sss_release",
-    "sss_version", "sss_options", "sss_stats", "load", "lib_path", "sort", "sss_autotune_batched",
+    "sss_version", "sss_options", "sss_stats", "sss_learned_stats", "load", "lib_path", "sort", "sss_autotune_batched",
 ]
 
 STATUS = {0: "SSS_OK", -1: "SSS_ERR_INVALID", -2: "SSS_ERR_NOMEM", -3: "SSS_ERR_CUDA",
@@ -61,7 +61,8 @@ class sss_stats(ctypes.Structure):
                 ("prof_ms", ctypes.c_double * len(K_CLASSES)),
                 ("round_segments", ctypes.c_uint32 * MAX_ROUNDS_LOGGED),
                 ("round_active", ctypes.c_uint32 * MAX_ROUNDS_LOGGED),
-                ("alphabet_symbols", ctypes.c_uint32), ("alphabet_group", ctypes.c_uint32)]
+                ("alphabet_symbols", ctypes.c_uint32), ("alphabet_group", ctypes.c_uint32),
+                ("learned_models", ctypes.c_uint32)]
 
     def as_dict(self):
         r = self.rounds
@@ -76,7 +77,13 @@ class sss_stats(ctypes.Structure):
                              for i in range(len(K_CLASSES))} if self.profiled else None),
                 "round_segments": list(self.round_segments)[:min(r, MAX_ROUNDS_LOGGED)],
                 "round_active": list(self.round_active)[:min(r, MAX_ROUNDS_LOGGED)],
-                "alphabet_symbols": self.alphabet_symbols, "alphabet_group": self.alphabet_group}
+                "alphabet_symbols": self.alphabet_symbols, "alphabet_group": self.alphabet_group,
+                "learned_models": self.learned_models}
+
+
+class sss_learned_stats(ctypes.Structure):
+    _fields_ = [("proposals", ctypes.c_uint64), ("misses", ctypes.c_uint64), ("models", ctypes.c_uint32),
+                ("pad", ctypes.c_uint32), ("miss_rate", ctypes.c_double)]
 
 
 _lib = None
@@ -90,7 +97,7 @@ _SIG = {
     "sss_sort_host": ([_P, ctypes.c_uint64, _P, ctypes.c_uint32, _P, _P], ctypes.c_int),
     "sss_sort_noalloc": ([_P, _P, ctypes.c_uint32, _P, _P, _P], ctypes.c_int),
     "sss_sort_batched": ([_P, _P, ctypes.c_uint32, _P, ctypes.c_uint32, _P, _P, _P], ctypes.c_int),
-    "sss_sort_learned": ([_P, _P, ctypes.c_uint32, _P, _P, _P], ctypes.c_int),
+    "sss_sort_learned": ([_P, _P, ctypes.c_uint32, _P, _P, _P, ctypes.POINTER(sss_learned_stats)], ctypes.c_int),
     "sss_autotune_batched": ([_P, _P, ctypes.c_uint32, _P, ctypes.c_uint32, _P, _P, ctypes.c_char_p,
                               ctypes.POINTER(sss_options), ctypes.POINTER(ctypes.c_double), _P], ctypes.c_int),
     "sss_gather_keys": ([_P, _P, _P, _P, ctypes.c_uint32, _P, _P], ctypes.c_int),
@@ -195,8 +202,11 @@ def sss_autotune_batched(chars, offsets, n, set_begin, num_sets, out_perm, out_l
 
 
 def sss_sort_learned(chars, offsets, n, out_perm, out_lcp, stream=None):
+    """Returns the call's sss_learned_stats."""
+    st = sss_learned_stats()
     _check(load().sss_sort_learned(_addr(chars), _addr(offsets), n, _addr(out_perm), _addr(out_lcp),
-                                   _stream(stream)))
+                                   _stream(stream), ctypes.byref(st)))
+    return st
 
 
 def sss_gather_keys(chars, offsets, idx, depth, n, out_keys, stream=None):

@@ -424,6 +424,7 @@ int run_sort(const Work& w, const sss_options& o, const Seg* roots_dev, uint32_t
     stats->base_iterations = hh->base_iters;
     stats->learned_keys = hh->learned_keys;
     stats->learned_misses = hh->learned_misses;
+    stats->learned_models = hh->learned_models;
     for (int i = 0; i < 8; i++) stats->base_segment_hist[i] = hh->small_hist[i];
     stats->launches = pf->launches;
     stats->profiled = pf->enabled ? 1u : 0u;
@@ -592,6 +593,7 @@ int run_sort_graph(const Work& w, const sss_options& o, const Seg* roots_dev, ui
     stats->base_iterations = hh->base_iters;
     stats->learned_keys = hh->learned_keys;
     stats->learned_misses = hh->learned_misses;
+    stats->learned_models = hh->learned_models;
     for (int i = 0; i < 8; i++) stats->base_segment_hist[i] = hh->small_hist[i];
     stats->launches = gc.launches_prologue + hh->round * gc.launches_body + gc.launches_epilogue;
     return SSS_OK;
@@ -671,6 +673,33 @@ int sort_common(const uint8_t* chars, const uint64_t* offsets, uint32_t n, uint3
     return SSS_OK;
 }
 
+
+// The set boundaries of a batched call as a host array: set_begin may point
+// to host or to device memory (a device array is copied, num_sets + 1
+// entries, on the caller's stream).  Checks set_begin[0] = 0,
+// set_begin[num_sets] = n and that it never decreases.
+int host_set_begin(const uint64_t* set_begin, uint32_t num_sets, uint32_t n, cudaStream_t st,
+                   std::vector<uint64_t>& out) {
+    if (!set_begin) return fail(SSS_ERR_INVALID, "null set_begin");
+    if (num_sets == 0xFFFFFFFFu) return fail(SSS_ERR_TOO_LARGE, "num_sets must be below 2^32 - 1");
+    out.resize((size_t)num_sets + 1);
+    cudaPointerAttributes a;
+    memset(&a, 0, sizeof(a));
+    const bool on_device = cudaPointerGetAttributes(&a, set_begin) == cudaSuccess &&
+                           (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged);
+    cudaGetLastError();
+    if (on_device) {
+        CK(cudaMemcpyAsync(out.data(), set_begin, 8ull * out.size(), cudaMemcpyDeviceToHost, st), "set_begin readback");
+        CK(cudaStreamSynchronize(st), "set_begin readback");
+    } else {
+        memcpy(out.data(), set_begin, 8ull * out.size());
+    }
+    if (out[0] != 0 || out[num_sets] != n) return fail(SSS_ERR_INVALID, "set_begin must start at 0 and end at n");
+    for (uint32_t j = 0; j < num_sets; j++)
+        if (out[j + 1] < out[j]) return fail(SSS_ERR_INVALID, "set_begin must be non-decreasing");
+    return SSS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -696,11 +725,10 @@ int sss_sort_ws(const uint8_t* chars, const uint64_t* offsets, uint32_t n, uint3
 int sss_sort_batched(const uint8_t* chars, const uint64_t* offsets, uint32_t n, const uint64_t* set_begin,
                      uint32_t num_sets, uint32_t* out_perm, uint32_t* out_lcp, void* stream) {
     std::lock_guard<std::mutex> g(g_mu);
-    if (!set_begin) return fail(SSS_ERR_INVALID, "null set_begin");
-    if (set_begin[0] != 0 || set_begin[num_sets] != n)
-        return fail(SSS_ERR_INVALID, "set_begin must start at 0 and end at n");
-    if (num_sets > n + 1u && n > 0) { /* empty sets are allowed */ }
-    return sort_common(chars, offsets, n, out_perm, out_lcp, nullptr, 0, set_begin, num_sets, stream);
+    std::vector<uint64_t> sb;
+    int rc = host_set_begin(set_begin, num_sets, n, (cudaStream_t)stream, sb);
+    if (rc) return rc;
+    return sort_common(chars, offsets, n, out_perm, out_lcp, nullptr, 0, sb.data(), num_sets, stream);
 }
 
 int sss_sort_host(const uint8_t* chars, uint64_t chars_bytes, const uint64_t* offsets, uint32_t n,
@@ -748,9 +776,19 @@ int sss_sort_host(const uint8_t* chars, uint64_t chars_bytes, const uint64_t* of
 }
 
 int sss_sort_learned(const uint8_t* chars, const uint64_t* offsets, uint32_t n, uint32_t* out_perm,
-                     uint32_t* out_lcp, void* stream) {
+                     uint32_t* out_lcp, void* stream, sss_learned_stats* stats) {
     std::lock_guard<std::mutex> g(g_mu);
-    return sort_common(chars, offsets, n, out_perm, out_lcp, nullptr, 0, nullptr, 0, stream, true);
+    const int rc = sort_common(chars, offsets, n, out_perm, out_lcp, nullptr, 0, nullptr, 0, stream, true);
+    if (rc == SSS_OK && stats) {
+        memset(stats, 0, sizeof(*stats));
+        if (n) {
+            stats->proposals = g_stats.learned_keys;
+            stats->misses = g_stats.learned_misses;
+            stats->models = g_stats.learned_models;
+            stats->miss_rate = g_stats.learned_keys ? (double)g_stats.learned_misses / (double)g_stats.learned_keys : 0.0;
+        }
+    }
+    return rc;
 }
 
 int sss_gather_keys(const uint8_t* chars, const uint64_t* offsets, const uint32_t* idx, const uint32_t* depth,
@@ -946,13 +984,17 @@ void cache_store(const char* path, const std::string& key, const sss_options& o,
 }  // namespace
 
 extern "C" int sss_autotune_batched(const uint8_t* chars, const uint64_t* offsets, uint32_t n,
-                                    const uint64_t* set_begin, uint32_t num_sets, uint32_t* out_perm,
+                                    const uint64_t* set_begin_arg, uint32_t num_sets, uint32_t* out_perm,
                                     uint32_t* out_lcp, const char* cache_path, sss_options* out_best,
                                     double* out_ms, void* stream) {
     std::lock_guard<std::mutex> g(g_mu);
-    if (!set_begin || !out_best) return fail(SSS_ERR_INVALID, "null pointer argument");
-    if (set_begin[0] != 0 || set_begin[num_sets] != n)
-        return fail(SSS_ERR_INVALID, "set_begin must start at 0 and end at n");
+    if (!out_best) return fail(SSS_ERR_INVALID, "null pointer argument");
+    std::vector<uint64_t> sb;
+    {
+        const int rc0 = host_set_begin(set_begin_arg, num_sets, n, (cudaStream_t)stream, sb);
+        if (rc0) return rc0;
+    }
+    const uint64_t* set_begin = sb.data();
     const std::string key = tune_key(n, num_sets);
     sss_options best = g_opt;
     double best_ms = 0.0;
@@ -1073,7 +1115,14 @@ extern "C" int sss_sort_noalloc(const uint8_t* chars, const uint64_t* offsets, u
     sss_stats stats;
     // serial round bodies: no library streams or events are created for it
     rc = run_sort(w, o, nullptr, 0, &g_noalloc_hdr[dev], (cudaStream_t)stream, &stats, false, false);
-    if (rc) return rc;
+    if (rc) {
+        // kernels of this call may still be queued: let them finish before
+        // the shared array can be handed to the next call (the status was
+        // already recorded)
+        cudaStreamSynchronize((cudaStream_t)stream);
+        cudaGetLastError();
+        return rc;
+    }
     g_stats = stats;
     return SSS_OK;
 }

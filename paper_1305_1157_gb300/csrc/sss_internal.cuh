@@ -82,7 +82,9 @@ struct SegPlan {
 // Device header: live append counters and the snapshot the host reads back.
 struct Hdr {
     // live, appended to by the round kernels
-    uint32_t n_large, n_med, n_small, n_bigrun, err, small_elems, med_elems, n_tiny, tiny_elems, pad0[3];
+    uint32_t n_large, n_med, n_small, n_bigrun, err, small_elems, med_elems, n_tiny, tiny_elems;
+    uint32_t learned_models;  // segment models fitted by k_cdf_fit
+    uint32_t pad0[2];
     // snapshot for the host, written by k_plan
     uint32_t L, total_chunks, total_counts, total_tree;
     uint32_t n_med_snap, n_small_snap, n_bigrun_snap, small_elems_snap;

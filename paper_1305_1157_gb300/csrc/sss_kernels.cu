@@ -183,6 +183,7 @@ __global__ void k_hdr_reset(Work w) {
     h->base_iters = 0ull;
     h->learned_keys = 0ull;
     h->learned_misses = 0ull;
+    h->learned_models = 0;
     h->round = 0;
     h->q_sample = 0; h->q_fit = 0; h->q_classify = 0; h->q_scatter = 0;
     h->q_med = 0; h->q_base = 0; h->q_bigrun = 0;

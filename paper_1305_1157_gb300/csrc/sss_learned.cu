@@ -246,6 +246,7 @@ __global__ void __launch_bounds__(kFitThreads) k_cdf_fit(Work w, Params p) {
         tab[M] = 1.0f;
         w.cdf_kmin[seg] = kmin;
         w.cdf_scale[seg] = scale;
+        atomicAdd(&w.hdr->learned_models, 1u);
     }
     __syncthreads();  // shared arrays are rewritten by the next segment
     }

@@ -99,6 +99,19 @@ def test_bad_splitter_arguments_are_rejected(lib):
     assert lib.sss_classify(None, 4, None, None, 11, None, None) == -1
 
 
+def test_batched_set_boundaries_are_checked_on_the_host(lib):
+    import numpy as np
+    P = ctypes.c_void_p
+    for sb, n in (([1, 5, 10], 10),    # does not start at 0
+                  ([0, 5, 9], 10),     # does not end at n
+                  ([0, 6, 5, 10], 10)):  # decreases
+        a = np.array(sb, dtype=np.uint64)
+        rc = lib.sss_sort_batched(P(1), P(1), n, a.ctypes.data, len(sb) - 1, P(1), P(1), None)
+        assert rc == -1, (sb, rc)
+        assert "set_begin" in sss.sss_last_error()
+    assert lib.sss_sort_batched(P(1), P(1), 10, None, 2, P(1), P(1), None) == -1
+
+
 def test_workspace_size_grows_with_n(lib):
     a, b = sss.sss_workspace_size(1000), sss.sss_workspace_size(1_000_000)
     assert 0 < a < b
@@ -125,7 +138,7 @@ int main(void) {{
     return {k: int(v) for k, v in (line.split() for line in out.splitlines())}
 
 
-@pytest.mark.parametrize("cls", [sss.sss_options, sss.sss_stats])
+@pytest.mark.parametrize("cls", [sss.sss_options, sss.sss_stats, sss.sss_learned_stats])
 def test_binding_structs_match_the_header_layout(cls, tmp_path):
     if shutil.which("gcc") is None:
         pytest.skip("no host C compiler")

@@ -53,6 +53,21 @@ def test_batch_recipe():
     assert b.set_begin[-1] == b.strings.n
 
 
+def test_literal_batch_sizes():
+    """The configured batch: 10,000 sets, sizes log-uniform in [100, 1M]
+    (mean (1M - 100) / ln(10^4), about 108.6k strings a set), kinds uniform."""
+    w = gen.BATCH_WORKLOADS["sets-literal"]
+    sizes, kinds = gen.batch_sizes(w["num_sets"], w["lo"], w["hi"], w["seed"])
+    assert len(sizes) == 10_000 and sizes.min() >= 100 and sizes.max() <= 1_000_000
+    assert int(sizes.sum()) == 1_092_616_105
+    assert abs(sizes.mean() / ((1e6 - 100) / np.log(1e4)) - 1) < 0.03
+    # log-uniform: each decade of sizes holds about a quarter of the sets
+    dec = np.histogram(np.log10(sizes), bins=[2, 3, 4, 5, 6.0001])[0]
+    assert (np.abs(dec / 10_000 - 0.25) < 0.03).all(), dec
+    assert all(abs(int((kinds == k).sum()) / 10_000 - 1 / 3) < 0.03 for k in (1, 2, 3))
+    assert sizes.max() < 2 ** 32 and int(sizes.sum()) < 2 ** 32 - 1
+
+
 def test_generators_are_deterministic_and_thread_independent():
     for kind in (1, 2, 3):
         a = gen.generate(kind, 20_000, 11, threads=1)

@@ -70,8 +70,12 @@ def _learned_sort(s):
     offsets = torch.from_numpy(s.offsets.view(np.int64)).cuda()
     perm = torch.full((s.n,), -1, dtype=torch.int32, device="cuda")
     lcp = torch.full((s.n,), -1, dtype=torch.int32, device="cuda")
-    sss.sss_sort_learned(chars, offsets, s.n, perm, lcp)
+    ls = sss.sss_sort_learned(chars, offsets, s.n, perm, lcp)
     torch.cuda.synchronize()
+    # the call's own stats out-parameter agrees with the library's last stats
+    st = sss.sss_get_last_stats()
+    assert (ls.proposals, ls.misses, ls.models) == (st.learned_keys, st.learned_misses, st.learned_models)
+    assert ls.miss_rate == pytest.approx(ls.misses / ls.proposals if ls.proposals else 0.0)
     return perm.cpu().numpy().view(np.uint32), lcp.cpu().numpy().view(np.uint32)
 
 
@@ -128,6 +132,6 @@ def test_learned_full_size_url_64m_verified():
     s = gen.workload("url-64m")
     perm, lcp = _learned_sort(s)
     st = sss.sss_get_last_stats()
-    assert st.learned_keys > 0 and st.learned_misses < st.learned_keys
+    assert st.learned_keys > 0 and st.learned_misses < st.learned_keys and st.learned_models >= 1
     code, bad = oracle.verify(s.chars, s.offsets, perm, lcp)
     assert code == 0, (oracle.VERIFY_CODES[code], bad)

@@ -420,3 +420,34 @@ def test_medium_rounds_step_over_shared_prefixes(key_bytes):
     perm, lcp = gpu_sort(s)
     assert_same(s, perm, lcp)
     assert sss.sss_get_last_stats().medium_refilled_strings > 0
+
+
+@pytest.mark.parametrize("opts", [dict(key_bytes=16), dict(key_bytes=8), dict(key_bytes=16, graph=1)])
+def test_offsets_beyond_4gib(opts):
+    """Strings placed after more than 4 GiB of other bytes in one chars
+    buffer (offsets >= 2^32, so every offset and address is 64-bit), mixed
+    with strings before that point; compared element by element with the
+    oracle on the same strings packed compactly (the answer does not depend
+    on where the strings lie)."""
+    pad = (1 << 32) + 4099  # odd, so the far strings start at every alignment
+    s = gen.generate(2, 60_000, 81)
+    cut = s.n // 3
+    head_bytes = int(s.offsets[cut])
+    if torch.cuda.mem_get_info()[0] < pad + 2 * len(s.chars) + (1 << 30):
+        pytest.skip("needs about 5 GB of device memory")
+    sss.sss_set_options(**opts)
+    chars = torch.zeros(pad + len(s.chars), dtype=torch.uint8, device="cuda")
+    body = torch.from_numpy(s.chars).cuda()
+    chars[:head_bytes] = body[:head_bytes]          # the first third below 4 GiB
+    chars[pad + head_bytes:] = body[head_bytes:]    # the rest beyond it
+    off = s.offsets.astype(np.uint64).copy()
+    off[cut:] += np.uint64(pad)
+    assert int(off[cut]) >= 2**32
+    offsets = torch.from_numpy(off.view(np.int64)).cuda()
+    perm = torch.full((s.n,), -1, dtype=torch.int32, device="cuda")
+    lcp = torch.full((s.n,), -1, dtype=torch.int32, device="cuda")
+    sss.sss_sort(chars, offsets, s.n, perm, lcp)
+    torch.cuda.synchronize()
+    del chars, body
+    torch.cuda.empty_cache()
+    assert_same(s, u32(perm), u32(lcp))

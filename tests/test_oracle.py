@@ -319,3 +319,22 @@ def test_cut_tree_keeps_the_nonempty_buckets():
         for i in range(len(keys) - 1):
             assert (full_b[i] == full_b[i + 1]) == (cut_b[i] == cut_b[i + 1])
         assert [b & 1 for b in full_b] == [b & 1 for b in cut_b]
+
+
+@pytest.mark.parametrize("threads", [1, 2, 5, 8])
+def test_parallel_oracle_equals_the_sequential_one(threads):
+    """The host-threaded baseline (sample-cut ranges, each sorted by the
+    multikey quicksort) gives exactly oracle.sort's answer: on the three
+    generator kinds, on input where most strings are equal (so one range
+    holds a long run of equal strings and many sample strings coincide), and
+    with empty strings."""
+    rng = random.Random(threads)
+    cases = [gen.generate(k, 30_000, 40 + k) for k in (1, 2, 3)]
+    items = [b"dup"] * 20_000 + [b""] * 500 + [bytes(rng.choice(b"ab") for _ in range(rng.randint(0, 6)))
+                                                for _ in range(9_000)]
+    rng.shuffle(items)
+    cases.append(gen.from_list(items))
+    for s in cases:
+        p1, l1 = oracle.sort(s.chars, s.offsets)
+        p2, l2 = oracle.sort_parallel(s.chars, s.offsets, threads)
+        assert np.array_equal(p1, p2) and np.array_equal(l1, l2)

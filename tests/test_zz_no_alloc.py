@@ -1,11 +1,14 @@
 """sss_sort_noalloc: the sort for callers that cannot allocate device memory
-(its scratch is a static device array of the library).  Its output must
-equal sss_sort's, exactly (integer work), on consecutive calls that reuse the
-same static scratch.  Kept in a file of its own, collected last."""
+(its scratch is a static device array of the library).  Its output must be
+the unique answer the oracle gives and equal sss_sort's, exactly (integer
+work), on consecutive calls that reuse the same static scratch, and the calls
+must not take any device memory.  Kept in a file of its own, collected last.
+"""
 import numpy as np
 import pytest
 
 import gen
+import oracle
 import paper_1305_1157_gb300 as sss
 from paper_1305_1157_gb300 import build as sbuild
 
@@ -21,30 +24,51 @@ def built():
     sss.load()
 
 
-def _dev(s):
-    return (torch.from_numpy(s.chars).cuda(), torch.from_numpy(s.offsets.view(np.int64)).cuda())
-
-
-def _run(fn, s):
-    chars, offsets = _dev(s)
+def _buffers(s):
+    chars = torch.from_numpy(s.chars).cuda()
+    offsets = torch.from_numpy(s.offsets.view(np.int64)).cuda()
     perm = torch.full((s.n,), -1, dtype=torch.int32, device="cuda")
     lcp = torch.full((s.n,), -1, dtype=torch.int32, device="cuda")
-    fn(chars, offsets, s.n, perm, lcp)
-    torch.cuda.synchronize()
-    return perm.cpu().numpy().view(np.uint32), lcp.cpu().numpy().view(np.uint32)
+    return chars, offsets, perm, lcp
 
 
-def test_noalloc_matches_sss_sort_on_two_calls_in_a_row():
+def _u32(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+def test_noalloc_matches_oracle_and_sss_sort_on_two_calls_in_a_row():
     inputs = [gen.generate(2, MAX_STRINGS, 71), gen.generate(3, 40_000, 72)]
-    got = [_run(sss.sss_sort_noalloc, s) for s in inputs]  # back to back on the shared scratch
-    for s, (perm, lcp) in zip(inputs, got):
-        ref_perm, ref_lcp = _run(sss.sss_sort, s)
-        assert np.array_equal(perm, ref_perm)
-        assert np.array_equal(lcp, ref_lcp)
+    bufs = [_buffers(s) for s in inputs]
+    # a first pass loads the library's kernels (module loading may take
+    # device memory once per process); then no cached workspace is left, so
+    # a call that fell back to the allocating path would show up below
+    for s, (chars, offsets, perm, lcp) in zip(inputs, bufs):
+        sss.sss_sort_noalloc(chars, offsets, s.n, perm, lcp)
+    torch.cuda.synchronize()
+    sss.sss_release()
+    torch.cuda.synchronize()
+    free_before, _ = torch.cuda.mem_get_info()
+    for s, (chars, offsets, perm, lcp) in zip(inputs, bufs):  # back to back on the shared scratch
+        sss.sss_sort_noalloc(chars, offsets, s.n, perm, lcp)
+    torch.cuda.synchronize()
+    free_after, _ = torch.cuda.mem_get_info()
+    assert free_after == free_before, f"device memory changed by {free_before - free_after} bytes"
+    for s, (chars, offsets, perm, lcp) in zip(inputs, bufs):
+        got_perm, got_lcp = _u32(perm), _u32(lcp)
+        ref_perm, ref_lcp = oracle.sort(s.chars, s.offsets)
+        assert np.array_equal(got_perm, ref_perm)
+        assert np.array_equal(got_lcp, ref_lcp)
+        p2 = torch.full((s.n,), -1, dtype=torch.int32, device="cuda")
+        l2 = torch.full((s.n,), -1, dtype=torch.int32, device="cuda")
+        sss.sss_sort(chars, offsets, s.n, p2, l2)
+        torch.cuda.synchronize()
+        assert np.array_equal(got_perm, _u32(p2))
+        assert np.array_equal(got_lcp, _u32(l2))
 
 
 def test_noalloc_rejects_more_than_its_maximum():
     s = gen.generate(1, MAX_STRINGS + 1, 73)
+    chars, offsets, perm, lcp = _buffers(s)
     with pytest.raises(sss.SSSError) as e:
-        _run(sss.sss_sort_noalloc, s)
+        sss.sss_sort_noalloc(chars, offsets, s.n, perm, lcp)
     assert e.value.code == -5
