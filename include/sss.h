@@ -55,8 +55,8 @@ typedef enum {
 } sss_status;
 
 /* Tuning knobs.  Defaults: k_max 10, base_threshold 128, medium_threshold
- * 8192, chunk 16384, seed 0x5eed, cdf_segments 4096, cdf_steps 16,
- * cdf_lr 0.05, profile 0, graph 0, key_bytes 16, classifier 0, alphabet 0. */
+ * 8192, chunk 32768, seed 0x5eed, cdf_segments 4096, cdf_steps 4,
+ * cdf_lr 0.005, profile 0, graph 0, key_bytes 16, classifier 0, alphabet 0. */
 typedef struct sss_options {
     int32_t k_max;             /* largest splitter tree depth k: v = 2^k - 1 splitters, 1..10 */
     uint32_t base_threshold;   /* buckets of at most this many strings go to the base case, 16..128 */
@@ -66,8 +66,9 @@ typedef struct sss_options {
                                   multiple of 2048 */
     uint64_t seed;           /* seed of the pseudo-random sample positions */
     uint32_t cdf_segments;   /* learned CDF: number of linear pieces, 16..4096 (power of two) */
-    uint32_t cdf_steps;      /* learned CDF: Adam steps per fit after a start from the
-                                sample's histogram; 0 = the untrained uniform model */
+    uint32_t cdf_steps;      /* learned CDF: Adam steps per fit after a start through the
+                                sample's per-piece mean points; 0 = the untrained
+                                uniform model */
     float cdf_lr;            /* learned CDF: Adam step size */
     uint32_t profile;        /* 1: time every kernel launch with CUDA events on the
                                 caller's stream and report per-class totals in
@@ -201,8 +202,11 @@ int sss_sort_noalloc(const uint8_t* chars, const uint64_t* offsets, uint32_t n,
 /* As sss_sort with every buffer in host memory: chars (host, chars_bytes
  * long), offsets (host), out_perm and out_lcp (host).  Copies the inputs to
  * the device, sorts (as one graph launch, unless options.profile = 1),
- * copies the results back and returns after the copy.  Pinned host buffers
- * copy fastest. */
+ * copies the results back and returns after the copy.  Copies and sort run
+ * on a non-blocking stream the library owns (freed by sss_release), so they
+ * neither wait for nor delay the caller's work on the legacy default
+ * stream.  Pinned host buffers copy fastest; the time is bound by the host
+ * link (the sort itself cannot start before every string has arrived). */
 int sss_sort_host(const uint8_t* chars, uint64_t chars_bytes, const uint64_t* offsets,
                   uint32_t n, uint32_t* out_perm, uint32_t* out_lcp);
 
@@ -247,8 +251,11 @@ int sss_autotune_batched(const uint8_t* chars, const uint64_t* offsets, uint32_t
 /* Learned bucket proposal (an addition to the paper, closest to the jump
  * tables of App. A.2): as sss_sort, but in every device-wide distribution
  * round each segment of at least 65,536 strings fits a monotone
- * piecewise-linear CDF of its key words (cdf_segments pieces, FP32) on its
- * own sorted splitter sample -- started from the sample's histogram, then
+ * piecewise-linear CDF of its key words (cdf_segments pieces, FP32) on a
+ * sample of 0.1 % of its strings (2,048 to 65,536 keys) -- the pieces spread
+ * over the key groups the sample's first differing byte defines, in
+ * proportion to their keys; started from the line through the sample's
+ * per-piece mean points, then
  * cdf_steps Adam steps of hand-written forward and backward passes on the
  * GPU -- and classification first proposes a bucket from the model and
  * checks it exactly against the bounding splitters (and the neighbouring
@@ -298,11 +305,12 @@ int sss_classify_equal(const uint64_t* keys, uint32_t n, const uint64_t* level, 
 /* The learned model's loss and gradient, exposed so the fit can be checked.
  * Model with M pieces on [0,1]: increments softplus(theta_j), normalised
  * cumulative knots, F linear inside a piece.  theta (device, float32[M],
- * 1 <= M <= 4096), u (device, float32[S], non-decreasing, clamped to
- * [0,1]: the fit's samples are sorted keys), y (device,
- * float32[S] targets), 1 <= S <= 2048.  Writes the mean of (F(u_s) - y_s)^2
- * to *out_loss (device float32) and dLoss/dtheta to out_grad (device
- * float32[M]); computed in FP32 on one CTA, the same code the fit uses. */
+ * 1 <= M <= 4096), u (device, float32[S], clamped to [0,1]; any order),
+ * y (device, float32[S] targets), 1 <= S <= 2^22.  Writes the mean of
+ * (F(u_s) - y_s)^2 to *out_loss (device float32) and dLoss/dtheta to
+ * out_grad (device float32[M]); computed in FP32 on one CTA by the code the
+ * fit uses (the gradient from per-piece sample statistics, the loss sample
+ * by sample). */
 int sss_cdf_loss_grad(const float* theta, uint32_t M, const float* u, const float* y,
                       uint32_t S, float* out_loss, float* out_grad, void* stream);
 

@@ -26,7 +26,7 @@ using namespace sss;
 namespace {
 
 std::mutex g_mu;
-sss_options g_opt = {10, 128u, 8192u, 16384u, 0x5eedull, 4096u, 16u, 0.05f, 0u, 0u, 16u, 0u, 0u};
+sss_options g_opt = {10, 128u, 8192u, 32768u, 0x5eedull, 4096u, 4u, 0.005f, 0u, 0u, 16u, 0u, 0u};
 sss_stats g_stats;
 Prof g_prof;
 std::vector<int> g_tl_cls;       // timeline of the last profiled host-driven call
@@ -46,6 +46,7 @@ struct DevPool {
     void* alpha_pack = nullptr;  // alphabet compression: packed offsets + packed strings
     size_t alpha_pack_bytes = 0;
     AlphaHdr* ah_host = nullptr; // pinned host copy of the alphabet header
+    cudaStream_t io_stream = nullptr;  // sss_sort_host's copies and sort (non-blocking, library-owned)
 };
 DevPool g_pool[kMaxDevices];
 Branches g_branches[kMaxDevices];  // concurrent round-body branches, created on first use
@@ -87,7 +88,7 @@ struct Layout {
     size_t o_rec0, o_rec1, o_counts, o_counts_scan, o_tlvl, o_tino, o_plans, o_chunk_seg,
         o_large, o_med0, o_med1, o_small0, o_small1, o_tiny0, o_tiny1, o_small_size0, o_small_size1, o_small_off, o_tile_first,
         o_bigrun0, o_bigrun1, o_bids, o_scan_tmp, o_scan_tmp2, o_hdr, o_roots,
-        o_cdf_samp, o_cdf_tab, o_cdf_kmin, o_cdf_scale;
+        o_cdf_tab, o_cdf_norm;
     uint32_t cmax, tmax, lmax, chmax, smax, ymax, bmax, scan_tmp_max, mmax;
 };
 
@@ -162,12 +163,10 @@ Layout layout_for(uint32_t n, const sss_options& o, uint32_t num_roots, bool lea
     L.o_scan_tmp2 = take(4 * scan_tmp);
     L.o_hdr = take(sizeof(Hdr));
     L.o_roots = take(sizeof(Seg) * (num_roots ? num_roots : 1));
-    L.o_cdf_samp = L.o_cdf_tab = L.o_cdf_kmin = L.o_cdf_scale = 0;
+    L.o_cdf_tab = L.o_cdf_norm = 0;
     if (learned) {
-        L.o_cdf_samp = take(sizeof(uint64_t) * kSampleMax * lmax);
         L.o_cdf_tab = take(sizeof(float) * ((size_t)o.cdf_segments + 1) * lmax);
-        L.o_cdf_kmin = take(sizeof(uint64_t) * lmax);
-        L.o_cdf_scale = take(sizeof(float) * lmax);
+        L.o_cdf_norm = take(sizeof(CdfNorm) * lmax);
     }
     L.total = off;
     return L;
@@ -203,11 +202,9 @@ Work make_work(const Layout& L, char* ws, const uint8_t* chars, const uint64_t* 
     w.scan_tmp = (uint32_t*)(ws + L.o_scan_tmp);
     w.scan_tmp2 = (uint32_t*)(ws + L.o_scan_tmp2);
     w.hdr = (Hdr*)(ws + L.o_hdr);
-    if (L.o_cdf_samp) {
-        w.cdf_samp = (uint64_t*)(ws + L.o_cdf_samp);
+    if (L.o_cdf_tab) {
         w.cdf_tab = (float*)(ws + L.o_cdf_tab);
-        w.cdf_kmin = (uint64_t*)(ws + L.o_cdf_kmin);
-        w.cdf_scale = (float*)(ws + L.o_cdf_scale);
+        w.cdf_norm = (CdfNorm*)(ws + L.o_cdf_norm);
     }
     w.cmax = L.cmax; w.tmax = L.tmax; w.lmax = L.lmax; w.chmax = L.chmax;
     w.smax = L.smax; w.ymax = L.ymax; w.bmax = L.bmax; w.scan_tmp_max = L.scan_tmp_max; w.mmax = L.mmax;
@@ -759,7 +756,10 @@ int sss_sort_host(const uint8_t* chars, uint64_t chars_bytes, const uint64_t* of
     uint64_t* d_off = (uint64_t*)(base + b_chars);
     uint32_t* d_perm = (uint32_t*)(base + b_chars + b_off);
     uint32_t* d_lcp = (uint32_t*)(base + b_chars + b_off + b_out);
-    cudaStream_t st = 0;
+    // a stream of the library's own: the copies and the sort neither wait
+    // for nor hold up work the caller has on the legacy default stream
+    if (!P->io_stream) CK(cudaStreamCreateWithFlags(&P->io_stream, cudaStreamNonBlocking), "io stream");
+    cudaStream_t st = P->io_stream;
     CK(cudaMemcpyAsync(d_chars, chars, chars_bytes, cudaMemcpyHostToDevice, st), "chars upload");
     CK(cudaMemcpyAsync(d_off, offsets, 8ull * n, cudaMemcpyHostToDevice, st), "offsets upload");
     // the sort between the copies runs as one graph launch (no per-round
@@ -835,7 +835,7 @@ int sss_cdf_loss_grad(const float* theta, uint32_t M, const float* u, const floa
                       float* out_grad, void* stream) {
     std::lock_guard<std::mutex> g(g_mu);
     if (M < 1 || M > 4096) return fail(SSS_ERR_INVALID, "M must be in 1..4096");
-    if (S < 1 || S > (uint32_t)kSampleMax) return fail(SSS_ERR_INVALID, "S must be in 1..%d", kSampleMax);
+    if (S < 1 || S > (1u << 22)) return fail(SSS_ERR_INVALID, "S must be in 1..2^22");
     if (!theta || !u || !y || !out_loss || !out_grad) return fail(SSS_ERR_INVALID, "null pointer argument");
     CK(launch_cdf_loss_grad(theta, M, u, y, S, out_loss, out_grad, (cudaStream_t)stream), "cdf loss/grad");
     return SSS_OK;
@@ -894,7 +894,7 @@ int sss_release(void) {
             cudaSetDevice(d);
             branches_destroy(g_branches[d]);
         }
-        if (!P.ws && !P.io && !P.hh && !P.alpha_scan && !P.alpha_pack && !P.ah_host) continue;
+        if (!P.ws && !P.io && !P.hh && !P.alpha_scan && !P.alpha_pack && !P.ah_host && !P.io_stream) continue;
         cudaSetDevice(d);
         if (P.ws) cudaFree(P.ws);
         if (P.io) cudaFree(P.io);
@@ -902,6 +902,7 @@ int sss_release(void) {
         if (P.alpha_pack) cudaFree(P.alpha_pack);
         if (P.hh) cudaFreeHost(P.hh);
         if (P.ah_host) cudaFreeHost(P.ah_host);
+        if (P.io_stream) cudaStreamDestroy(P.io_stream);
         P = DevPool();
     }
     cudaSetDevice(cur);

@@ -166,10 +166,8 @@ struct Work {
     uint32_t* scan_tmp2;     // [scan_tmp_max] scan scratch of the base case
     Hdr* hdr;
     // learned proposal (allocated for sss_sort_learned only)
-    uint64_t* cdf_samp;      // [lmax * kSampleMax] sorted splitter sample of each segment
     float* cdf_tab;          // [lmax * (M + 1)] CDF at the knots of each segment's model
-    uint64_t* cdf_kmin;      // [lmax] smallest sample key (u = 0)
-    float* cdf_scale;        // [lmax] 1 / (largest - smallest sample key)
+    struct CdfNorm* cdf_norm;  // [lmax] input coordinate of each segment's model
 
     uint32_t cmax, tmax, lmax, chmax, smax, ymax, bmax, scan_tmp_max, mmax;
 };
@@ -523,23 +521,49 @@ __device__ __forceinline__ uint32_t next_item(uint32_t* q, uint32_t* s_item) {
 // costs more than it can save on them).
 constexpr uint32_t kLearnedMinSize = 1u << 16;
 
-// Normalised key position for a segment's model: u = (key - kmin) * scale,
-// clamped to [0, 1], computed in FP32.
-__device__ __forceinline__ float cdf_u(uint64_t key, uint64_t kmin, float scale) {
-    if (key <= kmin) return 0.0f;
-    return fminf(1.0f, __ull2float_rn(key - kmin) * scale);
+// Input coordinate of a segment's model, t in [0, M] (the model's pieces
+// are [m, m + 1)), in two levels.  The fit sample's smallest and largest
+// keys share their first c bytes, so every key between them does too; its
+// byte c (the digit) picks one of at most 256 key groups, and group d owns
+// pieces [O_d, O_{d+1}), its share of the M pieces proportional to its
+// share of the sample.  Inside a group, u2 = (key - gmin_d) / (gmax_d -
+// gmin_d) measures the key from the group's own smallest sample key, past
+// the prefix the group shares, and t = O_d + (O_{d+1} - O_d) u2.  A single
+// normalisation over the whole sample (u = (key - kmin) / (kmax - kmin) in
+// FP32) cannot tell keys apart that differ only after the 24 bits that
+// follow the sample's common prefix, which is the rule for URL-like key
+// words ("http://a..." and "http://b..." differ in their eighth byte).
+// Keys below kmin get t = 0, above kmax t = M.  t is non-decreasing in
+// the key.
+struct CdfNorm {
+    uint64_t kmin, kmax;
+    uint32_t c;        // bytes kmin and kmax share (8 when they are equal)
+    uint32_t pad;
+    uint16_t O[260];   // first piece of digit group d, O[256] = M
+    uint64_t gmin[256];
+    float gscale[256]; // 1 / (gmax_d - gmin_d), 0 when the group holds one key value
+};
+
+__device__ __forceinline__ float cdf_coord(uint64_t key, const CdfNorm& n, uint32_t M) {
+    if (key < n.kmin) return 0.0f;
+    if (key > n.kmax) return (float)M;
+    if (n.c >= 8u) return 0.0f;  // one key value in the sample
+    const uint32_t d = (uint32_t)(key >> (56u - 8u * n.c)) & 0xFFu;  // kmin <= key <= kmax share c bytes
+    const uint64_t g = n.gmin[d];
+    const float u2 = key > g ? fminf(1.0f, __ull2float_rn(key - g) * n.gscale[d]) : 0.0f;
+    return (float)n.O[d] + (float)(n.O[d + 1] - n.O[d]) * u2;
 }
 
 // Learned bucket proposal with exact verification: the model's CDF value
-// F(u) (linear between the knots C[0..M]) proposes j = floor(F (v + 1));
+// F(t) (linear between the knots C[0..M]) proposes j = floor(F (v + 1));
 // the key's interval (x_{j-1}, x_j] is checked against the in-order
 // splitters, and failing that the neighbouring intervals j-1 and j+1.  On a
 // hit returns true and the bucket 2j + [key = x_j] (identical to the tree's
 // answer, since these intervals partition the keys); on a miss returns
 // false and the caller descends the tree.
-__device__ __forceinline__ bool propose_bucket(uint64_t key, const float* C, uint32_t M, uint64_t kmin, float scale,
+__device__ __forceinline__ bool propose_bucket(uint64_t key, const float* C, uint32_t M, const CdfNorm& nrm,
                                                const uint64_t* ino, uint32_t v, uint32_t& bucket) {
-    const float t = cdf_u(key, kmin, scale) * (float)M;
+    const float t = cdf_coord(key, nrm, M);
     const uint32_t m = min((uint32_t)t, M - 1u);
     const float f = t - (float)m;
     const float F = C[m] + f * (C[m + 1] - C[m]);

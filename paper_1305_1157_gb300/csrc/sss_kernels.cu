@@ -25,6 +25,8 @@
 // large); k_fixup resolves the LCP at bucket boundaries at the end.
 #include <string.h>
 
+#include <type_traits>
+
 #include "sss_internal.cuh"
 
 namespace sss {
@@ -76,52 +78,109 @@ __device__ uint32_t block_excl_sum(uint32_t x, uint32_t* wsum, uint32_t* total) 
 
 // Where a bucket of `size` strings goes next (Sec. 3.1 "Parallelization of
 // S^5": size classes).  isrun: all its strings are equal (finished).
-__device__ __forceinline__ void append_child(const Work& w, const Params& p, int out, uint32_t start,
-                                             uint32_t size, uint32_t cdepth, bool isrun, uint32_t runlcp) {
+enum : uint32_t { kChildNone = 0, kChildRuns, kChildTiny, kChildSmall, kChildMed, kChildLarge };
+
+__device__ __forceinline__ uint32_t child_kind(const Params& p, uint32_t size, bool isrun) {
+    if (size <= 1) return kChildNone;
+    if (isrun && size > p.base_threshold) return kChildRuns;
+    if (size <= min(p.base_threshold, kTinyMax)) return kChildTiny;
+    if (size <= p.base_threshold) return kChildSmall;
+    if (size <= p.med_threshold) return kChildMed;
+    return kChildLarge;
+}
+
+// First of `cnt` consecutive list slots for each lane whose `mine` is set:
+// one atomic add per warp (the lanes' list appends would otherwise hit the
+// same few counters once per bucket).  Called by all lanes of the warp.
+__device__ __forceinline__ uint32_t warp_reserve(uint32_t* counter, bool mine, uint32_t cnt) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t m = __ballot_sync(FULL_MASK, mine);
+    if (!m) return 0u;
+    uint32_t c = mine ? cnt : 0u;
+    // exclusive prefix of the lanes' counts
+    uint32_t inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL_MASK, inc, o);
+        if (lane >= (uint32_t)o) inc += y;
+    }
+    const uint32_t total = __shfl_sync(FULL_MASK, inc, 31);
+    uint32_t base = 0;
+    if (lane == 31) base = atomicAdd(counter, total);
+    base = __shfl_sync(FULL_MASK, base, 31);
+    return base + inc - c;
+}
+
+__device__ __forceinline__ void warp_add(uint32_t* counter, uint32_t x) {
+    x = __reduce_add_sync(FULL_MASK, x);
+    if ((threadIdx.x & 31u) == 0 && x) atomicAdd(counter, x);
+}
+
+// Appends the child segment of each lane that has one (valid) to the list of
+// its size class.  Called by all 32 lanes of a warp together; each list and
+// counter takes one atomic per warp.
+__device__ __forceinline__ void append_children(const Work& w, const Params& p, int out, bool valid, uint32_t start,
+                                                uint32_t size, uint32_t cdepth, bool isrun, uint32_t runlcp) {
     Hdr* h = w.hdr;
-    if (size <= 1) return;
-    if (isrun && size > p.base_threshold) {
-        // pieces of at most kRunPiece strings, so one large run spreads over
-        // many CTAs; depth holds the run's first position
-        const uint32_t np = (size + kRunPiece - 1u) / kRunPiece;
-        const uint32_t s = atomicAdd(&h->n_bigrun, np);
-        if (s + np <= w.bmax) {
-            for (uint32_t j = 0; j < np; j++)
-                w.bigrun[out][s + j] = Seg{start + j * kRunPiece, min(kRunPiece, size - j * kRunPiece), start, runlcp};
-        } else {
-            atomicOr(&h->err, kErrRunOverflow);
+    const uint32_t kind = valid ? child_kind(p, size, isrun) : kChildNone;
+    if (!__any_sync(FULL_MASK, kind != kChildNone)) return;
+    {   // large runs of equal strings: pieces of at most kRunPiece strings,
+        // so one large run spreads over many CTAs; depth holds the run's
+        // first position
+        const uint32_t np = kind == kChildRuns ? (size + kRunPiece - 1u) / kRunPiece : 0u;
+        const uint32_t s0 = warp_reserve(&h->n_bigrun, kind == kChildRuns, np);
+        if (kind == kChildRuns) {
+            if (s0 + np <= w.bmax) {
+                for (uint32_t j = 0; j < np; j++)
+                    w.bigrun[out][s0 + j] = Seg{start + j * kRunPiece, min(kRunPiece, size - j * kRunPiece), start, runlcp};
+            } else {
+                atomicOr(&h->err, kErrRunOverflow);
+            }
         }
-    } else if (size <= min(p.base_threshold, kTinyMax)) {
-        uint32_t s = atomicAdd(&h->n_tiny, 1u);
-        if (s < w.ymax) {
-            w.tiny[out][s] = Seg{start, size, cdepth, 0u};
-            atomicAdd(&h->tiny_elems, size);
-            atomicAdd(&h->small_hist[min(31 - __clz(size), 7)], 1u);
-        } else {
-            atomicOr(&h->err, kErrSmallOverflow);
+    }
+    {
+        const uint32_t s0 = warp_reserve(&h->n_tiny, kind == kChildTiny, 1u);
+        if (kind == kChildTiny) {
+            if (s0 < w.ymax) w.tiny[out][s0] = Seg{start, size, cdepth, 0u};
+            else atomicOr(&h->err, kErrSmallOverflow);
         }
-    } else if (size <= p.base_threshold) {
-        uint32_t s = atomicAdd(&h->n_small, 1u);
-        if (s < w.smax) {
-            w.small[out][s] = Seg{start, size, cdepth, 0u};
-            w.small_size[out][s] = size;
-            atomicAdd(&h->small_elems, size);
-            atomicAdd(&h->small_hist[min(31 - __clz(size), 7)], 1u);
-        } else {
-            atomicOr(&h->err, kErrSmallOverflow);
+        warp_add(&h->tiny_elems, kind == kChildTiny && s0 < w.ymax ? size : 0u);
+    }
+    {
+        const uint32_t s0 = warp_reserve(&h->n_small, kind == kChildSmall, 1u);
+        if (kind == kChildSmall) {
+            if (s0 < w.smax) {
+                w.small[out][s0] = Seg{start, size, cdepth, 0u};
+                w.small_size[out][s0] = size;
+            } else {
+                atomicOr(&h->err, kErrSmallOverflow);
+            }
         }
-    } else if (size <= p.med_threshold) {
-        uint32_t s = atomicAdd(&h->n_med, 1u);
-        if (s < w.mmax) {
-            w.med[out][s] = Seg{start, size, cdepth, 0u};
-            atomicAdd(&h->med_elems, size);
-        } else {
-            atomicOr(&h->err, kErrMedOverflow);
+        warp_add(&h->small_elems, kind == kChildSmall && s0 < w.smax ? size : 0u);
+    }
+    {   // base-case buckets by floor(log2(size))
+        const bool base = kind == kChildTiny || kind == kChildSmall;
+        const uint32_t bin = base ? min(31 - __clz(size), 7) : 8u;
+#pragma unroll
+        for (uint32_t b = 1; b < 8; b++) {
+            const uint32_t m = __ballot_sync(FULL_MASK, bin == b);
+            if ((threadIdx.x & 31u) == 0 && m) atomicAdd(&h->small_hist[b], (uint32_t)__popc(m));
         }
-    } else {
-        uint32_t s = atomicAdd(&h->n_large, 1u);
-        if (s < w.lmax) w.large[s] = Seg{start, size, cdepth, 0u};
-        else atomicOr(&h->err, kErrLargeOverflow);
+    }
+    {
+        const uint32_t s0 = warp_reserve(&h->n_med, kind == kChildMed, 1u);
+        if (kind == kChildMed) {
+            if (s0 < w.mmax) w.med[out][s0] = Seg{start, size, cdepth, 0u};
+            else atomicOr(&h->err, kErrMedOverflow);
+        }
+        warp_add(&h->med_elems, kind == kChildMed && s0 < w.mmax ? size : 0u);
+    }
+    {
+        const uint32_t s0 = warp_reserve(&h->n_large, kind == kChildLarge, 1u);
+        if (kind == kChildLarge) {
+            if (s0 < w.lmax) w.large[s0] = Seg{start, size, cdepth, 0u};
+            else atomicOr(&h->err, kErrLargeOverflow);
+        }
     }
 }
 
@@ -192,10 +251,15 @@ __global__ void k_hdr_reset(Work w) {
 
 // Roots: one segment per set (a single sort is one set) at depth 0.
 __global__ void k_roots(Work w, Params p, const Seg* roots, uint32_t num_roots, Seg single) {
-    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < num_roots; j += gridDim.x * blockDim.x) {
-        const Seg g = roots ? roots[j] : single;
-        if (g.size == 1) w.out_perm[g.begin] = g.begin;
-        else append_child(w, p, 0, g.begin, g.size, 0u, false, 0u);
+    const uint32_t stride = gridDim.x * blockDim.x;
+    // the loop runs while any lane of the warp has a root (the appends are
+    // made by whole warps)
+    for (uint32_t j0 = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; j0 < num_roots; j0 += stride) {
+        const uint32_t j = j0 + (threadIdx.x & 31u);
+        const bool ok = j < num_roots;
+        const Seg g = ok ? (roots ? roots[j] : single) : Seg{0u, 0u, 0u, 0u};
+        if (ok && g.size == 1) w.out_perm[g.begin] = g.begin;
+        append_children(w, p, 0, ok, g.begin, g.size, 0u, false, 0u);
     }
 }
 
@@ -425,13 +489,8 @@ __global__ void __launch_bounds__(1024) k_sample(Work w, Params p) {
                                  : KeyTraits<KT>::top();
         __syncthreads();
         bitonic_sort(sm.samp, pw);
-        if (p.learned) {
-            uint64_t* out = w.cdf_samp + (size_t)seg * kSampleMax;
-            for (uint32_t j = threadIdx.x; j < cnt; j += blockDim.x) out[j] = KeyTraits<KT>::word(sm.samp[j]);
-        }
-        // the learned model fits the planned sample and tree: no cut there
-        select_splitters(sm.samp, cnt, k, sm.lvl, sm.ra, sm.rb, p.learned ? nullptr : &s_depth);
-        const int kt = p.learned ? k : max(1, s_depth);
+        select_splitters(sm.samp, cnt, k, sm.lvl, sm.ra, sm.rb, &s_depth);
+        const int kt = max(1, s_depth);
         if (threadIdx.x == 0 && kt != k) w.plans[seg].k = (uint32_t)kt;
         emit_tree(sm.lvl, kt, tree_lvl + P.tree_base, tree_ino + P.tree_base);
     }
@@ -455,7 +514,13 @@ __global__ void __launch_bounds__(1024) k_build_splitters(const uint64_t* sample
 // ------------------------------------------------------------ classify + count
 
 constexpr int kClassifyThreads = 256;
-constexpr int kClassifyUnroll = 8;
+#ifndef SSS_CLASSIFY_UNROLL
+#define SSS_CLASSIFY_UNROLL 4
+#endif
+#ifndef SSS_CLASSIFY_MIN_BLOCKS
+#define SSS_CLASSIFY_MIN_BLOCKS 5
+#endif
+constexpr int kClassifyUnroll = SSS_CLASSIFY_UNROLL;  // keys a thread descends at once
 
 // Adds the buckets of the key words of recs[lo, hi) to hist (warp-aggregated shared atomics);
 // bid (optional) receives each bucket at bid[e - lo].  Loop bounds are
@@ -489,8 +554,8 @@ __device__ __forceinline__ void classify_range(const Rec* __restrict__ recs, uin
 // proposals and misses.
 __device__ __forceinline__ void classify_range_learned(const Rec* __restrict__ recs, uint32_t lo, uint32_t hi,
                                                        const uint64_t* t, const uint64_t* ino, int k, uint32_t nb,
-                                                       uint32_t* hist, const float* C, uint32_t M, uint64_t kmin,
-                                                       float scale, uint32_t& misses, uint16_t* bid) {
+                                                       uint32_t* hist, const float* C, uint32_t M, const CdfNorm& nrm,
+                                                       uint32_t& misses, uint16_t* bid) {
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t v = (1u << k) - 1u;
     for (uint32_t base = lo; base < hi; base += blockDim.x * kClassifyUnroll) {
@@ -504,7 +569,7 @@ __device__ __forceinline__ void classify_range_learned(const Rec* __restrict__ r
         for (int u = 0; u < kClassifyUnroll; u++) {
             const uint32_t e = base + u * blockDim.x + threadIdx.x;
             uint32_t b = nb;
-            if (e < hi && !propose_bucket(kk[u], C, M, kmin, scale, ino, v, b)) {
+            if (e < hi && !propose_bucket(kk[u], C, M, nrm, ino, v, b)) {
                 b = classify_key(kk[u], t, ino, k);
                 misses++;
             }
@@ -518,12 +583,14 @@ __device__ __forceinline__ void classify_range_learned(const Rec* __restrict__ r
 constexpr uint32_t kCdfMMax = 4096;
 
 template <class KT>
-__global__ void __launch_bounds__(kClassifyThreads) k_classify(Work w, Params p) {
+__global__ void __launch_bounds__(kClassifyThreads, SSS_CLASSIFY_MIN_BLOCKS) k_classify(Work w, Params p) {
     constexpr bool kLearned = KeyTraits<KT>::kBytes == 8;  // the learned model proposes on one word
     __shared__ LevelTree<KT, kVMax + 1> t;
     __shared__ KT ino[kVMax];
     __shared__ uint32_t hist[kNBMax + 1];
     __shared__ float C[kLearned ? kCdfMMax + 1 : 1];
+    // the learned model's input coordinate (a byte where it is not used)
+    __shared__ typename std::conditional<kLearned, CdfNorm, char>::type nrm_s;
     __shared__ uint32_t s_item;
     const int cur = w.hdr->round & 1u;
     const uint32_t total_chunks = w.hdr->total_chunks;
@@ -548,10 +615,15 @@ __global__ void __launch_bounds__(kClassifyThreads) k_classify(Work w, Params p)
             if (p.learned && P.size >= kLearnedMinSize) {
                 const float* tab = w.cdf_tab + (size_t)s * (p.cdf_M + 1);
                 for (uint32_t j = threadIdx.x; j <= p.cdf_M; j += blockDim.x) C[j] = tab[j];
+                {
+                    const uint32_t* src = reinterpret_cast<const uint32_t*>(w.cdf_norm + s);
+                    uint32_t* dst = reinterpret_cast<uint32_t*>(&nrm_s);
+                    for (uint32_t j = threadIdx.x; j < sizeof(CdfNorm) / 4; j += blockDim.x) dst[j] = src[j];
+                }
                 __syncthreads();
                 uint32_t misses = 0;
-                classify_range_learned(w.rec[cur], lo, hi, t.view(), ino, k, nb, hist, C, p.cdf_M, w.cdf_kmin[s],
-                                       w.cdf_scale[s], misses, w.bids + lo);
+                classify_range_learned(w.rec[cur], lo, hi, t.view(), ino, k, nb, hist, C, p.cdf_M, nrm_s, misses,
+                                       w.bids + lo);
                 misses = __reduce_add_sync(FULL_MASK, misses);
                 if ((threadIdx.x & 31u) == 0 && misses)
                     atomicAdd(&w.hdr->learned_misses, (unsigned long long)misses);
@@ -576,7 +648,7 @@ __global__ void __launch_bounds__(kClassifyThreads) k_classify(Work w, Params p)
 
 constexpr int kScatterWarps = kScatterThreads / 32;
 #ifndef SSS_SCATTER_MIN_BLOCKS
-#define SSS_SCATTER_MIN_BLOCKS 3
+#define SSS_SCATTER_MIN_BLOCKS 4
 #endif
 
 template <int NBCAP>
@@ -603,9 +675,7 @@ __device__ __forceinline__ uint32_t byte_sum_below(uint64_t x, uint32_t below) {
 template <int NBCAP, bool kFromBid, class KT, int ITEMS = kScatterItems, class TT>
 __device__ uint32_t scatter_range(const Work& w, int cur, uint32_t lo, uint32_t hi, uint32_t nb,
                                   ScatterState<NBCAP>& ss, const TT& t, const KT* ino, int k,
-                                  const uint16_t* bid, uint32_t seg_end, uint32_t depth, bool equal_test,
-                                  const float* C = nullptr,
-                                  uint32_t M = 0, uint64_t kmin = 0, float scale = 0.0f) {
+                                  const uint16_t* bid, uint32_t seg_end, uint32_t depth, bool equal_test) {
     constexpr int kBucketsPerThread = (NBCAP + kScatterThreads) / kScatterThreads;
     static_assert(32 * ITEMS <= 255, "per-warp bucket counts must fit a byte");
     uint8_t* wbytes = reinterpret_cast<uint8_t*>(ss.wcnt);
@@ -626,30 +696,14 @@ __device__ uint32_t scatter_range(const Work& w, int cur, uint32_t lo, uint32_t 
             else rr[j] = Rec{0ull, 0ull, 0ull, 0u, 0u};
             if (kFromBid) bb[j] = ok ? bid[e - lo] : nb;
         }
-        bool proposed = false;
-        if constexpr (!kFromBid && KeyTraits<KT>::kBytes == 8) {
-            if (C) {
-#pragma unroll
-                for (int j = 0; j < ITEMS; j++) {
-                    const uint32_t e = wbase + j * 32u;
-                    uint32_t b = nb;
-                    if (e < hi && !propose_bucket(rr[j].key, C, M, kmin, scale, ino, (nb - 1u) / 2u, b))
-                        b = classify_key(rr[j].key, t, ino, k);
-                    bb[j] = b;
-                }
-                proposed = true;
-            }
-        }
         if constexpr (!kFromBid) {
-            if (!proposed) {
-                KT kk[ITEMS];
+            KT kk[ITEMS];
 #pragma unroll
-                for (int j = 0; j < ITEMS; j++) kk[j] = KeyTraits<KT>::of(rr[j]);
-                classify_keys_by<ITEMS>(equal_test, kk, bb, t, ino, k);
+            for (int j = 0; j < ITEMS; j++) kk[j] = KeyTraits<KT>::of(rr[j]);
+            classify_keys_by<ITEMS>(equal_test, kk, bb, t, ino, k);
 #pragma unroll
-                for (int j = 0; j < ITEMS; j++)
-                    if (wbase + j * 32u >= hi) bb[j] = nb;
-            }
+            for (int j = 0; j < ITEMS; j++)
+                if (wbase + j * 32u >= hi) bb[j] = nb;
         }
         // next key words of strings whose bucket moves deeper: all gathers are
         // issued here, before any store, and complete during the ranking
@@ -751,18 +805,18 @@ __global__ void __launch_bounds__(kScatterThreads, SSS_SCATTER_MIN_BLOCKS) k_sca
         for (int q = 0; q < kBPT; q++) {
             const uint32_t b = threadIdx.x + q * kScatterThreads;
             if (b <= nb) sm.ss.wcnt[b] = 0ull;
+            uint32_t start = 0, size = 0;
+            BucketInfo bi{0u, 0u, false};
             if (b < nb) {
-                const uint32_t start = P.begin + (s_first[q] - S0);
+                start = P.begin + (s_first[q] - S0);
                 const uint32_t end = (b + 1 < nb) ? P.begin + (s_next[q] - S0) : seg_end;
-                const uint32_t size = end - start;
+                size = end - start;
                 sm.ss.run_pos[b] = P.begin + (s_mine[q] - S0);
-                const BucketInfo bi = bucket_info(b, nb, P.depth, sm.ino, size, p.base_threshold);
+                bi = bucket_info(b, nb, P.depth, sm.ino, size, p.base_threshold);
                 sm.ss.rdep[b] = refill_code(bi, size, P.depth);
-                if (ci == 0 && size > 0) {
-                    if (start > P.begin) w.out_lcp[start] = kLcpFlag | P.depth;
-                    append_child(w, p, med_out, start, size, bi.cdepth, bi.isrun, bi.runlcp);
-                }
+                if (ci == 0 && size > 0 && start > P.begin) w.out_lcp[start] = kLcpFlag | P.depth;
             }
+            if (ci == 0) append_children(w, p, med_out, b < nb && size > 0, start, size, bi.cdepth, bi.isrun, bi.runlcp);
         }
         __syncthreads();
         const uint32_t lo = P.begin + ci * P.chunk;
@@ -807,7 +861,7 @@ constexpr int kMedItems = 4;  // records per thread in a medium round's move
 // those characters in place (gathers the keys w deeper, same positions) and
 // classifies again, instead of moving the whole segment into one child.
 #ifndef SSS_MED_MIN_BLOCKS
-#define SSS_MED_MIN_BLOCKS 3
+#define SSS_MED_MIN_BLOCKS 4
 #endif
 template <class KT>
 __global__ void __launch_bounds__(kScatterThreads, SSS_MED_MIN_BLOCKS) k_med_round(Work w, Params p) {
@@ -874,16 +928,15 @@ __global__ void __launch_bounds__(kScatterThreads, SSS_MED_MIN_BLOCKS) k_med_rou
 #pragma unroll
         for (int q = 0; q < kPer; q++) {
             const uint32_t b = threadIdx.x * kPer + q;
+            const uint32_t size = cnts[q];
+            BucketInfo bi{0u, 0u, false};
             if (b < nb) {
-                const uint32_t size = cnts[q];
-                const BucketInfo bi = bucket_info(b, nb, g.depth, sm.ino, size, p.base_threshold);
+                bi = bucket_info(b, nb, g.depth, sm.ino, size, p.base_threshold);
                 sm.mv.ss.run_pos[b] = start;
                 sm.mv.ss.rdep[b] = refill_code(bi, size, g.depth);
-                if (size > 0) {
-                    if (start > g.begin) w.out_lcp[start] = kLcpFlag | g.depth;
-                    append_child(w, p, med_out, start, size, bi.cdepth, bi.isrun, bi.runlcp);
-                }
+                if (size > 0 && start > g.begin) w.out_lcp[start] = kLcpFlag | g.depth;
             }
+            append_children(w, p, med_out, b < nb && size > 0, start, size, bi.cdepth, bi.isrun, bi.runlcp);
             start += cnts[q];
         }
         __syncthreads();
@@ -1432,7 +1485,9 @@ static cudaError_t launch_round_t(const Work& w, const Params& p, const Hdr* hc,
             k_sample<KT><<<gL, 1024, sizeof(SampleSmem<KT>), st>>>(w, p);
         }
         if (p.learned) {
-            cudaError_t e = launch_cdf_fit(w, p, grid_of(sms, hc, hc ? hc->L : 0u), pf, st);
+            // one CTA per SM at most: a fit CTA holds most of an SM's shared
+            // memory, and most large segments are below the model's minimum size
+            cudaError_t e = launch_cdf_fit(w, p, hc ? min(hc->L, sms) : sms, pf, st);
             if (e != cudaSuccess) return e;
         }
         const uint32_t gc = grid_of(sms * 4u, hc, hc ? hc->total_chunks : 0u);

@@ -45,7 +45,7 @@ def test_python_binding_covers_every_symbol():
 
 def test_options_roundtrip_and_validation(lib):
     o = sss.sss_get_options()
-    assert o.k_max == 10 and o.base_threshold == 128 and o.medium_threshold == 8192 and o.chunk == 16384
+    assert o.k_max == 10 and o.base_threshold == 128 and o.medium_threshold == 8192 and o.chunk == 32768
     assert o.key_bytes == 16 and o.classifier == 0
     bad = sss.sss_options.from_buffer_copy(o)
     bad.k_max = 11
