@@ -389,8 +389,11 @@ def leg_learned(sss, torch, stream, dev, args, world, dist):
         r = {"value": n * world / (ms * 1e-3), "unit": "strings/s", "ms_per_step": ms, "steps": steps,
              "classify_ms": prof.get("classify", {}).get("ms"), "scatter_ms": prof.get("scatter", {}).get("ms")}
         if name == "learned":
+            rk, rm = list(st.round_learned_keys), list(st.round_learned_misses)
             r.update({"proposals": int(st.learned_keys), "misses": int(st.learned_misses),
                       "models": int(st.learned_models),
+                      "round_miss_rate": [round(rm[i] / rk[i], 4) for i in range(min(int(st.rounds), 64)) if rk[i]],
+                      "round_proposals": [int(rk[i]) for i in range(min(int(st.rounds), 64)) if rk[i]],
                       "miss_rate": (st.learned_misses / st.learned_keys) if st.learned_keys else None,
                       "fit_ms": prof.get("learned", {}).get("ms"),
                       "cdf_segments": int(o.cdf_segments), "cdf_steps": int(o.cdf_steps)})

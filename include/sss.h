@@ -56,7 +56,8 @@ typedef enum {
 
 /* Tuning knobs.  Defaults: k_max 10, base_threshold 128, medium_threshold
  * 8192, chunk 32768, seed 0x5eed, cdf_segments 4096, cdf_steps 4,
- * cdf_lr 0.005, profile 0, graph 0, key_bytes 16, classifier 0, alphabet 0. */
+ * cdf_lr 0.005, profile 0, graph 0, key_bytes 16, classifier 0, alphabet 0,
+ * radix 0. */
 typedef struct sss_options {
     int32_t k_max;             /* largest splitter tree depth k: v = 2^k - 1 splitters, 1..10 */
     uint32_t base_threshold;   /* buckets of at most this many strings go to the base case, 16..128 */
@@ -99,6 +100,16 @@ typedef struct sss_options {
                                 library-managed memory: sss_sort_ws and
                                 sss_sort_noalloc ignore it.  0: off.  The output does
                                 not depend on it. */
+    uint32_t radix;          /* classification of a device-wide round's segment by a
+                                digit instead of the splitter tree (App. A.2,
+                                adaptivity): the digit is the k_max bits of the key
+                                after the bits every sample key shares.  0: trees
+                                only; 1: a segment whose sample digits (at least
+                                4 bits) have an entropy of at least k - 1 bits
+                                (near uniform) is classified by its digit; 2:
+                                every segment whose
+                                sample keys differ.  The learned proposal always
+                                uses trees.  The output does not depend on it. */
 } sss_options;
 
 #define SSS_MAX_ROUNDS_LOGGED 64
@@ -147,6 +158,11 @@ typedef struct sss_stats {
                                         0 when the option is off */
     uint32_t learned_models;         /* learned CDF models fitted (one per segment of a
                                         device-wide round that got one) */
+    uint32_t radix_segments;         /* segments of device-wide rounds classified by a
+                                        digit instead of a splitter tree (option radix) */
+    uint64_t round_learned_keys[SSS_MAX_ROUNDS_LOGGED];   /* learned proposals per round
+                                                             (host-driven rounds only) */
+    uint64_t round_learned_misses[SSS_MAX_ROUNDS_LOGGED]; /* of those, rejected ones */
 } sss_stats;
 
 /* What the learned proposal did in the last sss_sort_learned call. */

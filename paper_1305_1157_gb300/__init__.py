@@ -45,7 +45,8 @@ class sss_options(ctypes.Structure):
                 ("medium_threshold", ctypes.c_uint32), ("chunk", ctypes.c_uint32),
                 ("seed", ctypes.c_uint64), ("cdf_segments", ctypes.c_uint32), ("cdf_steps", ctypes.c_uint32),
                 ("cdf_lr", ctypes.c_float), ("profile", ctypes.c_uint32), ("graph", ctypes.c_uint32),
-                ("key_bytes", ctypes.c_uint32), ("classifier", ctypes.c_uint32), ("alphabet", ctypes.c_uint32)]
+                ("key_bytes", ctypes.c_uint32), ("classifier", ctypes.c_uint32), ("alphabet", ctypes.c_uint32),
+                ("radix", ctypes.c_uint32)]
 
 
 class sss_stats(ctypes.Structure):
@@ -62,7 +63,9 @@ class sss_stats(ctypes.Structure):
                 ("round_segments", ctypes.c_uint32 * MAX_ROUNDS_LOGGED),
                 ("round_active", ctypes.c_uint32 * MAX_ROUNDS_LOGGED),
                 ("alphabet_symbols", ctypes.c_uint32), ("alphabet_group", ctypes.c_uint32),
-                ("learned_models", ctypes.c_uint32)]
+                ("learned_models", ctypes.c_uint32), ("radix_segments", ctypes.c_uint32),
+                ("round_learned_keys", ctypes.c_uint64 * MAX_ROUNDS_LOGGED),
+                ("round_learned_misses", ctypes.c_uint64 * MAX_ROUNDS_LOGGED)]
 
     def as_dict(self):
         r = self.rounds
@@ -78,7 +81,9 @@ class sss_stats(ctypes.Structure):
                 "round_segments": list(self.round_segments)[:min(r, MAX_ROUNDS_LOGGED)],
                 "round_active": list(self.round_active)[:min(r, MAX_ROUNDS_LOGGED)],
                 "alphabet_symbols": self.alphabet_symbols, "alphabet_group": self.alphabet_group,
-                "learned_models": self.learned_models}
+                "learned_models": self.learned_models, "radix_segments": self.radix_segments,
+                "round_learned_keys": list(self.round_learned_keys)[:min(r, MAX_ROUNDS_LOGGED)],
+                "round_learned_misses": list(self.round_learned_misses)[:min(r, MAX_ROUNDS_LOGGED)]}
 
 
 class sss_learned_stats(ctypes.Structure):

@@ -26,7 +26,7 @@ using namespace sss;
 namespace {
 
 std::mutex g_mu;
-sss_options g_opt = {10, 128u, 8192u, 32768u, 0x5eedull, 4096u, 4u, 0.005f, 0u, 0u, 16u, 0u, 0u};
+sss_options g_opt = {10, 128u, 8192u, 32768u, 0x5eedull, 4096u, 4u, 0.005f, 0u, 0u, 16u, 0u, 0u, 0u};
 sss_stats g_stats;
 Prof g_prof;
 std::vector<int> g_tl_cls;       // timeline of the last profiled host-driven call
@@ -223,6 +223,7 @@ int check_options(const sss_options& o) {
     if (o.key_bytes != 8 && o.key_bytes != 16) return fail(SSS_ERR_INVALID, "key_bytes must be 8 or 16");
     if (o.classifier > 1) return fail(SSS_ERR_INVALID, "classifier must be 0 (unroll) or 1 (equal)");
     if (o.alphabet > 1) return fail(SSS_ERR_INVALID, "alphabet must be 0 (off) or 1 (compress small alphabets)");
+    if (o.radix > 2) return fail(SSS_ERR_INVALID, "radix must be 0 (trees), 1 (by sample entropy) or 2 (always)");
     return SSS_OK;
 }
 
@@ -375,7 +376,7 @@ int run_sort(const Work& w, const sss_options& o, const Seg* roots_dev, uint32_t
              bool reset_prof = true) {
     Params p{learned ? 1 : 0, o.cdf_segments, o.cdf_steps, o.cdf_lr, o.k_max, o.base_threshold,
              o.medium_threshold, o.chunk, o.seed, device_sms(), learned ? 8u : o.key_bytes,
-             learned ? 0u : o.classifier, 0u};
+             learned ? 0u : o.classifier, learned ? 0u : o.radix};
     Prof* pf = &g_prof;
     if (reset_prof) pf->reset(o.profile != 0);
     memset(stats, 0, sizeof(*stats));
@@ -399,12 +400,17 @@ int run_sort(const Work& w, const sss_options& o, const Seg* roots_dev, uint32_t
         stats->medium_strings += hh->med_elems_snap;
         stats->base_strings += (uint64_t)hh->small_elems_snap + hh->tiny_elems_snap;
         uint32_t tiles = 0;
+        const unsigned long long lk0 = hh->learned_keys, lm0 = hh->learned_misses;
         CK(launch_body(w, p, hh, &tiles, pf, st, br), "round");
         stats->base_tiles += tiles;
         CK(launch_plan(w, p, pf, st), "plan");
         CK(launch_advance(w, pf, st), "advance");
         rc = read_hdr(hh, w, st);
         if (rc) return rc;
+        if (round < SSS_MAX_ROUNDS_LOGGED) {  // the learned proposals of this round
+            stats->round_learned_keys[round] = hh->learned_keys - lk0;
+            stats->round_learned_misses[round] = hh->learned_misses - lm0;
+        }
     }
     {
         uint32_t tiles = 0;
@@ -422,6 +428,7 @@ int run_sort(const Work& w, const sss_options& o, const Seg* roots_dev, uint32_t
     stats->learned_keys = hh->learned_keys;
     stats->learned_misses = hh->learned_misses;
     stats->learned_models = hh->learned_models;
+    stats->radix_segments = hh->radix_segments;
     for (int i = 0; i < 8; i++) stats->base_segment_hist[i] = hh->small_hist[i];
     stats->launches = pf->launches;
     stats->profiled = pf->enabled ? 1u : 0u;
@@ -567,7 +574,7 @@ int run_sort_graph(const Work& w, const sss_options& o, const Seg* roots_dev, ui
                    cudaStream_t st, sss_stats* stats, bool learned, const GraphKey& key) {
     Params p{learned ? 1 : 0, o.cdf_segments, o.cdf_steps, o.cdf_lr, o.k_max, o.base_threshold,
              o.medium_threshold, o.chunk, o.seed, device_sms(), learned ? 8u : o.key_bytes,
-             learned ? 0u : o.classifier, 0u};
+             learned ? 0u : o.classifier, learned ? 0u : o.radix};
     memset(stats, 0, sizeof(*stats));
     int dev = 0;
     CK(cudaGetDevice(&dev), "cudaGetDevice");
@@ -591,6 +598,7 @@ int run_sort_graph(const Work& w, const sss_options& o, const Seg* roots_dev, ui
     stats->learned_keys = hh->learned_keys;
     stats->learned_misses = hh->learned_misses;
     stats->learned_models = hh->learned_models;
+    stats->radix_segments = hh->radix_segments;
     for (int i = 0; i < 8; i++) stats->base_segment_hist[i] = hh->small_hist[i];
     stats->launches = gc.launches_prologue + hh->round * gc.launches_body + gc.launches_epilogue;
     return SSS_OK;

@@ -76,15 +76,33 @@ struct SegPlan {
     uint32_t chunk;                     // strings per work item in this round
     uint32_t kp;                        // k as planned (sizes the count rows and the sample);
                                         // k_sample may lower k to the levels its splitters use
-    uint32_t pad1, pad2;
+    uint32_t rbits;                     // > 0: classified by a digit of rbits bits (radix), not the tree
+    uint32_t rskip;                     // leading key bits every sample key shares (radix)
+    uint64_t rbase;                     // those shared bits (the rest 0) (radix)
 };
+
+// Radix classification of a segment (App. A.2, adaptivity: chosen from the
+// sample's digit entropy by k_sample).  The sample keys share their first
+// rskip bits; a key's next rbits bits form its digit.  Buckets: 0 holds the
+// keys whose first rskip bits are below the shared ones, 1 + digit the keys
+// that share them, 2^rbits + 1 the keys above.  Only the first key word
+// (8 characters) is used.
+__device__ __forceinline__ uint32_t radix_bucket(uint64_t h, uint32_t rskip, uint32_t rbits, uint64_t rbase) {
+    if (rskip) {
+        const uint64_t hp = h >> (64u - rskip), bp = rbase >> (64u - rskip);
+        if (hp != bp) return hp < bp ? 0u : (1u << rbits) + 1u;
+    }
+    return 1u + (uint32_t)((h << rskip) >> (64u - rbits));
+}
+__device__ __forceinline__ uint32_t radix_buckets(uint32_t rbits) { return (1u << rbits) + 2u; }
 
 // Device header: live append counters and the snapshot the host reads back.
 struct Hdr {
     // live, appended to by the round kernels
     uint32_t n_large, n_med, n_small, n_bigrun, err, small_elems, med_elems, n_tiny, tiny_elems;
     uint32_t learned_models;  // segment models fitted by k_cdf_fit
-    uint32_t pad0[2];
+    uint32_t radix_segments;  // segments of device-wide rounds classified by a digit
+    uint32_t pad0;
     // snapshot for the host, written by k_plan
     uint32_t L, total_chunks, total_counts, total_tree;
     uint32_t n_med_snap, n_small_snap, n_bigrun_snap, small_elems_snap;
@@ -127,7 +145,8 @@ struct Params {
     uint32_t num_sms;
     uint32_t key_bytes;       // w: 8 (one key word) or 16 (two words, wide keys)
     uint32_t equal_test;      // 1: equality test at every tree node (pS^5-Equal)
-    uint32_t pad;
+    uint32_t radix;           // 0: splitter trees only; 1: a digit where the sample's digits are
+                              // near uniform; 2: a digit wherever the sample keys differ
 };
 
 // Views of the workspace and the caller's buffers for one sort.

@@ -211,6 +211,30 @@ __device__ __forceinline__ BucketInfo bucket_info(uint32_t b, uint32_t nb, uint3
     return bi;
 }
 
+// Child depth of bucket b of a radix segment: the outer buckets (keys
+// outside the sample's shared leading bits) keep the depth; the strings of
+// digit bucket b share the first (rskip + rbits) / 8 whole bytes of their
+// key word, and when those bytes hold a zero the strings all end there and
+// are equal (a finished run).  A bucket bound for the base case keeps the
+// depth, as inner tree buckets do.
+__device__ __forceinline__ BucketInfo bucket_info_radix(uint32_t b, uint32_t nb, const SegPlan& P, uint32_t size,
+                                                        uint32_t base_threshold) {
+    BucketInfo bi{P.depth, 0u, false};
+    if (b == 0 || b + 1 == nb) return bi;
+    const uint32_t shared = P.rskip + P.rbits;  // <= 64
+    const uint64_t pw = P.rbase | ((uint64_t)(b - 1u) << (64u - shared));
+    const uint32_t nbytes = shared >> 3;
+    for (uint32_t j = 0; j < nbytes; j++) {
+        if (((pw >> (56u - 8u * j)) & 0xFFu) == 0u) {
+            bi.isrun = true;
+            bi.runlcp = P.depth + j;
+            return bi;
+        }
+    }
+    if (size > base_threshold) bi.cdepth = P.depth + nbytes;
+    return bi;
+}
+
 // What the scatter does with a string of the bucket: finish it (single),
 // copy its key word, or gather the word at the child's depth.
 __device__ __forceinline__ uint32_t refill_code(const BucketInfo& bi, uint32_t size, uint32_t depth) {
@@ -243,6 +267,7 @@ __global__ void k_hdr_reset(Work w) {
     h->learned_keys = 0ull;
     h->learned_misses = 0ull;
     h->learned_models = 0;
+    h->radix_segments = 0;
     h->round = 0;
     h->q_sample = 0; h->q_fit = 0; h->q_classify = 0; h->q_scatter = 0;
     h->q_med = 0; h->q_base = 0; h->q_bigrun = 0;
@@ -301,7 +326,7 @@ __global__ void __launch_bounds__(1024) k_plan(Work w, Params p) {
             const Seg g = w.large[s];
             const int k = choose_k(g.size, p.k_max);
             const uint32_t ch = (g.size + chunk - 1) / chunk;
-            w.plans[s] = SegPlan{g.begin, g.size, g.depth, (uint32_t)k, ch, bc, bn, bt, chunk, (uint32_t)k, 0u, 0u};
+            w.plans[s] = SegPlan{g.begin, g.size, g.depth, (uint32_t)k, ch, bc, bn, bt, chunk, (uint32_t)k, 0u, 0u, 0ull};
             for (uint32_t c = 0; c < ch; c++) w.chunk_seg[bc + c] = s;
             bc += ch;
             bn += ((2u << k) - 1u) * ch;
@@ -469,12 +494,63 @@ struct SampleSmem {
     int32_t ra[kVMax + 1], rb[kVMax + 1];
 };
 
+// Radix or tree for a segment (App. A.2: "inspect the sample" and switch
+// to radix-style classification where the sample shows it pays).  The
+// sorted sample's keys share their first `skip` bits; the digit is the next
+// `bits` = min(k, 64 - skip) bits of the first key word.  With option
+// radix = 1 the segment takes a digit of at least 4 bits when the sample
+// digits' entropy is at least bits - 1 (near uniform, so the digit buckets
+// are about as even as the tree's), with radix = 2 whenever the sample keys
+// differ.  The
+// smallest and largest sample key always fall into different digit
+// buckets, so a radix round always splits its segment.  Called by the whole
+// block after emit_tree; hist: shared scratch of 2^k ints.
+template <class KT>
+__device__ void choose_radix(const Work& w, const Params& p, uint32_t seg, const KT* samp, uint32_t cnt, uint32_t k,
+                             int32_t* hist, float* s_ent) {
+    // the 2^bits + 2 radix buckets must fit the 2^(k+1) - 1 count rows planned
+    if (k < 2u) return;
+    const uint64_t lo = KeyTraits<KT>::word(samp[0]), hi = KeyTraits<KT>::word(samp[cnt - 1]);
+    if (lo == hi) return;
+    const uint32_t skip = (uint32_t)__clzll((long long)(lo ^ hi));
+    const uint32_t bits = min(k, 64u - skip);
+    bool take = p.radix == 2u;
+    if (!take && bits >= 4u) {  // shorter digits split too little to choose them over a tree
+        const uint32_t nd = 1u << bits;
+        for (uint32_t d = threadIdx.x; d < nd; d += blockDim.x) hist[d] = 0;
+        if (threadIdx.x == 0) *s_ent = 0.0f;
+        __syncthreads();
+        for (uint32_t j = threadIdx.x; j < cnt; j += blockDim.x)
+            atomicAdd(&hist[(uint32_t)((KeyTraits<KT>::word(samp[j]) << skip) >> (64u - bits))], 1);
+        __syncthreads();
+        float e = 0.0f;  // sum of c log2 c over the digits
+        for (uint32_t d = threadIdx.x; d < nd; d += blockDim.x) {
+            const float c = (float)hist[d];
+            if (c > 1.0f) e += c * log2f(c);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(FULL_MASK, e, o);
+        if ((threadIdx.x & 31u) == 0) atomicAdd(s_ent, e);
+        __syncthreads();
+        const float H = log2f((float)cnt) - *s_ent / (float)cnt;  // entropy of the digits in bits
+        take = H >= (float)bits - 1.0f;
+        __syncthreads();  // hist and s_ent are reused
+    }
+    if (take && threadIdx.x == 0) {
+        atomicAdd(&w.hdr->radix_segments, 1u);
+        w.plans[seg].rbits = bits;
+        w.plans[seg].rskip = skip;
+        w.plans[seg].rbase = skip ? (lo >> (64u - skip)) << (64u - skip) : 0ull;
+    }
+}
+
 template <class KT>
 __global__ void __launch_bounds__(1024) k_sample(Work w, Params p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SampleSmem<KT>& sm = *reinterpret_cast<SampleSmem<KT>*>(smem_raw);
     __shared__ uint32_t s_item;
     __shared__ int s_depth;
+    __shared__ float s_ent;
     const Rec* recs = w.rec[w.hdr->round & 1u];
     const uint32_t L = w.hdr->L;
     KT* tree_lvl = reinterpret_cast<KT*>(w.tree_lvl);
@@ -493,6 +569,7 @@ __global__ void __launch_bounds__(1024) k_sample(Work w, Params p) {
         const int kt = max(1, s_depth);
         if (threadIdx.x == 0 && kt != k) w.plans[seg].k = (uint32_t)kt;
         emit_tree(sm.lvl, kt, tree_lvl + P.tree_base, tree_ino + P.tree_base);
+        if (p.radix && !p.learned) choose_radix<KT>(w, p, seg, sm.samp, cnt, (uint32_t)k, sm.ra, &s_ent);
     }
 }
 
@@ -544,6 +621,30 @@ __device__ __forceinline__ void classify_range(const Rec* __restrict__ recs, uin
             const uint32_t e = base + u * blockDim.x + threadIdx.x;
             const uint32_t b = e < hi ? bk[u] : nb;
             if (bid && e < hi) bid[e - lo] = (uint16_t)b;
+            const uint32_t peers = __match_any_sync(FULL_MASK, b);
+            if (lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&hist[b], (uint32_t)__popc(peers));
+        }
+    }
+}
+
+// Radix form of classify_range: the bucket of a key is its digit
+// (radix_bucket), no tree.
+__device__ __forceinline__ void classify_range_radix(const Rec* __restrict__ recs, uint32_t lo, uint32_t hi,
+                                                     uint32_t rskip, uint32_t rbits, uint64_t rbase, uint32_t nb,
+                                                     uint32_t* hist, uint16_t* bid) {
+    const uint32_t lane = threadIdx.x & 31u;
+    for (uint32_t base = lo; base < hi; base += blockDim.x * kClassifyUnroll) {
+        uint64_t kk[kClassifyUnroll];
+#pragma unroll
+        for (int u = 0; u < kClassifyUnroll; u++) {
+            const uint32_t e = base + u * blockDim.x + threadIdx.x;
+            kk[u] = e < hi ? recs[e].key : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < kClassifyUnroll; u++) {
+            const uint32_t e = base + u * blockDim.x + threadIdx.x;
+            const uint32_t b = e < hi ? radix_bucket(kk[u], rskip, rbits, rbase) : nb;
+            if (e < hi) bid[e - lo] = (uint16_t)b;
             const uint32_t peers = __match_any_sync(FULL_MASK, b);
             if (lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&hist[b], (uint32_t)__popc(peers));
         }
@@ -602,16 +703,21 @@ __global__ void __launch_bounds__(kClassifyThreads, SSS_CLASSIFY_MIN_BLOCKS) k_c
         const SegPlan P = w.plans[s];
         const uint32_t ci = c - P.chunk_base;
         const int k = (int)P.k;
-        const uint32_t v = (1u << k) - 1u, nb = 2u * v + 1u;
-        for (uint32_t i = threadIdx.x; i < v; i += blockDim.x) {
-            t.set(i + 1, tree_lvl[P.tree_base + i]);
-            ino[i] = tree_ino[P.tree_base + i];
+        const uint32_t v = (1u << k) - 1u;
+        const uint32_t nb = P.rbits ? radix_buckets(P.rbits) : 2u * v + 1u;
+        if (!P.rbits) {
+            for (uint32_t i = threadIdx.x; i < v; i += blockDim.x) {
+                t.set(i + 1, tree_lvl[P.tree_base + i]);
+                ino[i] = tree_ino[P.tree_base + i];
+            }
         }
         for (uint32_t b = threadIdx.x; b <= nb; b += blockDim.x) hist[b] = 0;
         __syncthreads();
         const uint32_t lo = P.begin + ci * P.chunk;
         const uint32_t hi = min(lo + P.chunk, P.begin + P.size);
-        if constexpr (kLearned) {
+        if (P.rbits) {
+            classify_range_radix(w.rec[cur], lo, hi, P.rskip, P.rbits, P.rbase, nb, hist, w.bids + lo);
+        } else if constexpr (kLearned) {
             if (p.learned && P.size >= kLearnedMinSize) {
                 const float* tab = w.cdf_tab + (size_t)s * (p.cdf_M + 1);
                 for (uint32_t j = threadIdx.x; j <= p.cdf_M; j += blockDim.x) C[j] = tab[j];
@@ -784,8 +890,10 @@ __global__ void __launch_bounds__(kScatterThreads, SSS_SCATTER_MIN_BLOCKS) k_sca
         const SegPlan P = w.plans[s];
         const uint32_t ci = c - P.chunk_base;
         const int k = (int)P.k;
-        const uint32_t v = (1u << k) - 1u, nb = 2u * v + 1u;
-        for (uint32_t i = threadIdx.x; i < v; i += blockDim.x) sm.ino[i] = tree_ino[P.tree_base + i];
+        const uint32_t v = (1u << k) - 1u;
+        const uint32_t nb = P.rbits ? radix_buckets(P.rbits) : 2u * v + 1u;
+        if (!P.rbits)
+            for (uint32_t i = threadIdx.x; i < v; i += blockDim.x) sm.ino[i] = tree_ino[P.tree_base + i];
         __syncthreads();
         const uint32_t* S = w.counts_scan + P.count_base;
         const uint32_t seg_end = P.begin + P.size;
@@ -812,7 +920,8 @@ __global__ void __launch_bounds__(kScatterThreads, SSS_SCATTER_MIN_BLOCKS) k_sca
                 const uint32_t end = (b + 1 < nb) ? P.begin + (s_next[q] - S0) : seg_end;
                 size = end - start;
                 sm.ss.run_pos[b] = P.begin + (s_mine[q] - S0);
-                bi = bucket_info(b, nb, P.depth, sm.ino, size, p.base_threshold);
+                bi = P.rbits ? bucket_info_radix(b, nb, P, size, p.base_threshold)
+                             : bucket_info(b, nb, P.depth, sm.ino, size, p.base_threshold);
                 sm.ss.rdep[b] = refill_code(bi, size, P.depth);
                 if (ci == 0 && size > 0 && start > P.begin) w.out_lcp[start] = kLcpFlag | P.depth;
             }

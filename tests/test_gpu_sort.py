@@ -208,6 +208,11 @@ SMALL_OPTS = [
     # the pS5-Equal classifier
     dict(base_threshold=16, medium_threshold=16, k_max=3, chunk=2048, key_bytes=16, classifier=1),
     dict(base_threshold=128, medium_threshold=2048, k_max=10, chunk=32768, key_bytes=8, classifier=1),
+    # radix classification of every device-wide segment whose sample keys
+    # differ (F4), both key widths, and the entropy-driven choice
+    dict(base_threshold=16, medium_threshold=16, k_max=3, chunk=2048, key_bytes=16, radix=2),
+    dict(base_threshold=16, medium_threshold=16, k_max=6, chunk=2048, key_bytes=8, radix=2),
+    dict(base_threshold=128, medium_threshold=1024, k_max=10, chunk=8192, key_bytes=16, radix=1),
 ]
 
 
@@ -244,7 +249,7 @@ EDGE_CASES = {
 
 @pytest.mark.parametrize("name", sorted(EDGE_CASES))
 @pytest.mark.parametrize("opts", [SMALL_OPTS[0], SMALL_OPTS[1], SMALL_OPTS[3], SMALL_OPTS[4], SMALL_OPTS[5],
-                                  SMALL_OPTS[6], SMALL_OPTS[7]])
+                                  SMALL_OPTS[6], SMALL_OPTS[7], SMALL_OPTS[8], SMALL_OPTS[9]])
 def test_edge_cases(name, opts):
     sss.sss_set_options(**opts)
     items = list(EDGE_CASES[name])
@@ -451,3 +456,45 @@ def test_offsets_beyond_4gib(opts):
     del chars, body
     torch.cuda.empty_cache()
     assert_same(s, u32(perm), u32(lcp))
+
+
+@pytest.mark.parametrize("key_bytes", [8, 16])
+def test_radix_classification_by_sample_entropy(key_bytes):
+    """Option radix = 1 (App. A.2 adaptivity): letters a-z spread the sample's
+    digits almost evenly, so device-wide segments take the digit.  Output
+    identical to the oracle with and without radix rounds, on letters and on
+    DNA (4 characters a byte position: its roots keep the tree)."""
+    sss.sss_set_options(base_threshold=16, medium_threshold=64, k_max=10, chunk=2048, key_bytes=key_bytes, radix=1)
+    s = gen.generate(1, 300_000, 61)
+    perm, lcp = gpu_sort(s)
+    assert sss.sss_get_last_stats().radix_segments > 0
+    assert_same(s, perm, lcp)
+    d = gen.generate(3, 200_000, 62)
+    perm, lcp = gpu_sort(d)
+    assert_same(d, perm, lcp)
+    sss.sss_set_options(radix=0)
+    perm0, lcp0 = gpu_sort(s)
+    assert sss.sss_get_last_stats().radix_segments == 0
+    assert_same(s, perm0, lcp0)
+
+
+@pytest.mark.parametrize("radix", [1, 2])
+def test_radix_graph_and_batched_forms(radix):
+    """Radix rounds inside the graph form and the batched sort."""
+    sss.sss_set_options(base_threshold=16, medium_threshold=16, k_max=8, chunk=2048, radix=radix, graph=1)
+    for kind in (1, 2, 3):
+        s = gen.generate(kind, 80_000, 70 + kind)
+        perm, lcp = gpu_sort(s)
+        assert_same(s, perm, lcp)
+    b = gen.generate_batch(120, 100, 3000, 77)
+    chars, offsets = to_dev(b.strings)
+    perm = torch.full((b.strings.n,), -1, dtype=torch.int32, device="cuda")
+    lcp = torch.full((b.strings.n,), -1, dtype=torch.int32, device="cuda")
+    sss.sss_sort_batched(chars, offsets, b.strings.n, b.set_begin, 120, perm, lcp)
+    torch.cuda.synchronize()
+    p, l = u32(perm), u32(lcp)
+    for j in range(120):
+        lo, hi = int(b.set_begin[j]), int(b.set_begin[j + 1])
+        ss = gen.set_strings(b, j)
+        code, bad = oracle.verify(ss.chars, ss.offsets, p[lo:hi], l[lo:hi])
+        assert code == 0, (j, code, bad)
