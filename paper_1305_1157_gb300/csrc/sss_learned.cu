@@ -371,30 +371,49 @@ __global__ void __launch_bounds__(kFitThreads) k_cdf_fit(Work w, Params p) {
     }
     __syncthreads();
     // pieces of each group: one, plus a share of the rest proportional to
-    // the group's keys; what rounding leaves goes to the largest group
-    if (tid == 0) {
-        X.nrm.kmin = kmin;
-        X.nrm.kmax = kmax;
-        X.nrm.c = cb;
-        X.nrm.pad = 0;
-        uint32_t G = 0, big = 0;
-        for (uint32_t d = 0; d < 256; d++) {
-            if (X.cnt[d]) G++;
-            if (X.cnt[d] > X.cnt[big]) big = d;
-        }
+    // the group's keys; what rounding leaves goes to the largest group.  One
+    // thread a digit group; the first piece of each group is a prefix sum.
+    {
+        const uint32_t cnt = tid < 256u ? X.cnt[tid] : 0u;
+        const uint32_t G = (uint32_t)__syncthreads_count(cnt > 0u);  // groups with sample keys
         const bool one_each = G <= M;
         const uint32_t spare = one_each ? M - G : M;
-        uint32_t total = 0;
-        for (uint32_t d = 0; d < 256; d++)
-            if (X.cnt[d]) total += (one_each ? 1u : 0u) + (uint32_t)(((uint64_t)spare * X.cnt[d]) / S);
-        uint32_t o = 0;
-        for (uint32_t d = 0; d < 256; d++) {
-            X.nrm.O[d] = (uint16_t)o;
-            if (X.cnt[d]) o += (one_each ? 1u : 0u) + (uint32_t)(((uint64_t)spare * X.cnt[d]) / S);
-            if (d == big) o += M - total;
+        const uint32_t K = cnt ? (one_each ? 1u : 0u) + (spare * cnt) / S : 0u;  // spare * cnt < 2^28
+        if (tid == 0) {
+            X.kmin = 0ull;  // reused: largest group (count, digit) and total pieces
+            X.kmax = 0ull;
         }
-        X.nrm.O[256] = (uint16_t)(cb < 8u ? o : M);
-        for (uint32_t d = 257; d < 260; d++) X.nrm.O[d] = 0;
+        __syncthreads();
+        if (tid < 256u && cnt) {
+            atomicMax(&X.kmin, ((unsigned long long)cnt << 8) | tid);
+            atomicAdd(&X.kmax, (unsigned long long)K);
+        }
+        // exclusive prefix of K over the 256 digits (warps 0-7)
+        uint32_t inc = K;
+        const uint32_t w8 = tid >> 5;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+            if (lane >= (uint32_t)o) inc += y;
+        }
+        __shared__ uint32_t wtot[8];
+        if (tid < 256u && lane == 31u) wtot[w8] = inc;
+        __syncthreads();
+        if (tid < 256u) {
+            uint32_t before = 0;
+            for (uint32_t q = 0; q < w8; q++) before += wtot[q];
+            const uint32_t big = (uint32_t)(X.kmin & 0xFFull);
+            const uint32_t rem = M - (uint32_t)X.kmax;
+            X.nrm.O[tid] = (uint16_t)(before + inc - K + (tid > big ? rem : 0u));
+        }
+        if (tid == 0) {
+            X.nrm.kmin = kmin;
+            X.nrm.kmax = kmax;
+            X.nrm.c = cb;
+            X.nrm.pad = 0;
+            X.nrm.O[256] = (uint16_t)M;
+            for (uint32_t d = 257; d < 260; d++) X.nrm.O[d] = 0;
+        }
     }
     for (uint32_t d = tid; d < 256; d += blockDim.x) {
         const uint64_t g0 = X.nrm.gmin[d], g1 = X.gmax[d];
