@@ -644,6 +644,10 @@ def main():
     prof_ms = np.zeros(len(sss.K_CLASSES))
     prof_launches = np.zeros(len(sss.K_CLASSES), dtype=np.int64)
     large_strings = large_refills = medium_strings = medium_refills = base_strings = 0
+    # a single sort above the medium threshold classifies its root round while
+    # k_init_classify builds the records (class "init"), not in k_classify
+    root_fused = args.mode != "learned" and n > int(opts.medium_threshold)
+    fused_root_strings = 0
     sort_fn(chars, offsets, n, perm, lcp, stream)  # warm the host-driven form
     torch.cuda.synchronize(dev)
     p_start = torch.cuda.Event(enable_timing=True)
@@ -655,6 +659,8 @@ def main():
         prof_ms += np.array(list(st.prof_ms))
         prof_launches += np.array(list(st.prof_launches))
         large_strings += st.round_strings - st.medium_strings
+        if root_fused and st.rounds:
+            fused_root_strings += st.round_active[0]
         large_refills += st.refilled_strings - st.medium_refilled_strings
         medium_strings += st.medium_strings
         medium_refills += st.medium_refilled_strings
@@ -722,10 +728,10 @@ def main():
     # algorithmic bytes per kernel class: device-wide rounds (k_classify,
     # k_scatter) see the large segments' strings, k_med_round the medium ones
     algo = {"scatter": SCATTER_BYTES_PER_STRING * large_strings + REFILL_BYTES * large_refills,
-            "classify": CLASSIFY_BYTES_PER_STRING * large_strings,
+            "classify": CLASSIFY_BYTES_PER_STRING * (large_strings - fused_root_strings),
             "medium": MEDIUM_BYTES_PER_STRING * medium_strings + REFILL_BYTES * medium_refills,
             "base": BASE_BYTES_PER_STRING * base_strings}
-    units = {"scatter": large_strings, "classify": large_strings, "medium": medium_strings,
+    units = {"scatter": large_strings, "classify": large_strings - fused_root_strings, "medium": medium_strings,
              "base": base_strings}
     kname = {"scatter": "k_scatter", "classify": "k_classify", "base": "k_base",
              "medium": "k_med_round"}.get(cls[dom], "k_" + cls[dom])

@@ -376,12 +376,13 @@ int run_sort(const Work& w, const sss_options& o, const Seg* roots_dev, uint32_t
              bool reset_prof = true) {
     Params p{learned ? 1 : 0, o.cdf_segments, o.cdf_steps, o.cdf_lr, o.k_max, o.base_threshold,
              o.medium_threshold, o.chunk, o.seed, device_sms(), learned ? 8u : o.key_bytes,
-             learned ? 0u : o.classifier, learned ? 0u : o.radix};
+             learned ? 0u : o.classifier, learned ? 0u : o.radix,
+             (!roots_dev && !learned && w.n > o.medium_threshold) ? 1u : 0u};
     Prof* pf = &g_prof;
     if (reset_prof) pf->reset(o.profile != 0);
     memset(stats, 0, sizeof(*stats));
     CK(prepare_kernels(o.cdf_segments), "kernel attributes");
-    CK(launch_init(w, pf, st), "init");
+    CK(launch_init(w, p, pf, st), "init");
     CK(launch_roots(w, p, roots_dev, num_roots, pf, st), "roots");
     CK(launch_plan(w, p, pf, st), "plan");
     const Branches* br = nullptr;
@@ -389,6 +390,7 @@ int run_sort(const Work& w, const sss_options& o, const Seg* roots_dev, uint32_t
     if (rc) return rc;
     rc = read_hdr(hh, w, st);
     if (rc) return rc;
+    CK(launch_fused_root(w, p, hh, pf, st), "root round");
     for (uint32_t round = 0; hh->L > 0 || hh->n_med_snap > 0; round++) {
         if (round >= 1u << 22) return fail(SSS_ERR_INTERNAL, "round limit exceeded");
         if (round < SSS_MAX_ROUNDS_LOGGED) {
@@ -510,9 +512,10 @@ int build_graph(const Work& w, const Params& p, const Seg* roots_dev, uint32_t n
     if ((err = cudaGraphConditionalHandleCreate(&cond, graph, 0, 0)) != cudaSuccess)
         return done(err, "conditional handle");
     // prologue
-    if ((err = launch_init(w, &counter, st)) != cudaSuccess ||
+    if ((err = launch_init(w, p, &counter, st)) != cudaSuccess ||
         (err = launch_roots(w, p, roots_dev, num_roots, &counter, st)) != cudaSuccess ||
         (err = launch_plan(w, p, &counter, st)) != cudaSuccess ||
+        (err = launch_fused_root(w, p, nullptr, &counter, st)) != cudaSuccess ||
         (err = launch_set_cond(w, cond, st)) != cudaSuccess)
         return done(err, "graph prologue");
     gc.launches_prologue = counter.launches + 1;
@@ -574,7 +577,8 @@ int run_sort_graph(const Work& w, const sss_options& o, const Seg* roots_dev, ui
                    cudaStream_t st, sss_stats* stats, bool learned, const GraphKey& key) {
     Params p{learned ? 1 : 0, o.cdf_segments, o.cdf_steps, o.cdf_lr, o.k_max, o.base_threshold,
              o.medium_threshold, o.chunk, o.seed, device_sms(), learned ? 8u : o.key_bytes,
-             learned ? 0u : o.classifier, learned ? 0u : o.radix};
+             learned ? 0u : o.classifier, learned ? 0u : o.radix,
+             (!roots_dev && !learned && w.n > o.medium_threshold) ? 1u : 0u};
     memset(stats, 0, sizeof(*stats));
     int dev = 0;
     CK(cudaGetDevice(&dev), "cudaGetDevice");

@@ -147,6 +147,8 @@ struct Params {
     uint32_t equal_test;      // 1: equality test at every tree node (pS^5-Equal)
     uint32_t radix;           // 0: splitter trees only; 1: a digit where the sample's digits are
                               // near uniform; 2: a digit wherever the sample keys differ
+    uint32_t fuse_root;       // 1: one root above the medium threshold, whose first round samples
+                              // the strings directly and classifies while the records are built
 };
 
 // Views of the workspace and the caller's buffers for one sort.
@@ -675,7 +677,13 @@ struct ProfScope {
 
 // ------------------------------------------------------------ launches
 
-cudaError_t launch_init(const Work& w, Prof* pf, cudaStream_t st);
+// records: the key words at depth 0 of every string (skipped with
+// p.fuse_root: launch_fused_root builds them)
+cudaError_t launch_init(const Work& w, const Params& p, Prof* pf, cudaStream_t st);
+// p.fuse_root: the root's sample and splitter tree straight from the strings,
+// then one pass that builds the records and classifies them for round 0
+// (round 0's k_sample and k_classify then return at once).  Needs the plan.
+cudaError_t launch_fused_root(const Work& w, const Params& p, const Hdr* hc, Prof* pf, cudaStream_t st);
 // roots == nullptr: one root [0, n); else num_roots device segments (batched)
 cudaError_t launch_roots(const Work& w, const Params& p, const Seg* roots, uint32_t num_roots, Prof* pf,
                          cudaStream_t st);

@@ -544,13 +544,29 @@ __device__ void choose_radix(const Work& w, const Params& p, uint32_t seg, const
     }
 }
 
+// The key of the string at byte offset o at depth 0, read from the strings.
+template <class KT> __device__ __forceinline__ KT key_at(const uint8_t* chars, uint64_t o);
+template <> __device__ __forceinline__ uint64_t key_at<uint64_t>(const uint8_t* chars, uint64_t o) {
+    return load_key(chars, o);
+}
+template <> __device__ __forceinline__ Key16 key_at<Key16>(const uint8_t* chars, uint64_t o) {
+    Key16 x;
+    load_key2(chars, o, x.h, x.l);
+    return x;
+}
+
+// from_strings = 1: round 0 of a fused sort (p.fuse_root), launched before
+// the records exist: the sample keys come from the strings themselves.  The
+// round body's own launch in that round returns at once.
 template <class KT>
-__global__ void __launch_bounds__(1024) k_sample(Work w, Params p) {
+__global__ void __launch_bounds__(1024) k_sample(Work w, Params p, int from_strings) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SampleSmem<KT>& sm = *reinterpret_cast<SampleSmem<KT>*>(smem_raw);
     __shared__ uint32_t s_item;
     __shared__ int s_depth;
     __shared__ float s_ent;
+    const bool fused0 = p.fuse_root && w.hdr->round == 0u;
+    if (fused0 != (from_strings != 0)) return;
     const Rec* recs = w.rec[w.hdr->round & 1u];
     const uint32_t L = w.hdr->L;
     KT* tree_lvl = reinterpret_cast<KT*>(w.tree_lvl);
@@ -560,9 +576,14 @@ __global__ void __launch_bounds__(1024) k_sample(Work w, Params p) {
         const int k = (int)P.kp;
         const uint32_t pw = 2u << k;
         const uint32_t cnt = pw - 1u;  // alpha (v + 1) - 1 with alpha = 2
-        for (uint32_t j = threadIdx.x; j < pw; j += blockDim.x)
-            sm.samp[j] = j < cnt ? KeyTraits<KT>::load(recs + P.begin + sample_pos(p.seed, P.begin, P.size, j))
-                                 : KeyTraits<KT>::top();
+        for (uint32_t j = threadIdx.x; j < pw; j += blockDim.x) {
+            KT x = KeyTraits<KT>::top();
+            if (j < cnt) {
+                const uint32_t e = P.begin + sample_pos(p.seed, P.begin, P.size, j);
+                x = from_strings ? key_at<KT>(w.chars, w.offsets[e]) : KeyTraits<KT>::load(recs + e);
+            }
+            sm.samp[j] = x;
+        }
         __syncthreads();
         bitonic_sort(sm.samp, pw);
         select_splitters(sm.samp, cnt, k, sm.lvl, sm.ra, sm.rb, &s_depth);
@@ -694,6 +715,7 @@ __global__ void __launch_bounds__(kClassifyThreads, SSS_CLASSIFY_MIN_BLOCKS) k_c
     __shared__ typename std::conditional<kLearned, CdfNorm, char>::type nrm_s;
     __shared__ uint32_t s_item;
     const int cur = w.hdr->round & 1u;
+    if (p.fuse_root && cur == 0 && w.hdr->round == 0u) return;  // classified while the records were built
     const uint32_t total_chunks = w.hdr->total_chunks;
     const KT* tree_lvl = reinterpret_cast<const KT*>(w.tree_lvl);
     const KT* tree_ino = reinterpret_cast<const KT*>(w.tree_ino);
@@ -743,6 +765,82 @@ __global__ void __launch_bounds__(kClassifyThreads, SSS_CLASSIFY_MIN_BLOCKS) k_c
         __syncthreads();
         // the count rows were planned for 2^(kp+1) - 1 buckets: the rows a
         // smaller tree leaves unused are zero
+        const uint32_t nbp = (2u << P.kp) - 1u;
+        for (uint32_t b = threadIdx.x; b < nbp; b += blockDim.x)
+            w.counts[P.count_base + b * P.chunks + ci] = b < nb ? hist[b] : 0u;
+        __syncthreads();
+    }
+}
+
+// Round 0 of a fused sort: one pass over the root's work chunks builds each
+// string's record (its key words at depth 0, as k_init does) and classifies
+// the keys while they are in registers, as k_classify does (tree or digit,
+// bucket ids, per-chunk histogram): the round's classification needs no
+// second read of the records.
+template <class KT>
+__global__ void __launch_bounds__(kClassifyThreads, SSS_CLASSIFY_MIN_BLOCKS) k_init_classify(Work w, Params p) {
+    __shared__ LevelTree<KT, kVMax + 1> t;
+    __shared__ KT ino[kVMax];
+    __shared__ uint32_t hist[kNBMax + 1];
+    __shared__ uint32_t s_item;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t total_chunks = w.hdr->total_chunks;
+    const KT* tree_lvl = reinterpret_cast<const KT*>(w.tree_lvl);
+    const KT* tree_ino = reinterpret_cast<const KT*>(w.tree_ino);
+    Rec* recs = w.rec[0];
+    for (uint32_t c = first_item(); c < total_chunks; c = next_item(&w.hdr->q_classify, &s_item)) {
+        const uint32_t s = w.chunk_seg[c];
+        const SegPlan P = w.plans[s];
+        const uint32_t ci = c - P.chunk_base;
+        const int k = (int)P.k;
+        const uint32_t v = (1u << k) - 1u;
+        const uint32_t nb = P.rbits ? radix_buckets(P.rbits) : 2u * v + 1u;
+        if (!P.rbits) {
+            for (uint32_t i = threadIdx.x; i < v; i += blockDim.x) {
+                t.set(i + 1, tree_lvl[P.tree_base + i]);
+                ino[i] = tree_ino[P.tree_base + i];
+            }
+        }
+        for (uint32_t b = threadIdx.x; b <= nb; b += blockDim.x) hist[b] = 0;
+        __syncthreads();
+        const uint32_t lo = P.begin + ci * P.chunk;
+        const uint32_t hi = min(lo + P.chunk, P.begin + P.size);
+        for (uint32_t base = lo; base < hi; base += blockDim.x * kClassifyUnroll) {
+            KT kk[kClassifyUnroll];
+#pragma unroll
+            for (int u = 0; u < kClassifyUnroll; u++) {
+                const uint32_t e = base + u * blockDim.x + threadIdx.x;
+                kk[u] = KeyTraits<KT>::top();
+                if (e < hi) {
+                    const uint64_t o = w.offsets[e];
+                    Rec r;
+                    load_key2(w.chars, o, r.key, r.key2);
+                    r.off = o | kK2Valid;
+                    r.idx = e;
+                    r.pad = 0;
+                    store_rec(recs + e, r);
+                    w.out_lcp[e] = 0u;
+                    kk[u] = KeyTraits<KT>::of(r);
+                }
+            }
+            uint32_t bk[kClassifyUnroll];
+            if (P.rbits) {
+#pragma unroll
+                for (int u = 0; u < kClassifyUnroll; u++)
+                    bk[u] = radix_bucket(KeyTraits<KT>::word(kk[u]), P.rskip, P.rbits, P.rbase);
+            } else {
+                classify_keys_by<kClassifyUnroll>(p.equal_test != 0, kk, bk, t.view(), ino, k);
+            }
+#pragma unroll
+            for (int u = 0; u < kClassifyUnroll; u++) {
+                const uint32_t e = base + u * blockDim.x + threadIdx.x;
+                const uint32_t b = e < hi ? bk[u] : nb;
+                if (e < hi) w.bids[e] = (uint16_t)b;
+                const uint32_t peers = __match_any_sync(FULL_MASK, b);
+                if (lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&hist[b], (uint32_t)__popc(peers));
+            }
+        }
+        __syncthreads();
         const uint32_t nbp = (2u << P.kp) - 1u;
         for (uint32_t b = threadIdx.x; b < nbp; b += blockDim.x)
             w.counts[P.count_base + b * P.chunks + ci] = b < nb ? hist[b] : 0u;
@@ -1545,15 +1643,39 @@ uint32_t device_sms() {
     return sms > 0 ? (uint32_t)sms : 148u;
 }
 
-cudaError_t launch_init(const Work& w, Prof* pf, cudaStream_t st) {
+// Grid of a queue-driven kernel: one CTA per work item when the host knows
+// the count (0 = nothing to launch), else `fixed` persistent CTAs.
+static uint32_t grid_of(uint32_t fixed, const Hdr* hc, uint32_t known) { return hc ? known : fixed; }
+
+cudaError_t launch_init(const Work& w, const Params& p, Prof* pf, cudaStream_t st) {
     if (w.n) {
         // the shadow arrays only ever hold valid string indices and offsets
         cudaError_t e = cudaMemsetAsync(w.rec[1], 0, sizeof(Rec) * (size_t)w.n, st);  // index 0, offset 0
         if (e != cudaSuccess) return e;
-        ProfScope ps(pf, kInit, st);
-        k_init<<<grid_for(w.n, 256, 16, device_sms()), 256, 0, st>>>(w);
+        if (!p.fuse_root) {
+            ProfScope ps(pf, kInit, st);
+            k_init<<<grid_for(w.n, 256, 16, device_sms()), 256, 0, st>>>(w);
+        }
     }
     return cudaGetLastError();
+}
+
+template <class KT>
+static cudaError_t launch_fused_root_t(const Work& w, const Params& p, const Hdr* hc, Prof* pf, cudaStream_t st) {
+    {
+        ProfScope ps(pf, kSample, st);
+        k_sample<KT><<<1, 1024, sizeof(SampleSmem<KT>), st>>>(w, p, 1);
+    }
+    ProfScope ps(pf, kInit, st);
+    const uint32_t g = grid_of(p.num_sms * SSS_CLASSIFY_MIN_BLOCKS, hc, hc ? hc->total_chunks : 0u);
+    if (g) k_init_classify<KT><<<g, kClassifyThreads, 0, st>>>(w, p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fused_root(const Work& w, const Params& p, const Hdr* hc, Prof* pf, cudaStream_t st) {
+    if (!p.fuse_root) return cudaSuccess;
+    return p.key_bytes == 16 ? launch_fused_root_t<Key16>(w, p, hc, pf, st)
+                             : launch_fused_root_t<uint64_t>(w, p, hc, pf, st);
 }
 
 cudaError_t launch_roots(const Work& w, const Params& p, const Seg* roots, uint32_t num_roots, Prof* pf,
@@ -1578,10 +1700,6 @@ cudaError_t launch_plan(const Work& w, const Params& p, Prof* pf, cudaStream_t s
     return cudaGetLastError();
 }
 
-// Grid of a queue-driven kernel: one CTA per work item when the host knows
-// the count (0 = nothing to launch), else `fixed` persistent CTAs.
-static uint32_t grid_of(uint32_t fixed, const Hdr* hc, uint32_t known) { return hc ? known : fixed; }
-
 __global__ void k_advance(Work w) { w.hdr->round += 1u; }
 
 template <class KT>
@@ -1591,7 +1709,7 @@ static cudaError_t launch_round_t(const Work& w, const Params& p, const Hdr* hc,
     if (gL) {
         {
             ProfScope ps(pf, kSample, st);
-            k_sample<KT><<<gL, 1024, sizeof(SampleSmem<KT>), st>>>(w, p);
+            k_sample<KT><<<gL, 1024, sizeof(SampleSmem<KT>), st>>>(w, p, 0);
         }
         if (p.learned) {
             // one CTA per SM at most: a fit CTA holds most of an SM's shared
