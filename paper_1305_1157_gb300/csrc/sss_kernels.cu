@@ -381,6 +381,63 @@ __device__ void bitonic_sort(KT* s, uint32_t pw) {
     }
 }
 
+template <class KT> __device__ __forceinline__ KT shfl_xor_key(const KT& x, int m);
+template <> __device__ __forceinline__ uint64_t shfl_xor_key<uint64_t>(const uint64_t& x, int m) {
+    return __shfl_xor_sync(FULL_MASK, x, m);
+}
+template <> __device__ __forceinline__ Key16 shfl_xor_key<Key16>(const Key16& x, int m) {
+    return Key16{__shfl_xor_sync(FULL_MASK, x.h, m), __shfl_xor_sync(FULL_MASK, x.l, m)};
+}
+
+// One compare-exchange of the bitonic network seen from element i holding x,
+// whose partner i ^ stride holds y: the lower element of an ascending pair
+// (and the upper of a descending one) keeps the smaller key.
+template <class KT>
+__device__ __forceinline__ KT bitonic_keep(const KT& x, const KT& y, uint32_t i, uint32_t stride, uint32_t size) {
+    const bool keep_min = ((i & stride) == 0u) == ((i & size) == 0u);
+    return kgt(x, y) == keep_min ? y : x;
+}
+
+// The same ascending bitonic network as bitonic_sort over n2 = max(pw, 64)
+// keys, two a thread: element 2t + r is x[r] of thread t (threads with
+// 2t >= n2 idle; keys past the caller's own are top).  Stride 1 is exchanged
+// within the thread, strides 2..32 by warp shuffles, and only the strides
+// of 64 and more through s, so that most of the network's stages need
+// neither shared memory nor a barrier.  Leaves s[0..pw) sorted; called by
+// the whole block, ends with __syncthreads.
+template <class KT>
+__device__ void bitonic_sort_regs(KT* s, KT x0, KT x1, uint32_t pw) {
+    const uint32_t n2 = max(pw, 64u);
+    const uint32_t i0 = 2u * threadIdx.x, i1 = i0 + 1u;
+    const bool act = i0 < n2;  // whole warps: n2 is a multiple of 64
+    for (uint32_t size = 2; size <= n2; size <<= 1) {
+        for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+            if (stride >= 64u) {
+                if (act) { s[i0] = x0; s[i1] = x1; }
+                __syncthreads();
+                if (act) {
+                    const KT y0 = s[i0 ^ stride], y1 = s[i1 ^ stride];
+                    x0 = bitonic_keep(x0, y0, i0, stride, size);
+                    x1 = bitonic_keep(x1, y1, i1, stride, size);
+                }
+                __syncthreads();
+            } else if (act) {
+                if (stride >= 2u) {
+                    const KT y0 = shfl_xor_key(x0, (int)(stride >> 1)), y1 = shfl_xor_key(x1, (int)(stride >> 1));
+                    x0 = bitonic_keep(x0, y0, i0, stride, size);
+                    x1 = bitonic_keep(x1, y1, i1, stride, size);
+                } else if (kgt(x0, x1) == ((i0 & size) == 0u)) {
+                    const KT y = x0;
+                    x0 = x1;
+                    x1 = y;
+                }
+            }
+        }
+    }
+    if (i0 < pw) { s[i0] = x0; s[i1] = x1; }
+    __syncthreads();
+}
+
 template <class KT>
 __device__ __forceinline__ uint32_t lower_bound_k(const KT* s, uint32_t n, const KT& x) {
     uint32_t lo = 0, hi = n;
@@ -576,16 +633,18 @@ __global__ void __launch_bounds__(1024) k_sample(Work w, Params p, int from_stri
         const int k = (int)P.kp;
         const uint32_t pw = 2u << k;
         const uint32_t cnt = pw - 1u;  // alpha (v + 1) - 1 with alpha = 2
-        for (uint32_t j = threadIdx.x; j < pw; j += blockDim.x) {
-            KT x = KeyTraits<KT>::top();
+        // sample keys 2t and 2t + 1 go to thread t (top past the sample)
+        KT x[2];
+#pragma unroll
+        for (int r = 0; r < 2; r++) {
+            const uint32_t j = 2u * threadIdx.x + r;
+            x[r] = KeyTraits<KT>::top();
             if (j < cnt) {
                 const uint32_t e = P.begin + sample_pos(p.seed, P.begin, P.size, j);
-                x = from_strings ? key_at<KT>(w.chars, w.offsets[e]) : KeyTraits<KT>::load(recs + e);
+                x[r] = from_strings ? key_at<KT>(w.chars, w.offsets[e]) : KeyTraits<KT>::load(recs + e);
             }
-            sm.samp[j] = x;
         }
-        __syncthreads();
-        bitonic_sort(sm.samp, pw);
+        bitonic_sort_regs(sm.samp, x[0], x[1], pw);
         select_splitters(sm.samp, cnt, k, sm.lvl, sm.ra, sm.rb, &s_depth);
         const int kt = max(1, s_depth);
         if (threadIdx.x == 0 && kt != k) w.plans[seg].k = (uint32_t)kt;
@@ -777,8 +836,13 @@ __global__ void __launch_bounds__(kClassifyThreads, SSS_CLASSIFY_MIN_BLOCKS) k_c
 // the keys while they are in registers, as k_classify does (tree or digit,
 // bucket ids, per-chunk histogram): the round's classification needs no
 // second read of the records.
+// four CTAs per SM: the phased loads of four keys need 64 registers (at
+// five CTAs per SM they spill, and the kernel was slower)
+#ifndef SSS_INIT_CLASSIFY_MIN_BLOCKS
+#define SSS_INIT_CLASSIFY_MIN_BLOCKS 4
+#endif
 template <class KT>
-__global__ void __launch_bounds__(kClassifyThreads, SSS_CLASSIFY_MIN_BLOCKS) k_init_classify(Work w, Params p) {
+__global__ void __launch_bounds__(kClassifyThreads, SSS_INIT_CLASSIFY_MIN_BLOCKS) k_init_classify(Work w, Params p) {
     __shared__ LevelTree<KT, kVMax + 1> t;
     __shared__ KT ino[kVMax];
     __shared__ uint32_t hist[kNBMax + 1];
@@ -806,16 +870,30 @@ __global__ void __launch_bounds__(kClassifyThreads, SSS_CLASSIFY_MIN_BLOCKS) k_i
         const uint32_t lo = P.begin + ci * P.chunk;
         const uint32_t hi = min(lo + P.chunk, P.begin + P.size);
         for (uint32_t base = lo; base < hi; base += blockDim.x * kClassifyUnroll) {
+            // three phases, so that every load of the unrolled keys is in
+            // flight before the first store: offsets, key words, records
+            uint64_t o[kClassifyUnroll], k1[kClassifyUnroll], k2[kClassifyUnroll];
+#pragma unroll
+            for (int u = 0; u < kClassifyUnroll; u++) {
+                const uint32_t e = base + u * blockDim.x + threadIdx.x;
+                o[u] = e < hi ? __ldg(w.offsets + e) : 0ull;
+            }
+#pragma unroll
+            for (int u = 0; u < kClassifyUnroll; u++) {
+                const uint32_t e = base + u * blockDim.x + threadIdx.x;
+                k1[u] = k2[u] = 0ull;
+                if (e < hi) load_key2(w.chars, o[u], k1[u], k2[u]);
+            }
             KT kk[kClassifyUnroll];
 #pragma unroll
             for (int u = 0; u < kClassifyUnroll; u++) {
                 const uint32_t e = base + u * blockDim.x + threadIdx.x;
                 kk[u] = KeyTraits<KT>::top();
                 if (e < hi) {
-                    const uint64_t o = w.offsets[e];
                     Rec r;
-                    load_key2(w.chars, o, r.key, r.key2);
-                    r.off = o | kK2Valid;
+                    r.key = k1[u];
+                    r.key2 = k2[u];
+                    r.off = o[u] | kK2Valid;
                     r.idx = e;
                     r.pad = 0;
                     store_rec(recs + e, r);
@@ -1648,14 +1726,14 @@ uint32_t device_sms() {
 static uint32_t grid_of(uint32_t fixed, const Hdr* hc, uint32_t known) { return hc ? known : fixed; }
 
 cudaError_t launch_init(const Work& w, const Params& p, Prof* pf, cudaStream_t st) {
-    if (w.n) {
+    if (w.n && !p.fuse_root) {
         // the shadow arrays only ever hold valid string indices and offsets
+        // (a fused root needs no clearing: its round 0 scatters the single
+        // root over every position of the shadow array before any reads)
         cudaError_t e = cudaMemsetAsync(w.rec[1], 0, sizeof(Rec) * (size_t)w.n, st);  // index 0, offset 0
         if (e != cudaSuccess) return e;
-        if (!p.fuse_root) {
-            ProfScope ps(pf, kInit, st);
-            k_init<<<grid_for(w.n, 256, 16, device_sms()), 256, 0, st>>>(w);
-        }
+        ProfScope ps(pf, kInit, st);
+        k_init<<<grid_for(w.n, 256, 16, device_sms()), 256, 0, st>>>(w);
     }
     return cudaGetLastError();
 }
@@ -1667,7 +1745,7 @@ static cudaError_t launch_fused_root_t(const Work& w, const Params& p, const Hdr
         k_sample<KT><<<1, 1024, sizeof(SampleSmem<KT>), st>>>(w, p, 1);
     }
     ProfScope ps(pf, kInit, st);
-    const uint32_t g = grid_of(p.num_sms * SSS_CLASSIFY_MIN_BLOCKS, hc, hc ? hc->total_chunks : 0u);
+    const uint32_t g = grid_of(p.num_sms * SSS_INIT_CLASSIFY_MIN_BLOCKS, hc, hc ? hc->total_chunks : 0u);
     if (g) k_init_classify<KT><<<g, kClassifyThreads, 0, st>>>(w, p);
     return cudaGetLastError();
 }
