@@ -458,6 +458,65 @@ __device__ __forceinline__ uint32_t upper_bound_k(const KT* s, uint32_t n, const
     return lo;
 }
 
+// Runs of equal keys in the sorted sample s[0..cnt): lo[i] is the first
+// index of the run holding s[i] and hi[i] one past its last, i.e. the lower
+// and upper bound of s[i] in s.  Thread t takes indices PER t .. PER t +
+// PER - 1; a prefix maximum over the run heads and a suffix minimum over the
+// run tails (within the thread, by warp shuffles, then over the warps'
+// totals in wtmp[2 * warps]) give them for every index in one pass, where a
+// binary search per tree node would read the sample at data-dependent
+// indices.  Needs PER * blockDim.x >= cnt; called by the whole block, ends
+// with __syncthreads.
+template <int PER, class KT>
+__device__ void equal_runs(const KT* s, uint32_t cnt, uint16_t* lo, uint16_t* hi, uint32_t* wtmp) {
+    constexpr uint32_t kInf = 0xFFFFu;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t base = PER * threadIdx.x;
+    // a[j]: index of the latest run head at or before base + j; b[j]: one
+    // past the earliest run tail at or after it (within this thread)
+    uint32_t a[PER], b[PER];
+    uint32_t run = 0u;
+#pragma unroll
+    for (int j = 0; j < PER; j++) {
+        const uint32_t i = base + j;
+        if (i < cnt && (i == 0u || !keq(s[i - 1u], s[i]))) run = i;
+        a[j] = run;
+    }
+    uint32_t nxt = kInf;
+#pragma unroll
+    for (int j = PER - 1; j >= 0; j--) {
+        const uint32_t i = base + j;
+        if (i < cnt && (i + 1u >= cnt || !keq(s[i], s[i + 1u]))) nxt = i + 1u;
+        b[j] = nxt;
+    }
+    uint32_t pa = a[PER - 1], sb = b[0];  // inclusive scans over the lanes
+#pragma unroll
+    for (uint32_t o = 1; o < 32u; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL_MASK, pa, o);
+        const uint32_t z = __shfl_down_sync(FULL_MASK, sb, o);
+        if (lane >= o) pa = max(pa, y);
+        if (lane + o < 32u) sb = min(sb, z);
+    }
+    if (lane == 31u) wtmp[warp] = pa;
+    if (lane == 0u) wtmp[nw + warp] = sb;
+    __syncthreads();
+    uint32_t cpre = __shfl_up_sync(FULL_MASK, pa, 1);
+    uint32_t csuf = __shfl_down_sync(FULL_MASK, sb, 1);
+    if (lane == 0u) cpre = 0u;
+    if (lane == 31u) csuf = kInf;
+    for (uint32_t v = 0; v < warp; v++) cpre = max(cpre, wtmp[v]);
+    for (uint32_t v = warp + 1u; v < nw; v++) csuf = min(csuf, wtmp[nw + v]);
+#pragma unroll
+    for (int j = 0; j < PER; j++) {
+        const uint32_t i = base + j;
+        if (i < cnt) {
+            lo[i] = (uint16_t)max(cpre, a[j]);
+            hi[i] = (uint16_t)min(csuf, b[j]);
+        }
+    }
+    __syncthreads();
+}
+
 // Splitter choice of Sec. 3.1 on the sorted sample s[0..cnt): a node owning
 // the range a..b takes its middle sample x; its children own a..b' and a'..b
 // where b' and a' skip every sample equal to x.  A node whose range is empty
@@ -467,10 +526,13 @@ __device__ __forceinline__ uint32_t upper_bound_k(const KT* s, uint32_t n, const
 // non-empty range.  Below them every node repeats its parent's splitter, so
 // the tree cut to those levels has the same non-empty buckets (the paper's
 // "inspect the sample" adaptivity, App. A.2: samples with many equal keys
-// get smaller trees).
+// get smaller trees).  run_lo/run_hi (optional): for every index i of s, the
+// first index of the run of keys equal to s[i] and one past its last (see
+// equal_runs); without them each node finds its run by binary search.
 template <class KT>
 __device__ void select_splitters(const KT* s, uint32_t cnt, int k, KT* lvl, int32_t* ra, int32_t* rb,
-                                 int* depth_used = nullptr) {
+                                 int* depth_used = nullptr, const uint16_t* run_lo = nullptr,
+                                 const uint16_t* run_hi = nullptr) {
     const uint32_t v = (1u << k) - 1u;
     if (threadIdx.x == 0) {
         ra[1] = 0;
@@ -488,8 +550,9 @@ __device__ void select_splitters(const KT* s, uint32_t cnt, int k, KT* lvl, int3
                 if (depth_used) atomicMax(depth_used, l + 1);
                 int32_t m = a + (b - a) / 2;
                 x = s[m];
-                int32_t first_eq = (int32_t)lower_bound_k(s, cnt, x);
-                int32_t past_eq = (int32_t)upper_bound_k(s, cnt, x);
+                // the run of samples equal to x: precomputed, or by binary search
+                const int32_t first_eq = run_lo ? (int32_t)run_lo[m] : (int32_t)lower_bound_k(s, cnt, x);
+                const int32_t past_eq = run_hi ? (int32_t)run_hi[m] : (int32_t)upper_bound_k(s, cnt, x);
                 bl = max(a, first_eq) - 1;
                 ar = min(b + 1, past_eq);
             } else {
@@ -549,6 +612,8 @@ struct SampleSmem {
     KT samp[kSampleMax];
     KT lvl[kVMax + 1];
     int32_t ra[kVMax + 1], rb[kVMax + 1];
+    uint16_t run_lo[kSampleMax], run_hi[kSampleMax];  // equal_runs of samp
+    uint32_t wtmp[64];
 };
 
 // Radix or tree for a segment (App. A.2: "inspect the sample" and switch
@@ -616,7 +681,7 @@ template <> __device__ __forceinline__ Key16 key_at<Key16>(const uint8_t* chars,
 // the records exist: the sample keys come from the strings themselves.  The
 // round body's own launch in that round returns at once.
 template <class KT>
-__global__ void __launch_bounds__(1024) k_sample(Work w, Params p, int from_strings) {
+__global__ void __launch_bounds__(1024, 2) k_sample(Work w, Params p, int from_strings) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SampleSmem<KT>& sm = *reinterpret_cast<SampleSmem<KT>*>(smem_raw);
     __shared__ uint32_t s_item;
@@ -645,7 +710,8 @@ __global__ void __launch_bounds__(1024) k_sample(Work w, Params p, int from_stri
             }
         }
         bitonic_sort_regs(sm.samp, x[0], x[1], pw);
-        select_splitters(sm.samp, cnt, k, sm.lvl, sm.ra, sm.rb, &s_depth);
+        equal_runs<2>(sm.samp, cnt, sm.run_lo, sm.run_hi, sm.wtmp);
+        select_splitters(sm.samp, cnt, k, sm.lvl, sm.ra, sm.rb, &s_depth, sm.run_lo, sm.run_hi);
         const int kt = max(1, s_depth);
         if (threadIdx.x == 0 && kt != k) w.plans[seg].k = (uint32_t)kt;
         emit_tree(sm.lvl, kt, tree_lvl + P.tree_base, tree_ino + P.tree_base);
@@ -653,18 +719,24 @@ __global__ void __launch_bounds__(1024) k_sample(Work w, Params p, int from_stri
     }
 }
 
-// Stand-alone splitter construction for a caller's sample (sss_build_splitters).
+// Stand-alone splitter construction for a caller's sample (sss_build_splitters),
+// by the same steps as k_sample: register bitonic sort, runs of equal keys,
+// splitter choice.
 __global__ void __launch_bounds__(1024) k_build_splitters(const uint64_t* sample, uint32_t count, int k,
                                                           uint64_t* out_lvl, uint64_t* out_ino) {
     __shared__ uint64_t samp[kSampleMax];
     __shared__ uint64_t lvl[kVMax + 1];
     __shared__ int32_t ra[kVMax + 1], rb[kVMax + 1];
-    uint32_t pw = 1;
+    __shared__ uint16_t run_lo[kSampleMax], run_hi[kSampleMax];
+    __shared__ uint32_t wtmp[64];
+    uint32_t pw = 2;
     while (pw < count) pw <<= 1;
-    for (uint32_t j = threadIdx.x; j < pw; j += blockDim.x) samp[j] = j < count ? sample[j] : ~0ull;
-    __syncthreads();
-    bitonic_sort(samp, pw);
-    select_splitters(samp, count, k, lvl, ra, rb);
+    const uint32_t i0 = 2u * threadIdx.x;
+    const uint64_t x0 = i0 < count ? sample[i0] : ~0ull;
+    const uint64_t x1 = i0 + 1u < count ? sample[i0 + 1u] : ~0ull;
+    bitonic_sort_regs(samp, x0, x1, pw);
+    equal_runs<2>(samp, count, run_lo, run_hi, wtmp);
+    select_splitters(samp, count, k, lvl, ra, rb, nullptr, run_lo, run_hi);
     emit_tree(lvl, k, out_lvl, out_ino);
 }
 
@@ -1128,6 +1200,7 @@ struct MedSmem {
             KT samp[1 << (kMedKMax + 1)];
             KT lvl[1 << kMedKMax];
             int32_t ra[1 << kMedKMax], rb[1 << kMedKMax];
+            uint16_t run_lo[1 << (kMedKMax + 1)], run_hi[1 << (kMedKMax + 1)];  // equal_runs of samp
         } sel;
         struct {  // classification and move
             uint16_t bid[kMedMax];
@@ -1174,7 +1247,10 @@ __global__ void __launch_bounds__(kScatterThreads, SSS_MED_MIN_BLOCKS) k_med_rou
             if (threadIdx.x == 0) sm.full = kNoRefill;
             __syncthreads();
             bitonic_sort(sm.sel.samp, pw);
-            select_splitters(sm.sel.samp, cnt, kp, sm.sel.lvl, sm.sel.ra, sm.sel.rb, &s_depth);
+            equal_runs<(1 << (kMedKMax + 1)) / kScatterThreads>(sm.sel.samp, cnt, sm.sel.run_lo, sm.sel.run_hi,
+                                                                sm.wsum);
+            select_splitters(sm.sel.samp, cnt, kp, sm.sel.lvl, sm.sel.ra, sm.sel.rb, &s_depth, sm.sel.run_lo,
+                             sm.sel.run_hi);
             k = max(1, s_depth);
             nb = (2u << k) - 1u;
             emit_tree_smem(sm.sel.lvl, k, sm.t, sm.ino);
