@@ -438,26 +438,6 @@ __device__ void bitonic_sort_regs(KT* s, KT x0, KT x1, uint32_t pw) {
     __syncthreads();
 }
 
-template <class KT>
-__device__ __forceinline__ uint32_t lower_bound_k(const KT* s, uint32_t n, const KT& x) {
-    uint32_t lo = 0, hi = n;
-    while (lo < hi) {
-        uint32_t m = (lo + hi) >> 1;
-        if (klt(s[m], x)) lo = m + 1; else hi = m;
-    }
-    return lo;
-}
-
-template <class KT>
-__device__ __forceinline__ uint32_t upper_bound_k(const KT* s, uint32_t n, const KT& x) {
-    uint32_t lo = 0, hi = n;
-    while (lo < hi) {
-        uint32_t m = (lo + hi) >> 1;
-        if (!kgt(s[m], x)) lo = m + 1; else hi = m;
-    }
-    return lo;
-}
-
 // Runs of equal keys in the sorted sample s[0..cnt): lo[i] is the first
 // index of the run holding s[i] and hi[i] one past its last, i.e. the lower
 // and upper bound of s[i] in s.  Thread t takes indices PER t .. PER t +
@@ -526,13 +506,11 @@ __device__ void equal_runs(const KT* s, uint32_t cnt, uint16_t* lo, uint16_t* hi
 // non-empty range.  Below them every node repeats its parent's splitter, so
 // the tree cut to those levels has the same non-empty buckets (the paper's
 // "inspect the sample" adaptivity, App. A.2: samples with many equal keys
-// get smaller trees).  run_lo/run_hi (optional): for every index i of s, the
-// first index of the run of keys equal to s[i] and one past its last (see
-// equal_runs); without them each node finds its run by binary search.
+// get smaller trees).  run_lo/run_hi: for every index i of s, the first
+// index of the run of keys equal to s[i] and one past its last (equal_runs).
 template <class KT>
 __device__ void select_splitters(const KT* s, uint32_t cnt, int k, KT* lvl, int32_t* ra, int32_t* rb,
-                                 int* depth_used = nullptr, const uint16_t* run_lo = nullptr,
-                                 const uint16_t* run_hi = nullptr) {
+                                 const uint16_t* run_lo, const uint16_t* run_hi, int* depth_used = nullptr) {
     const uint32_t v = (1u << k) - 1u;
     if (threadIdx.x == 0) {
         ra[1] = 0;
@@ -550,9 +528,8 @@ __device__ void select_splitters(const KT* s, uint32_t cnt, int k, KT* lvl, int3
                 if (depth_used) atomicMax(depth_used, l + 1);
                 int32_t m = a + (b - a) / 2;
                 x = s[m];
-                // the run of samples equal to x: precomputed, or by binary search
-                const int32_t first_eq = run_lo ? (int32_t)run_lo[m] : (int32_t)lower_bound_k(s, cnt, x);
-                const int32_t past_eq = run_hi ? (int32_t)run_hi[m] : (int32_t)upper_bound_k(s, cnt, x);
+                const int32_t first_eq = (int32_t)run_lo[m];  // the run of samples equal to x
+                const int32_t past_eq = (int32_t)run_hi[m];
                 bl = max(a, first_eq) - 1;
                 ar = min(b + 1, past_eq);
             } else {
@@ -711,7 +688,7 @@ __global__ void __launch_bounds__(1024, 2) k_sample(Work w, Params p, int from_s
         }
         bitonic_sort_regs(sm.samp, x[0], x[1], pw);
         equal_runs<2>(sm.samp, cnt, sm.run_lo, sm.run_hi, sm.wtmp);
-        select_splitters(sm.samp, cnt, k, sm.lvl, sm.ra, sm.rb, &s_depth, sm.run_lo, sm.run_hi);
+        select_splitters(sm.samp, cnt, k, sm.lvl, sm.ra, sm.rb, sm.run_lo, sm.run_hi, &s_depth);
         const int kt = max(1, s_depth);
         if (threadIdx.x == 0 && kt != k) w.plans[seg].k = (uint32_t)kt;
         emit_tree(sm.lvl, kt, tree_lvl + P.tree_base, tree_ino + P.tree_base);
@@ -736,7 +713,7 @@ __global__ void __launch_bounds__(1024) k_build_splitters(const uint64_t* sample
     const uint64_t x1 = i0 + 1u < count ? sample[i0 + 1u] : ~0ull;
     bitonic_sort_regs(samp, x0, x1, pw);
     equal_runs<2>(samp, count, run_lo, run_hi, wtmp);
-    select_splitters(samp, count, k, lvl, ra, rb, nullptr, run_lo, run_hi);
+    select_splitters(samp, count, k, lvl, ra, rb, run_lo, run_hi);
     emit_tree(lvl, k, out_lvl, out_ino);
 }
 
@@ -1249,8 +1226,8 @@ __global__ void __launch_bounds__(kScatterThreads, SSS_MED_MIN_BLOCKS) k_med_rou
             bitonic_sort(sm.sel.samp, pw);
             equal_runs<(1 << (kMedKMax + 1)) / kScatterThreads>(sm.sel.samp, cnt, sm.sel.run_lo, sm.sel.run_hi,
                                                                 sm.wsum);
-            select_splitters(sm.sel.samp, cnt, kp, sm.sel.lvl, sm.sel.ra, sm.sel.rb, &s_depth, sm.sel.run_lo,
-                             sm.sel.run_hi);
+            select_splitters(sm.sel.samp, cnt, kp, sm.sel.lvl, sm.sel.ra, sm.sel.rb, sm.sel.run_lo, sm.sel.run_hi,
+                             &s_depth);
             k = max(1, s_depth);
             nb = (2u << k) - 1u;
             emit_tree_smem(sm.sel.lvl, k, sm.t, sm.ino);

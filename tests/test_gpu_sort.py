@@ -99,6 +99,16 @@ def test_build_splitters_matches_oracle(k):
         ref_level, ref_ino = oracle.select_splitters(np.sort(sample), k)
         assert np.array_equal(level.cpu().numpy().view(np.uint64), ref_level)
         assert np.array_equal(ino.cpu().numpy().view(np.uint64), ref_ino)
+    # keys equal to the all-ones padding of the sorted sample: their run of
+    # equal keys must end at the sample's end, not run on into the padding
+    for count in (full, max(1, full - 2)):
+        sample = rng.choice(np.array([0, 7, 2 ** 64 - 1], dtype=np.uint64), size=count)
+        level = torch.zeros(2 ** k - 1, dtype=torch.int64, device="cuda")
+        ino = torch.zeros(2 ** k - 1, dtype=torch.int64, device="cuda")
+        sss.sss_build_splitters(torch.from_numpy(sample.view(np.int64)).cuda(), count, k, level, ino)
+        ref_level, ref_ino = oracle.select_splitters(np.sort(sample), k)
+        assert np.array_equal(level.cpu().numpy().view(np.uint64), ref_level)
+        assert np.array_equal(ino.cpu().numpy().view(np.uint64), ref_ino)
 
 
 def _classify_gpu(keys, level, ino, k):
