@@ -725,7 +725,7 @@ cudaError_t launch_small(const Work& w, const Params& p, const Hdr* hc, uint32_t
 cudaError_t launch_fixup(const Work& w, Prof* pf, cudaStream_t st);
 cudaError_t launch_localize(uint32_t* perm, const Seg* roots, uint32_t num_roots, Prof* pf, cudaStream_t st);
 cudaError_t launch_scan_u32(const uint32_t* in, uint32_t* out, const uint32_t* n_ptr, const uint32_t* n_host,
-                            uint32_t* tmp, Prof* pf, cudaStream_t st);
+                            uint32_t* tmp, uint32_t* done, Prof* pf, cudaStream_t st);
 size_t scan_tmp_elems(uint32_t n);
 uint32_t device_sms();
 

@@ -272,6 +272,9 @@ __global__ void k_hdr_reset(Work w) {
     h->q_sample = 0; h->q_fit = 0; h->q_classify = 0; h->q_scatter = 0;
     h->q_med = 0; h->q_base = 0; h->q_bigrun = 0;
     for (int i = 0; i < 8; i++) h->small_hist[i] = 0;
+    // the scans' completion counters (the last entry of their scratch)
+    w.scan_tmp[w.scan_tmp_max - 1u] = 0u;
+    w.scan_tmp2[w.scan_tmp_max - 1u] = 0u;
 }
 
 // Roots: one segment per set (a single sort is one set) at depth 0.
@@ -1653,7 +1656,7 @@ __global__ void k_fixup(Work w) {
     }
 }
 
-// ------------------------------------------------------------ scan (3 phase)
+// ------------------------------------------------------------ scan (tile sums, down-sweep)
 
 constexpr int kScanThreads = 256;
 constexpr int kScanPer = 16;
@@ -1669,8 +1672,13 @@ struct ScanIn {
     __device__ __forceinline__ const uint32_t* get() const { return sel ? in[*sel & 1u] : in[0]; }
 };
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(ScanIn src, const uint32_t* n_ptr, uint32_t* sums) {
+// Tile sums of the input; the CTA that finishes last (a counter in device
+// memory, no waiting) scans them in place, writes the total to out[n] and
+// resets the counter.
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(ScanIn src, const uint32_t* n_ptr, uint32_t* sums,
+                                                              uint32_t* out, uint32_t* done) {
     __shared__ uint32_t wsum[33];
+    __shared__ uint32_t s_last;
     const uint32_t n = *n_ptr;
     const uint32_t* in = src.get();
     const uint32_t tiles = (n + kScanTile - 1) / kScanTile;
@@ -1686,59 +1694,83 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(ScanIn src, const 
         block_excl_sum(s, wsum, &tot);
         if (threadIdx.x == 0) sums[tile] = tot;
     }
-}
-
-__global__ void __launch_bounds__(1024) k_scan_tiles(uint32_t* sums, const uint32_t* n_ptr, uint32_t* out) {
-    __shared__ uint32_t wsum[33];
-    const uint32_t n = *n_ptr;
-    const uint32_t ntiles = (n + kScanTile - 1) / kScanTile;
-    const uint32_t per = (ntiles + blockDim.x - 1) / blockDim.x;
-    const uint32_t lo = min(ntiles, threadIdx.x * per), hi = min(ntiles, lo + per);
+    if (threadIdx.x == 0) {
+        __threadfence();  // this CTA's tile sums before its count
+        s_last = atomicAdd(done, 1u) == gridDim.x - 1u ? 1u : 0u;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const uint32_t per = (tiles + blockDim.x - 1) / blockDim.x;
+    const uint32_t lo = min(tiles, threadIdx.x * per), hi = min(tiles, lo + per);
     uint32_t s = 0;
-    for (uint32_t i = lo; i < hi; i++) s += sums[i];
+    for (uint32_t i = lo; i < hi; i++) s += __ldcg(sums + i);
     uint32_t tot;
     uint32_t ex = block_excl_sum(s, wsum, &tot);
     for (uint32_t i = lo; i < hi; i++) {
-        const uint32_t x = sums[i];
+        const uint32_t x = __ldcg(sums + i);
         sums[i] = ex;
         ex += x;
     }
-    if (threadIdx.x == 0) out[n] = tot;
+    if (threadIdx.x == 0) {
+        out[n] = tot;
+        *done = 0u;
+    }
 }
 
+// Down-sweep: each tile of kScanTile entries goes through shared memory
+// (padded, entry i at i + i / 32, so that neither the coalesced copies nor
+// the threads' runs of kScanPer consecutive entries conflict on banks), so
+// that both its loads and its stores are whole coalesced lines.
 __global__ void __launch_bounds__(kScanThreads) k_scan_down(ScanIn src, uint32_t* out, const uint32_t* n_ptr,
                                                             const uint32_t* sums) {
     __shared__ uint32_t wsum[33];
+    __shared__ uint32_t tb[kScanTile + kScanTile / 32];
     const uint32_t n = *n_ptr;
     const uint32_t* in = src.get();
     const uint32_t tiles = (n + kScanTile - 1) / kScanTile;
     for (uint32_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-        const uint32_t base = tile * kScanTile + threadIdx.x * kScanPer;
+        const uint32_t t0 = tile * kScanTile;
+#pragma unroll
+        for (int j = 0; j < kScanPer; j++) {
+            const uint32_t i = j * kScanThreads + threadIdx.x;
+            tb[i + (i >> 5)] = t0 + i < n ? in[t0 + i] : 0u;
+        }
+        __syncthreads();
+        const uint32_t b = threadIdx.x * kScanPer;
         uint32_t v[kScanPer];
         uint32_t s = 0;
 #pragma unroll
         for (int j = 0; j < kScanPer; j++) {
-            const uint32_t i = base + j;
-            v[j] = i < n ? in[i] : 0u;
+            const uint32_t i = b + j;
+            v[j] = tb[i + (i >> 5)];
             s += v[j];
         }
+        // (block_excl_sum's barriers also end every read of tb above)
         uint32_t ex = block_excl_sum(s, wsum, nullptr) + sums[tile];
 #pragma unroll
         for (int j = 0; j < kScanPer; j++) {
-            const uint32_t i = base + j;
-            if (i < n) out[i] = ex;
+            const uint32_t i = b + j;
+            tb[i + (i >> 5)] = ex;
             ex += v[j];
         }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kScanPer; j++) {
+            const uint32_t i = j * kScanThreads + threadIdx.x;
+            if (t0 + i < n) out[t0 + i] = tb[i + (i >> 5)];
+        }
+        __syncthreads();
     }
 }
 
 // out[0..n) = exclusive prefix sums of the input, out[n] = total, with n read
 // from device memory (*n_ptr); n_host (if known) only sizes the grid.  tmp
-// holds scan_tmp_elems(n) entries.  The input is in, or with sel given
-// in_alt when *sel is odd.
+// holds scan_tmp_elems(n) entries; done is a counter that is zero between
+// scans.  The input is in, or with sel given in_alt when *sel is odd.
 static cudaError_t launch_scan_sel(const uint32_t* in, const uint32_t* in_alt, const uint32_t* sel, uint32_t* out,
-                                   const uint32_t* n_ptr, const uint32_t* n_host, uint32_t* tmp, Prof* pf,
-                                   cudaStream_t st) {
+                                   const uint32_t* n_ptr, const uint32_t* n_host, uint32_t* tmp, uint32_t* done,
+                                   Prof* pf, cudaStream_t st) {
     const ScanIn src{{in, in_alt}, sel};
     uint32_t grid = device_sms() * 8u;
     if (n_host) {
@@ -1746,16 +1778,15 @@ static cudaError_t launch_scan_sel(const uint32_t* in, const uint32_t* in_alt, c
         grid = max(1u, min(grid, tiles));
     }
     ProfScope ps(pf, kScan, st);
-    k_scan_reduce<<<grid, kScanThreads, 0, st>>>(src, n_ptr, tmp);
-    k_scan_tiles<<<1, 1024, 0, st>>>(tmp, n_ptr, out);
+    k_scan_reduce<<<grid, kScanThreads, 0, st>>>(src, n_ptr, tmp, out, done);
     k_scan_down<<<grid, kScanThreads, 0, st>>>(src, out, n_ptr, tmp);
-    if (pf) { pf->launches += 2; pf->cls_launches[kScan] += 2; }
+    if (pf) { pf->launches += 1; pf->cls_launches[kScan] += 1; }
     return cudaGetLastError();
 }
 
 cudaError_t launch_scan_u32(const uint32_t* in, uint32_t* out, const uint32_t* n_ptr, const uint32_t* n_host,
-                            uint32_t* tmp, Prof* pf, cudaStream_t st) {
-    return launch_scan_sel(in, in, nullptr, out, n_ptr, n_host, tmp, pf, st);
+                            uint32_t* tmp, uint32_t* done, Prof* pf, cudaStream_t st) {
+    return launch_scan_sel(in, in, nullptr, out, n_ptr, n_host, tmp, done, pf, st);
 }
 
 // ------------------------------------------------------------ launches
@@ -1854,7 +1885,7 @@ static cudaError_t launch_round_t(const Work& w, const Params& p, const Hdr* hc,
             k_classify<KT><<<gc, kClassifyThreads, 0, st>>>(w, p);
         }
         cudaError_t e = launch_scan_u32(w.counts, w.counts_scan, &w.hdr->total_counts, hc ? &hc->total_counts : nullptr,
-                                        w.scan_tmp, pf, st);
+                                        w.scan_tmp, w.scan_tmp + (w.scan_tmp_max - 1u), pf, st);
         if (e != cudaSuccess) return e;
         {
             ProfScope ps(pf, kScatter, st);
@@ -2017,7 +2048,8 @@ static cudaError_t launch_tiles(const Work& w, const Params& p, const Hdr* hc, u
     uint32_t tiles = hc ? (hc->small_elems_snap + p.base_threshold - 1) / p.base_threshold : 0u;
     if (!hc || hc->n_small_snap) {
         cudaError_t e = launch_scan_sel(w.small_size[0], w.small_size[1], &w.hdr->round, w.small_off,
-                                        &w.hdr->n_small_snap, hc ? &hc->n_small_snap : nullptr, w.scan_tmp2, pf, st);
+                                        &w.hdr->n_small_snap, hc ? &hc->n_small_snap : nullptr, w.scan_tmp2,
+                                        w.scan_tmp2 + (w.scan_tmp_max - 1u), pf, st);
         if (e != cudaSuccess) return e;
         {
             ProfScope ps(pf, kBase, st);

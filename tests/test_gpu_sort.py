@@ -415,7 +415,7 @@ def test_profiled_timeline():
     assert all(c in sss.K_CLASSES and 0.0 <= a <= b for c, a, b in tl)
     # every kernel class with timed launches appears in the timeline as often
     for i, c in enumerate(sss.K_CLASSES):
-        if c != "scan":  # one timed entry covers the scan's three kernels
+        if c != "scan":  # one timed entry covers the scan's two kernels
             assert sum(1 for x in tl if x[0] == c) == st.prof_launches[i], c
 
 
