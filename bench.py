@@ -209,6 +209,33 @@ def ncu_traffic(kernel: str, workload: str):
         return None
 
 
+def host_link(torch, stream, dev, h_chars, h_perm, chars, perm, e2e, sort_ms):
+    """The host link's copy rates (the step's own pinned buffers, copy engine
+    on the bench stream, best of 3) and the end-to-end time they leave: the
+    step's uploads and downloads at those rates plus the device-timed sort.
+    The entry point uploads before it sorts (the root sample needs every
+    string), so that sum is the floor of its end-to-end time."""
+    def best(dst, src):
+        ts = []
+        for _ in range(3):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            with torch.cuda.stream(stream):
+                dst.copy_(src, non_blocking=True)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            ts.append(a.elapsed_time(b))
+        return min(ts)
+    up = best(chars, h_chars)
+    down = best(h_perm, perm)
+    h2d_gbs = h_chars.numel() / up / 1e6
+    d2h_gbs = 4 * h_perm.numel() / down / 1e6
+    copy_ms = e2e["h2d_bytes_per_step"] / h2d_gbs / 1e6 + e2e["d2h_bytes_per_step"] / d2h_gbs / 1e6
+    return {"h2d_gbs": h2d_gbs, "d2h_gbs": d2h_gbs, "copy_ms": copy_ms, "floor_ms": copy_ms + sort_ms,
+            "note": "copies at the measured link rates plus the device-timed sort"}
+
+
 # ------------------------------------------------------------------ reference arm
 
 def run_reference(args, rank):
@@ -689,6 +716,7 @@ def main():
         te = reduce_max((time.perf_counter() - t0) / args.e2e_steps, dist, dev)
         e2e = {"value": n * world / te, "unit": "strings/s", "h2d_bytes_per_step": int(len(s.chars) + 8 * n),
                "d2h_bytes_per_step": int(8 * n), "ms_per_step": te * 1e3}
+        e2e["link"] = host_link(torch, stream, dev, h_chars, h_perm, chars, perm, e2e, ms)
 
     legs = set(x for x in args.legs.split(",") if x and x != "none")
     extra = {}
