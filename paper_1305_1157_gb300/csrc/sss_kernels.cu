@@ -116,72 +116,119 @@ __device__ __forceinline__ void warp_add(uint32_t* counter, uint32_t x) {
     if ((threadIdx.x & 31u) == 0 && x) atomicAdd(counter, x);
 }
 
-// Appends the child segment of each lane that has one (valid) to the list of
-// its size class.  Called by all 32 lanes of a warp together; each list and
-// counter takes one atomic per warp.
-__device__ __forceinline__ void append_children(const Work& w, const Params& p, int out, bool valid, uint32_t start,
-                                                uint32_t size, uint32_t cdepth, bool isrun, uint32_t runlcp) {
+// Appends the child segments of a warp's lanes, PER buckets a lane (kind[q]
+// from child_kind, kChildNone for none), to the lists of their size
+// classes.  Called by all 32 lanes of a warp together; each list and
+// counter takes one atomic per warp for all PER buckets of its lanes.
+template <int PER>
+__device__ __forceinline__ void append_children_n(const Work& w, int out, const uint32_t (&kind)[PER],
+                                                  const uint32_t (&start)[PER], const uint32_t (&size)[PER],
+                                                  const uint32_t (&cdepth)[PER], const uint32_t (&runlcp)[PER]) {
     Hdr* h = w.hdr;
-    const uint32_t kind = valid ? child_kind(p, size, isrun) : kChildNone;
-    if (!__any_sync(FULL_MASK, kind != kChildNone)) return;
+    uint32_t n_runs = 0, n_tiny = 0, n_small = 0, n_med = 0, n_large = 0;
+#pragma unroll
+    for (int q = 0; q < PER; q++) {
+        n_runs += kind[q] == kChildRuns ? (size[q] + kRunPiece - 1u) / kRunPiece : 0u;
+        n_tiny += kind[q] == kChildTiny ? 1u : 0u;
+        n_small += kind[q] == kChildSmall ? 1u : 0u;
+        n_med += kind[q] == kChildMed ? 1u : 0u;
+        n_large += kind[q] == kChildLarge ? 1u : 0u;
+    }
+    if (!__any_sync(FULL_MASK, n_runs + n_tiny + n_small + n_med + n_large > 0u)) return;
     {   // large runs of equal strings: pieces of at most kRunPiece strings,
         // so one large run spreads over many CTAs; depth holds the run's
         // first position
-        const uint32_t np = kind == kChildRuns ? (size + kRunPiece - 1u) / kRunPiece : 0u;
-        const uint32_t s0 = warp_reserve(&h->n_bigrun, kind == kChildRuns, np);
-        if (kind == kChildRuns) {
+        uint32_t s0 = warp_reserve(&h->n_bigrun, n_runs > 0u, n_runs);
+#pragma unroll
+        for (int q = 0; q < PER; q++) {
+            if (kind[q] != kChildRuns) continue;
+            const uint32_t np = (size[q] + kRunPiece - 1u) / kRunPiece;
             if (s0 + np <= w.bmax) {
                 for (uint32_t j = 0; j < np; j++)
-                    w.bigrun[out][s0 + j] = Seg{start + j * kRunPiece, min(kRunPiece, size - j * kRunPiece), start, runlcp};
+                    w.bigrun[out][s0 + j] = Seg{start[q] + j * kRunPiece, min(kRunPiece, size[q] - j * kRunPiece),
+                                                start[q], runlcp[q]};
             } else {
                 atomicOr(&h->err, kErrRunOverflow);
             }
+            s0 += np;
         }
     }
     {
-        const uint32_t s0 = warp_reserve(&h->n_tiny, kind == kChildTiny, 1u);
-        if (kind == kChildTiny) {
-            if (s0 < w.ymax) w.tiny[out][s0] = Seg{start, size, cdepth, 0u};
-            else atomicOr(&h->err, kErrSmallOverflow);
-        }
-        warp_add(&h->tiny_elems, kind == kChildTiny && s0 < w.ymax ? size : 0u);
-    }
-    {
-        const uint32_t s0 = warp_reserve(&h->n_small, kind == kChildSmall, 1u);
-        if (kind == kChildSmall) {
-            if (s0 < w.smax) {
-                w.small[out][s0] = Seg{start, size, cdepth, 0u};
-                w.small_size[out][s0] = size;
+        uint32_t s0 = warp_reserve(&h->n_tiny, n_tiny > 0u, n_tiny), elems = 0;
+#pragma unroll
+        for (int q = 0; q < PER; q++) {
+            if (kind[q] != kChildTiny) continue;
+            if (s0 < w.ymax) {
+                w.tiny[out][s0] = Seg{start[q], size[q], cdepth[q], 0u};
+                elems += size[q];
             } else {
                 atomicOr(&h->err, kErrSmallOverflow);
             }
+            s0++;
         }
-        warp_add(&h->small_elems, kind == kChildSmall && s0 < w.smax ? size : 0u);
+        warp_add(&h->tiny_elems, elems);
+    }
+    {
+        uint32_t s0 = warp_reserve(&h->n_small, n_small > 0u, n_small), elems = 0;
+#pragma unroll
+        for (int q = 0; q < PER; q++) {
+            if (kind[q] != kChildSmall) continue;
+            if (s0 < w.smax) {
+                w.small[out][s0] = Seg{start[q], size[q], cdepth[q], 0u};
+                w.small_size[out][s0] = size[q];
+                elems += size[q];
+            } else {
+                atomicOr(&h->err, kErrSmallOverflow);
+            }
+            s0++;
+        }
+        warp_add(&h->small_elems, elems);
     }
     {   // base-case buckets by floor(log2(size))
-        const bool base = kind == kChildTiny || kind == kChildSmall;
-        const uint32_t bin = base ? min(31 - __clz(size), 7) : 8u;
 #pragma unroll
         for (uint32_t b = 1; b < 8; b++) {
-            const uint32_t m = __ballot_sync(FULL_MASK, bin == b);
-            if ((threadIdx.x & 31u) == 0 && m) atomicAdd(&h->small_hist[b], (uint32_t)__popc(m));
+            uint32_t c = 0;
+#pragma unroll
+            for (int q = 0; q < PER; q++)
+                c += ((kind[q] == kChildTiny || kind[q] == kChildSmall) && min(31 - __clz(size[q]), 7) == (int)b)
+                         ? 1u : 0u;
+            c = __reduce_add_sync(FULL_MASK, c);
+            if ((threadIdx.x & 31u) == 0 && c) atomicAdd(&h->small_hist[b], c);
         }
     }
     {
-        const uint32_t s0 = warp_reserve(&h->n_med, kind == kChildMed, 1u);
-        if (kind == kChildMed) {
-            if (s0 < w.mmax) w.med[out][s0] = Seg{start, size, cdepth, 0u};
-            else atomicOr(&h->err, kErrMedOverflow);
+        uint32_t s0 = warp_reserve(&h->n_med, n_med > 0u, n_med), elems = 0;
+#pragma unroll
+        for (int q = 0; q < PER; q++) {
+            if (kind[q] != kChildMed) continue;
+            if (s0 < w.mmax) {
+                w.med[out][s0] = Seg{start[q], size[q], cdepth[q], 0u};
+                elems += size[q];
+            } else {
+                atomicOr(&h->err, kErrMedOverflow);
+            }
+            s0++;
         }
-        warp_add(&h->med_elems, kind == kChildMed && s0 < w.mmax ? size : 0u);
+        warp_add(&h->med_elems, elems);
     }
     {
-        const uint32_t s0 = warp_reserve(&h->n_large, kind == kChildLarge, 1u);
-        if (kind == kChildLarge) {
-            if (s0 < w.lmax) w.large[s0] = Seg{start, size, cdepth, 0u};
+        uint32_t s0 = warp_reserve(&h->n_large, n_large > 0u, n_large);
+#pragma unroll
+        for (int q = 0; q < PER; q++) {
+            if (kind[q] != kChildLarge) continue;
+            if (s0 < w.lmax) w.large[s0] = Seg{start[q], size[q], cdepth[q], 0u};
             else atomicOr(&h->err, kErrLargeOverflow);
+            s0++;
         }
     }
+}
+
+// One bucket a lane (valid: the lane has one).
+__device__ __forceinline__ void append_children(const Work& w, const Params& p, int out, bool valid, uint32_t start,
+                                                uint32_t size, uint32_t cdepth, bool isrun, uint32_t runlcp) {
+    const uint32_t kind[1] = {valid ? child_kind(p, size, isrun) : kChildNone};
+    const uint32_t st[1] = {start}, sz[1] = {size}, cd[1] = {cdepth}, rl[1] = {runlcp};
+    append_children_n<1>(w, out, kind, st, sz, cd, rl);
 }
 
 // Child depth of bucket b of a segment at depth `depth` (Eq. (1), Sec. 3.1):
@@ -1137,6 +1184,9 @@ __global__ void __launch_bounds__(kScatterThreads, SSS_SCATTER_MIN_BLOCKS) k_sca
             s_mine[q] = b < nb ? S[b * P.chunks + ci] : 0u;
             s_next[q] = b + 1 < nb ? S[(b + 1) * P.chunks] : 0u;
         }
+        // child segments of this thread's buckets (chunk 0 appends them):
+        // start and size replace s_first and s_next in place
+        uint32_t ckind[kBPT], cdep[kBPT], crun[kBPT];
 #pragma unroll
         for (int q = 0; q < kBPT; q++) {
             const uint32_t b = threadIdx.x + q * kScatterThreads;
@@ -1153,8 +1203,13 @@ __global__ void __launch_bounds__(kScatterThreads, SSS_SCATTER_MIN_BLOCKS) k_sca
                 sm.ss.rdep[b] = refill_code(bi, size, P.depth);
                 if (ci == 0 && size > 0 && start > P.begin) w.out_lcp[start] = kLcpFlag | P.depth;
             }
-            if (ci == 0) append_children(w, p, med_out, b < nb && size > 0, start, size, bi.cdepth, bi.isrun, bi.runlcp);
+            s_first[q] = start;
+            s_next[q] = size;
+            ckind[q] = b < nb && size > 0 ? child_kind(p, size, bi.isrun) : kChildNone;
+            cdep[q] = bi.cdepth;
+            crun[q] = bi.runlcp;
         }
+        if (ci == 0) append_children_n<kBPT>(w, med_out, ckind, s_first, s_next, cdep, crun);
         __syncthreads();
         const uint32_t lo = P.begin + ci * P.chunk;
         const uint32_t hi = min(lo + P.chunk, seg_end);
@@ -1266,6 +1321,7 @@ __global__ void __launch_bounds__(kScatterThreads, SSS_MED_MIN_BLOCKS) k_med_rou
             sum += cnts[q];
         }
         uint32_t start = g.begin + block_excl_sum(sum, sm.wsum, nullptr);
+        uint32_t ckind[kPer], cstart[kPer], cdep[kPer], crun[kPer];
 #pragma unroll
         for (int q = 0; q < kPer; q++) {
             const uint32_t b = threadIdx.x * kPer + q;
@@ -1277,9 +1333,13 @@ __global__ void __launch_bounds__(kScatterThreads, SSS_MED_MIN_BLOCKS) k_med_rou
                 sm.mv.ss.rdep[b] = refill_code(bi, size, g.depth);
                 if (size > 0 && start > g.begin) w.out_lcp[start] = kLcpFlag | g.depth;
             }
-            append_children(w, p, med_out, b < nb && size > 0, start, size, bi.cdepth, bi.isrun, bi.runlcp);
+            ckind[q] = b < nb && size > 0 ? child_kind(p, size, bi.isrun) : kChildNone;
+            cstart[q] = start;
+            cdep[q] = bi.cdepth;
+            crun[q] = bi.runlcp;
             start += cnts[q];
         }
+        append_children_n<kPer>(w, med_out, ckind, cstart, cnts, cdep, crun);
         __syncthreads();
         const uint32_t nref =
             scatter_range<kMedNB, true, KT, kMedItems>(w, cur, g.begin, g.begin + m, nb, sm.mv.ss, sm.t.view(), sm.ino, k,
