@@ -89,37 +89,30 @@ __device__ __forceinline__ uint32_t child_kind(const Params& p, uint32_t size, b
     return kChildLarge;
 }
 
-// First of `cnt` consecutive list slots for each lane whose `mine` is set:
-// one atomic add per warp (the lanes' list appends would otherwise hit the
-// same few counters once per bucket).  Called by all lanes of the warp.
-__device__ __forceinline__ uint32_t warp_reserve(uint32_t* counter, bool mine, uint32_t cnt) {
-    const uint32_t lane = threadIdx.x & 31u;
-    const uint32_t m = __ballot_sync(FULL_MASK, mine);
-    if (!m) return 0u;
-    uint32_t c = mine ? cnt : 0u;
-    // exclusive prefix of the lanes' counts
-    uint32_t inc = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(FULL_MASK, inc, o);
-        if (lane >= (uint32_t)o) inc += y;
-    }
-    const uint32_t total = __shfl_sync(FULL_MASK, inc, 31);
-    uint32_t base = 0;
-    if (lane == 31) base = atomicAdd(counter, total);
-    base = __shfl_sync(FULL_MASK, base, 31);
-    return base + inc - c;
-}
-
 __device__ __forceinline__ void warp_add(uint32_t* counter, uint32_t x) {
     x = __reduce_add_sync(FULL_MASK, x);
     if ((threadIdx.x & 31u) == 0 && x) atomicAdd(counter, x);
 }
 
+// Exclusive prefix over the lanes of x; *total receives the warp's sum.
+__device__ __forceinline__ uint32_t warp_excl(uint32_t x, uint32_t* total) {
+    const uint32_t lane = threadIdx.x & 31u;
+    uint32_t inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL_MASK, inc, o);
+        if (lane >= (uint32_t)o) inc += y;
+    }
+    *total = __shfl_sync(FULL_MASK, inc, 31);
+    return inc - x;
+}
+
 // Appends the child segments of a warp's lanes, PER buckets a lane (kind[q]
 // from child_kind, kChildNone for none), to the lists of their size
-// classes.  Called by all 32 lanes of a warp together; each list and
-// counter takes one atomic per warp for all PER buckets of its lanes.
+// classes.  Called by all 32 lanes of a warp together.  Each list's slots
+// for all PER buckets of all lanes take one atomic per warp, and lane 31
+// issues the lists' atomics back to back before any of their results is
+// used, so the warp waits for one round trip, not one per list.
 template <int PER>
 __device__ __forceinline__ void append_children_n(const Work& w, int out, const uint32_t (&kind)[PER],
                                                   const uint32_t (&start)[PER], const uint32_t (&size)[PER],
@@ -135,91 +128,84 @@ __device__ __forceinline__ void append_children_n(const Work& w, int out, const 
         n_large += kind[q] == kChildLarge ? 1u : 0u;
     }
     if (!__any_sync(FULL_MASK, n_runs + n_tiny + n_small + n_med + n_large > 0u)) return;
-    {   // large runs of equal strings: pieces of at most kRunPiece strings,
-        // so one large run spreads over many CTAs; depth holds the run's
-        // first position
-        uint32_t s0 = warp_reserve(&h->n_bigrun, n_runs > 0u, n_runs);
+    const uint32_t lane = threadIdx.x & 31u;
+    uint32_t t_runs, t_tiny, t_small, t_med, t_large;
+    const uint32_t x_runs = warp_excl(n_runs, &t_runs), x_tiny = warp_excl(n_tiny, &t_tiny);
+    const uint32_t x_small = warp_excl(n_small, &t_small), x_med = warp_excl(n_med, &t_med);
+    const uint32_t x_large = warp_excl(n_large, &t_large);
+    uint32_t b_runs = 0, b_tiny = 0, b_small = 0, b_med = 0, b_large = 0;
+    if (lane == 31u) {
+        if (t_runs) b_runs = atomicAdd(&h->n_bigrun, t_runs);
+        if (t_tiny) b_tiny = atomicAdd(&h->n_tiny, t_tiny);
+        if (t_small) b_small = atomicAdd(&h->n_small, t_small);
+        if (t_med) b_med = atomicAdd(&h->n_med, t_med);
+        if (t_large) b_large = atomicAdd(&h->n_large, t_large);
+    }
+    uint32_t s_runs = __shfl_sync(FULL_MASK, b_runs, 31) + x_runs;
+    uint32_t s_tiny = __shfl_sync(FULL_MASK, b_tiny, 31) + x_tiny;
+    uint32_t s_small = __shfl_sync(FULL_MASK, b_small, 31) + x_small;
+    uint32_t s_med = __shfl_sync(FULL_MASK, b_med, 31) + x_med;
+    uint32_t s_large = __shfl_sync(FULL_MASK, b_large, 31) + x_large;
+    uint32_t e_tiny = 0, e_small = 0, e_med = 0;
+    uint32_t hist[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 #pragma unroll
-        for (int q = 0; q < PER; q++) {
-            if (kind[q] != kChildRuns) continue;
+    for (int q = 0; q < PER; q++) {
+        const uint32_t kq = kind[q];
+        if (kq == kChildRuns) {
+            // large runs of equal strings: pieces of at most kRunPiece
+            // strings, so one large run spreads over many CTAs; depth holds
+            // the run's first position
             const uint32_t np = (size[q] + kRunPiece - 1u) / kRunPiece;
-            if (s0 + np <= w.bmax) {
+            if (s_runs + np <= w.bmax) {
                 for (uint32_t j = 0; j < np; j++)
-                    w.bigrun[out][s0 + j] = Seg{start[q] + j * kRunPiece, min(kRunPiece, size[q] - j * kRunPiece),
-                                                start[q], runlcp[q]};
+                    w.bigrun[out][s_runs + j] = Seg{start[q] + j * kRunPiece,
+                                                    min(kRunPiece, size[q] - j * kRunPiece), start[q], runlcp[q]};
             } else {
                 atomicOr(&h->err, kErrRunOverflow);
             }
-            s0 += np;
-        }
-    }
-    {
-        uint32_t s0 = warp_reserve(&h->n_tiny, n_tiny > 0u, n_tiny), elems = 0;
-#pragma unroll
-        for (int q = 0; q < PER; q++) {
-            if (kind[q] != kChildTiny) continue;
-            if (s0 < w.ymax) {
-                w.tiny[out][s0] = Seg{start[q], size[q], cdepth[q], 0u};
-                elems += size[q];
+            s_runs += np;
+        } else if (kq == kChildTiny) {
+            if (s_tiny < w.ymax) {
+                w.tiny[out][s_tiny] = Seg{start[q], size[q], cdepth[q], 0u};
+                e_tiny += size[q];
             } else {
                 atomicOr(&h->err, kErrSmallOverflow);
             }
-            s0++;
-        }
-        warp_add(&h->tiny_elems, elems);
-    }
-    {
-        uint32_t s0 = warp_reserve(&h->n_small, n_small > 0u, n_small), elems = 0;
-#pragma unroll
-        for (int q = 0; q < PER; q++) {
-            if (kind[q] != kChildSmall) continue;
-            if (s0 < w.smax) {
-                w.small[out][s0] = Seg{start[q], size[q], cdepth[q], 0u};
-                w.small_size[out][s0] = size[q];
-                elems += size[q];
+            s_tiny++;
+        } else if (kq == kChildSmall) {
+            if (s_small < w.smax) {
+                w.small[out][s_small] = Seg{start[q], size[q], cdepth[q], 0u};
+                w.small_size[out][s_small] = size[q];
+                e_small += size[q];
             } else {
                 atomicOr(&h->err, kErrSmallOverflow);
             }
-            s0++;
-        }
-        warp_add(&h->small_elems, elems);
-    }
-    {   // base-case buckets by floor(log2(size))
-#pragma unroll
-        for (uint32_t b = 1; b < 8; b++) {
-            uint32_t c = 0;
-#pragma unroll
-            for (int q = 0; q < PER; q++)
-                c += ((kind[q] == kChildTiny || kind[q] == kChildSmall) && min(31 - __clz(size[q]), 7) == (int)b)
-                         ? 1u : 0u;
-            c = __reduce_add_sync(FULL_MASK, c);
-            if ((threadIdx.x & 31u) == 0 && c) atomicAdd(&h->small_hist[b], c);
-        }
-    }
-    {
-        uint32_t s0 = warp_reserve(&h->n_med, n_med > 0u, n_med), elems = 0;
-#pragma unroll
-        for (int q = 0; q < PER; q++) {
-            if (kind[q] != kChildMed) continue;
-            if (s0 < w.mmax) {
-                w.med[out][s0] = Seg{start[q], size[q], cdepth[q], 0u};
-                elems += size[q];
+            s_small++;
+        } else if (kq == kChildMed) {
+            if (s_med < w.mmax) {
+                w.med[out][s_med] = Seg{start[q], size[q], cdepth[q], 0u};
+                e_med += size[q];
             } else {
                 atomicOr(&h->err, kErrMedOverflow);
             }
-            s0++;
-        }
-        warp_add(&h->med_elems, elems);
-    }
-    {
-        uint32_t s0 = warp_reserve(&h->n_large, n_large > 0u, n_large);
-#pragma unroll
-        for (int q = 0; q < PER; q++) {
-            if (kind[q] != kChildLarge) continue;
-            if (s0 < w.lmax) w.large[s0] = Seg{start[q], size[q], cdepth[q], 0u};
+            s_med++;
+        } else if (kq == kChildLarge) {
+            if (s_large < w.lmax) w.large[s_large] = Seg{start[q], size[q], cdepth[q], 0u};
             else atomicOr(&h->err, kErrLargeOverflow);
-            s0++;
+            s_large++;
         }
+        // base-case buckets by floor(log2(size))
+        const int bin = (kq == kChildTiny || kq == kChildSmall) ? min(31 - __clz(size[q]), 7) : 0;
+#pragma unroll
+        for (int b = 1; b < 8; b++) hist[b] += bin == b ? 1u : 0u;
+    }
+    warp_add(&h->tiny_elems, e_tiny);
+    warp_add(&h->small_elems, e_small);
+    warp_add(&h->med_elems, e_med);
+#pragma unroll
+    for (int b = 1; b < 8; b++) {
+        const uint32_t c = __reduce_add_sync(FULL_MASK, hist[b]);
+        if (lane == 0u && c) atomicAdd(&h->small_hist[b], c);
     }
 }
 
