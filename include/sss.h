@@ -137,7 +137,7 @@ typedef struct sss_stats {
     uint32_t base_tiles;             /* base-case work tiles launched */
     uint64_t round_strings;          /* sum over rounds of strings distributed */
     uint64_t medium_strings;         /* of those, strings in per-CTA (medium) rounds */
-    uint64_t base_iterations;        /* base-case sort passes summed over tiles */
+    uint64_t base_iterations;        /* base-case sort passes summed over tiles and warp packs */
     uint32_t base_segment_hist[8];   /* base-case buckets by floor(log2(size)) (2-3, 4-7, ..., >= 128) */
     uint64_t base_strings;           /* strings finished by the base case */
     uint64_t run_strings;            /* strings finished as large runs of equal strings */

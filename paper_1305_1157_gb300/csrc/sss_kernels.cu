@@ -1163,12 +1163,19 @@ __global__ void __launch_bounds__(kScatterThreads, SSS_SCATTER_MIN_BLOCKS) k_sca
         constexpr int kBPT = (kNBMax + kScatterThreads) / kScatterThreads;
         uint32_t s_first[kBPT], s_next[kBPT], s_mine[kBPT];
         const uint32_t S0 = S[0];
+        const bool last_lane = (threadIdx.x & 31u) == 31u;
 #pragma unroll
         for (int q = 0; q < kBPT; q++) {
             const uint32_t b = threadIdx.x + q * kScatterThreads;
             s_first[q] = b < nb ? S[b * P.chunks] : 0u;
             s_mine[q] = b < nb ? S[b * P.chunks + ci] : 0u;
-            s_next[q] = b + 1 < nb ? S[(b + 1) * P.chunks] : 0u;
+            // the next bucket's start is the next lane's s_first; lane 31 reads it
+            s_next[q] = last_lane && b + 1 < nb ? S[(b + 1) * P.chunks] : 0u;
+        }
+#pragma unroll
+        for (int q = 0; q < kBPT; q++) {
+            const uint32_t nx = __shfl_down_sync(FULL_MASK, s_first[q], 1);
+            if (!last_lane) s_next[q] = nx;
         }
         // child segments of this thread's buckets (chunk 0 appends them):
         // start and size replace s_first and s_next in place
@@ -1538,20 +1545,25 @@ __global__ void __launch_bounds__(kBaseThreads) k_base(Work w, Params p) {
     }
 }
 
-// Base case of the buckets of at most kTinyMax strings: one warp per bucket,
-// lane i holds the bucket's i-th string.  The passes are those of k_base
-// (rank every string of an active run by (key, lane), move it there, fix the
-// LCP of neighbours whose keys differ, turn groups of equal keys without the
-// terminator into runs w bytes deeper) with a per-warp shared buffer and
-// ballots instead of block-wide barriers, so a warp stops as soon as its own
-// bucket is sorted.
+// Base case of the buckets of at most kTinyMax strings.  A warp takes the
+// list's buckets kTinyChunk at a time and packs consecutive ones into its 32
+// lanes (a bucket's strings on consecutive lanes, as many buckets as fit), so
+// that small buckets do not leave most lanes idle.  The passes are those of
+// k_base (rank every string of an active run by (key, lane), move it there,
+// fix the LCP of neighbours whose keys differ, turn groups of equal keys
+// without the terminator into runs w bytes deeper) with a per-warp shared
+// buffer and ballots instead of block-wide barriers; a bucket's first lane
+// is always a run head, so runs never cross buckets, and a warp stops as
+// soon as its own buckets are sorted.
 constexpr int kTinyWarps = 8;
+constexpr uint32_t kTinyChunk = 8;
 
 template <class KT>
 __global__ void __launch_bounds__(32 * kTinyWarps) k_tiny(Work w, Params p) {
     constexpr uint32_t kW = KeyTraits<KT>::kBytes;
     __shared__ uint64_t sK[kTinyWarps][32], sK2[kTinyWarps][32], sO[kTinyWarps][32];
     __shared__ uint32_t sI[kTinyWarps][32];
+    __shared__ uint8_t sOwn[kTinyWarps][32];  // the pack's bucket of each lane
     __shared__ unsigned long long s_iters;
     const int buf = w.hdr->round & 1u;
     const uint32_t nt = w.hdr->n_tiny_snap;
@@ -1560,11 +1572,37 @@ __global__ void __launch_bounds__(32 * kTinyWarps) k_tiny(Work w, Params p) {
     if (threadIdx.x == 0) s_iters = 0ull;
     __syncthreads();
     uint32_t my_iters = 0;
-    for (uint32_t t = blockIdx.x * kTinyWarps + wid; t < nt; t += gridDim.x * kTinyWarps) {
-        const Seg g = w.tiny[buf][t];
-        const uint32_t r = g.size;  // 2..kTinyMax
-        const bool live = lane < r;
-        const uint32_t G = g.begin + lane;
+    const uint32_t nchunks = (nt + kTinyChunk - 1u) / kTinyChunk;
+    for (uint32_t c = blockIdx.x * kTinyWarps + wid; c < nchunks; c += gridDim.x * kTinyWarps) {
+    const uint32_t c_end = min(nt, (c + 1u) * kTinyChunk);
+    for (uint32_t e0 = c * kTinyChunk; e0 < c_end;) {
+        // the buckets e0, e0 + 1, ... that fit 32 lanes together
+        Seg sg{0u, 0u, 0u, 0u};
+        if (e0 + lane < c_end) sg = w.tiny[buf][e0 + lane];
+        uint32_t inc = sg.size;  // inclusive prefix of the sizes over the lanes
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL_MASK, inc, o);
+            if (lane >= (uint32_t)o) inc += y;
+        }
+        const uint32_t nb = (uint32_t)__popc(__ballot_sync(FULL_MASK, e0 + lane < c_end && inc <= 32u));
+        if (nb == 0u) {  // never expected: listed buckets hold at most kTinyMax strings
+            if (lane == 0) atomicOr(&w.hdr->err, kErrSmallOverflow);
+            break;
+        }
+        const uint32_t used = __shfl_sync(FULL_MASK, inc, nb - 1u);
+        if (lane < nb)
+            for (uint32_t x = inc - sg.size; x < inc; x++) sOwn[wid][x] = (uint8_t)lane;
+        __syncwarp();
+        const bool live = lane < used;
+        const uint32_t j = live ? sOwn[wid][lane] : 0u;
+        const uint32_t jbegin = __shfl_sync(FULL_MASK, sg.begin, j);
+        const uint32_t jdepth = __shfl_sync(FULL_MASK, sg.depth, j);
+        const uint32_t jend = __shfl_sync(FULL_MASK, inc, j);
+        const uint32_t jfirst = jend - __shfl_sync(FULL_MASK, sg.size, j);
+        __syncwarp();  // sOwn is rewritten by the next pack
+        e0 += nb;
+        const uint32_t G = jbegin + (lane - jfirst);
         uint64_t k = 0, k2 = 0, o = 0;
         uint32_t id = 0;
         if (live) {
@@ -1574,7 +1612,7 @@ __global__ void __launch_bounds__(32 * kTinyWarps) k_tiny(Work w, Params p) {
             o = rc.off;
             id = rc.idx;
         }
-        uint32_t rs = 0, re = r, d = g.depth;  // my run [rs, re) and its common prefix
+        uint32_t rs = jfirst, re = jend, d = jdepth;  // my run [rs, re) and its common prefix
         bool act = live;
         for (uint32_t iter = 0;; iter++) {
             if (iter >= kBaseMaxIters) {  // never expected: strings end, so runs end
@@ -1651,6 +1689,7 @@ __global__ void __launch_bounds__(32 * kTinyWarps) k_tiny(Work w, Params p) {
             if (!__any_sync(FULL_MASK, go)) break;
         }
         if (live) w.out_perm[G] = id;
+    }
     }
     if ((threadIdx.x & 31u) == 0 && my_iters) atomicAdd(&s_iters, (unsigned long long)my_iters);
     __syncthreads();
@@ -2077,7 +2116,8 @@ cudaError_t launch_advance(const Work& w, Prof* pf, cudaStream_t st) {
 
 // The warp-form base case (buckets of at most kTinyMax strings).
 static cudaError_t launch_tiny(const Work& w, const Params& p, const Hdr* hc, Prof* pf, cudaStream_t st) {
-    const uint32_t gt = grid_of(p.num_sms * 8u, hc, hc ? (hc->n_tiny_snap + kTinyWarps - 1) / kTinyWarps : 0u);
+    const uint32_t gt = grid_of(p.num_sms * 8u, hc,
+                                hc ? (hc->n_tiny_snap + kTinyWarps * kTinyChunk - 1) / (kTinyWarps * kTinyChunk) : 0u);
     if (gt) {
         ProfScope ps(pf, kBase, st);
         if (p.key_bytes == 16) k_tiny<Key16><<<gt, 32 * kTinyWarps, 0, st>>>(w, p);
