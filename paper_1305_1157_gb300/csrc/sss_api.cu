@@ -86,8 +86,8 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 struct Layout {
     size_t total = 0;
     size_t o_rec0, o_rec1, o_counts, o_counts_scan, o_tlvl, o_tino, o_plans, o_chunk_seg,
-        o_large, o_med0, o_med1, o_small0, o_small1, o_tiny0, o_tiny1, o_small_size0, o_small_size1, o_small_off, o_tile_first,
-        o_bigrun0, o_bigrun1, o_bids, o_scan_tmp, o_scan_tmp2, o_hdr, o_roots,
+        o_large, o_med0, o_med1, o_small0, o_small1, o_tiny0, o_tiny1,
+        o_bigrun0, o_bigrun1, o_bids, o_scan_tmp, o_hdr, o_roots,
         o_cdf_tab, o_cdf_norm;
     uint32_t cmax, tmax, lmax, chmax, smax, ymax, bmax, scan_tmp_max, mmax;
 };
@@ -131,7 +131,7 @@ Layout layout_for(uint32_t n, const sss_options& o, uint32_t num_roots, bool lea
     const uint64_t smax = (T > kTinyMax ? nn / (kTinyMax + 1) : 0) + num_roots + 2;
     const uint64_t ymax = nn / 2 + num_roots + 2;
     const uint64_t bmax = nn / (T + 1) + nn / kRunPiece + 2;  // runs > T strings, in pieces
-    const uint64_t scan_tmp = scan_tmp_elems((uint32_t)(cmax > smax ? cmax : smax)) + 1;
+    const uint64_t scan_tmp = scan_tmp_elems((uint32_t)cmax) + 1;
     L.cmax = (uint32_t)cmax; L.tmax = (uint32_t)tmax; L.lmax = (uint32_t)lmax; L.chmax = (uint32_t)chmax;
     L.smax = (uint32_t)smax; L.ymax = (uint32_t)ymax; L.bmax = (uint32_t)bmax; L.scan_tmp_max = (uint32_t)scan_tmp;
     L.mmax = (uint32_t)mmax;
@@ -152,15 +152,10 @@ Layout layout_for(uint32_t n, const sss_options& o, uint32_t num_roots, bool lea
     L.o_small1 = take(sizeof(Seg) * smax);
     L.o_tiny0 = take(sizeof(Seg) * ymax);
     L.o_tiny1 = take(sizeof(Seg) * ymax);
-    L.o_small_size0 = take(4 * smax);
-    L.o_small_size1 = take(4 * smax);
-    L.o_small_off = take(4 * (smax + 1));
-    L.o_tile_first = take(4 * (nn / T + 2));
     L.o_bigrun0 = take(sizeof(Seg) * bmax);
     L.o_bigrun1 = take(sizeof(Seg) * bmax);
     L.o_bids = take(sizeof(uint16_t) * nn);
     L.o_scan_tmp = take(4 * scan_tmp);
-    L.o_scan_tmp2 = take(4 * scan_tmp);
     L.o_hdr = take(sizeof(Hdr));
     L.o_roots = take(sizeof(Seg) * (num_roots ? num_roots : 1));
     L.o_cdf_tab = L.o_cdf_norm = 0;
@@ -192,15 +187,10 @@ Work make_work(const Layout& L, char* ws, const uint8_t* chars, const uint64_t* 
     w.small[1] = (Seg*)(ws + L.o_small1);
     w.tiny[0] = (Seg*)(ws + L.o_tiny0);
     w.tiny[1] = (Seg*)(ws + L.o_tiny1);
-    w.small_size[0] = (uint32_t*)(ws + L.o_small_size0);
-    w.small_size[1] = (uint32_t*)(ws + L.o_small_size1);
-    w.small_off = (uint32_t*)(ws + L.o_small_off);
-    w.tile_first = (uint32_t*)(ws + L.o_tile_first);
     w.bigrun[0] = (Seg*)(ws + L.o_bigrun0);
     w.bigrun[1] = (Seg*)(ws + L.o_bigrun1);
     w.bids = (uint16_t*)(ws + L.o_bids);
     w.scan_tmp = (uint32_t*)(ws + L.o_scan_tmp);
-    w.scan_tmp2 = (uint32_t*)(ws + L.o_scan_tmp2);
     w.hdr = (Hdr*)(ws + L.o_hdr);
     if (L.o_cdf_tab) {
         w.cdf_tab = (float*)(ws + L.o_cdf_tab);

@@ -178,13 +178,9 @@ struct Work {
     Seg* med[2];             // [mmax] children for the next per-CTA round
     Seg* small[2];           // [smax] children for the base case (tile form)
     Seg* tiny[2];            // [ymax] children of at most kTinyMax strings (warp form)
-    uint32_t* small_size[2]; // [smax] their sizes
     Seg* bigrun[2];          // [bmax] pieces of large runs of equal strings
     uint16_t* bids;          // [n] bucket of each string of a device-wide round (k_classify -> k_scatter)
-    uint32_t* small_off;     // [smax + 1] packed start of each small segment
-    uint32_t* tile_first;    // [n / base_threshold + 2] first small segment packed into each base-case tile
     uint32_t* scan_tmp;      // [scan_tmp_max] scan scratch of the distribution rounds
-    uint32_t* scan_tmp2;     // [scan_tmp_max] scan scratch of the base case
     Hdr* hdr;
     // learned proposal (allocated for sss_sort_learned only)
     float* cdf_tab;          // [lmax * (M + 1)] CDF at the knots of each segment's model

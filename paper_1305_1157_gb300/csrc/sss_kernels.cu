@@ -175,7 +175,6 @@ __device__ __forceinline__ void append_children_n(const Work& w, int out, const 
         } else if (kq == kChildSmall) {
             if (s_small < w.smax) {
                 w.small[out][s_small] = Seg{start[q], size[q], cdepth[q], 0u};
-                w.small_size[out][s_small] = size[q];
                 e_small += size[q];
             } else {
                 atomicOr(&h->err, kErrSmallOverflow);
@@ -305,9 +304,8 @@ __global__ void k_hdr_reset(Work w) {
     h->q_sample = 0; h->q_fit = 0; h->q_classify = 0; h->q_scatter = 0;
     h->q_med = 0; h->q_base = 0; h->q_bigrun = 0;
     for (int i = 0; i < 8; i++) h->small_hist[i] = 0;
-    // the scans' completion counters (the last entry of their scratch)
+    // the scan's completion counter (the last entry of its scratch)
     w.scan_tmp[w.scan_tmp_max - 1u] = 0u;
-    w.scan_tmp2[w.scan_tmp_max - 1u] = 0u;
 }
 
 // Roots: one segment per set (a single sort is one set) at depth 0.
@@ -1345,6 +1343,14 @@ __global__ void __launch_bounds__(kScatterThreads, SSS_MED_MIN_BLOCKS) k_med_rou
 // ------------------------------------------------------------ base case
 
 constexpr int kBaseThreads = kBaseCap;  // one thread per slot of a tile
+// small-list buckets a CTA takes at a time (<= 32: one warp packs them).
+// Four keep the work items fine enough for the persistent grid of the graph
+// form (8 and 16 measured up to 2.7 % slower on url-16m, no faster on dna-20m)
+#ifndef SSS_BASE_CHUNK
+#define SSS_BASE_CHUNK 4
+#endif
+constexpr uint32_t kBaseChunk = SSS_BASE_CHUNK;
+static_assert(kBaseChunk >= 1 && kBaseChunk <= 32, "one warp packs a chunk");
 
 struct BaseSmem {
     uint64_t K[kBaseCap];             // key word of the element in a slot
@@ -1360,31 +1366,14 @@ struct BaseSmem {
     uint32_t wmax[kBaseThreads / 32];
 };
 
-// tile_first[t]: the first small segment whose packed start lies at or after
-// t * T (segments are at most T strings, so every tile but an empty tail
-// holds the start of one).
-__global__ void k_tile_map(Work w, Params p) {
-    const uint32_t ns = w.hdr->n_small_snap, total = w.hdr->small_elems_snap;
-    const uint32_t T = p.base_threshold;
-    const uint32_t tiles = (total + T - 1) / T;
-    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < tiles; t += gridDim.x * blockDim.x) {
-        const uint32_t x = t * T;
-        uint32_t lo = 0, hi = ns;
-        while (lo < hi) {
-            const uint32_t m = (lo + hi) >> 1;
-            if (w.small_off[m] < x) lo = m + 1; else hi = m;
-        }
-        w.tile_first[t] = lo;
-    }
-}
-
 template <class KT> __device__ __forceinline__ KT base_key(uint64_t a, uint64_t b);
 template <> __device__ __forceinline__ uint64_t base_key<uint64_t>(uint64_t a, uint64_t) { return a; }
 template <> __device__ __forceinline__ Key16 base_key<Key16>(uint64_t a, uint64_t b) { return Key16{a, b}; }
 
-// One CTA per tile of packed small segments: the segments whose packed start
-// lies in [t*T, (t+1)*T) (T = base_threshold <= kBaseMax), at most 2T - 1 <=
-// kBaseCap strings; thread s owns slot s.  A run is a contiguous slot range
+// Buckets of the small list (kTinyMax < size <= base_threshold <= kBaseMax),
+// kBaseChunk at a time per CTA (the work queue hands out chunks), packed into
+// tiles of at most kBaseCap slots: as many consecutive buckets as fit, on
+// consecutive slots; thread s owns slot s.  A run is a contiguous slot range
 // whose strings share a prefix of drun[run] bytes, held in index order.
 // Each pass ranks every element of every active run among the run's
 // elements by (key word, slot) and moves it there (a stable sort of the
@@ -1394,31 +1383,51 @@ template <> __device__ __forceinline__ Key16 base_key<Key16>(uint64_t a, uint64_
 // next pass.  KT: the key of a pass, one word (w = 8) or both cached words
 // (w = 16).
 template <class KT>
-__global__ void __launch_bounds__(kBaseThreads) k_base(Work w, Params p) {
+__global__ void __launch_bounds__(kBaseThreads, 8) k_base(Work w, Params p) {
     constexpr bool kWide = KeyTraits<KT>::kBytes == 16;
     __shared__ BaseSmem sm;
     const uint32_t s = threadIdx.x;
     const uint32_t lane = s & 31u, warp = s >> 5;
     const int buf = w.hdr->round & 1u;
-    const uint32_t ns = w.hdr->n_small_snap, total = w.hdr->small_elems_snap;
-    const uint32_t T = p.base_threshold;
-    const uint32_t tiles = (total + T - 1) / T;
-    __shared__ uint32_t s_item;
-    for (uint32_t tile = first_item(); tile < tiles; tile = next_item(&w.hdr->q_base, &s_item)) {
-    const uint32_t lo = w.tile_first[tile], hi = tile + 1 < tiles ? w.tile_first[tile + 1] : ns;
-    if (lo >= hi) continue;  // an empty tail tile
-    const uint32_t slot0 = w.small_off[lo];
-    const uint32_t cnt = (hi < ns ? w.small_off[hi] : total) - slot0;
-    const uint32_t nseg = hi - lo;
-    for (uint32_t i = s; i < nseg; i += blockDim.x) {
-        const uint32_t b = w.small_off[lo + i] - slot0;
-        const Seg g = w.small[buf][lo + i];
-        sm.sbase[i] = b;
-        sm.sbegin[i] = g.begin;
-        sm.drun[b] = g.depth;
-        sm.RL[b] = g.size;
+    const uint32_t ns = w.hdr->n_small_snap;
+    const uint32_t nchunks = (ns + kBaseChunk - 1u) / kBaseChunk;
+    __shared__ uint32_t s_item, s_nseg, s_cnt;
+    for (uint32_t chunk = first_item(); chunk < nchunks; chunk = next_item(&w.hdr->q_base, &s_item)) {
+    const uint32_t c_end = min(ns, (chunk + 1u) * kBaseChunk);
+    for (uint32_t e0 = chunk * kBaseChunk; e0 < c_end;) {
+    if (warp == 0) {
+        // the buckets e0, e0 + 1, ... that fit kBaseCap slots together, on
+        // consecutive slots
+        Seg g{0u, 0u, 0u, 0u};
+        const bool have = e0 + lane < c_end;
+        if (have) g = w.small[buf][e0 + lane];
+        uint32_t inc = g.size;  // inclusive prefix of the sizes over the lanes
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL_MASK, inc, o);
+            if (lane >= (uint32_t)o) inc += y;
+        }
+        const uint32_t ng = (uint32_t)__popc(__ballot_sync(FULL_MASK, have && inc <= (uint32_t)kBaseCap));
+        const uint32_t used = __shfl_sync(FULL_MASK, inc, ng ? ng - 1u : 0u);
+        if (lane < ng) {
+            const uint32_t b = inc - g.size;
+            sm.sbase[lane] = b;
+            sm.sbegin[lane] = g.begin;
+            sm.drun[b] = g.depth;
+            sm.RL[b] = g.size;
+        }
+        if (lane == 0) {
+            s_nseg = ng;
+            s_cnt = ng ? used : 0u;
+        }
     }
     __syncthreads();
+    const uint32_t nseg = s_nseg, cnt = s_cnt;
+    if (nseg == 0u) {  // never expected: listed buckets hold at most kBaseMax strings
+        if (s == 0) atomicOr(&w.hdr->err, kErrSmallOverflow);
+        break;
+    }
+    e0 += nseg;
     bool act = s < cnt;  // the slot lies in a run to rank in this pass
     uint32_t G = 0, id = 0;
     uint64_t k = 0, k2 = 0, o = 0;
@@ -1541,7 +1550,8 @@ __global__ void __launch_bounds__(kBaseThreads) k_base(Work w, Params p) {
     }
     if (s < cnt) w.out_perm[G] = id;
     if (s == 0) atomicAdd(&w.hdr->base_iters, (unsigned long long)(iter + 1));
-    __syncthreads();  // shared arrays are rewritten by the next tile
+    __syncthreads();  // shared arrays are rewritten by the next pack
+    }
     }
 }
 
@@ -1749,23 +1759,14 @@ constexpr uint32_t kScanTile = kScanThreads * kScanPer;
 
 size_t scan_tmp_elems(uint32_t n) { return (size_t)(n + kScanTile - 1) / kScanTile + 1; }
 
-// Scan input: in[0], or in[*sel & 1] when sel is given (a list chosen by
-// round parity on the device).
-struct ScanIn {
-    const uint32_t* in[2];
-    const uint32_t* sel;
-    __device__ __forceinline__ const uint32_t* get() const { return sel ? in[*sel & 1u] : in[0]; }
-};
-
 // Tile sums of the input; the CTA that finishes last (a counter in device
 // memory, no waiting) scans them in place, writes the total to out[n] and
 // resets the counter.
-__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(ScanIn src, const uint32_t* n_ptr, uint32_t* sums,
-                                                              uint32_t* out, uint32_t* done) {
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* in, const uint32_t* n_ptr,
+                                                              uint32_t* sums, uint32_t* out, uint32_t* done) {
     __shared__ uint32_t wsum[33];
     __shared__ uint32_t s_last;
     const uint32_t n = *n_ptr;
-    const uint32_t* in = src.get();
     const uint32_t tiles = (n + kScanTile - 1) / kScanTile;
     for (uint32_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
         const uint32_t base = tile * kScanTile;
@@ -1807,12 +1808,11 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(ScanIn src, const 
 // (padded, entry i at i + i / 32, so that neither the coalesced copies nor
 // the threads' runs of kScanPer consecutive entries conflict on banks), so
 // that both its loads and its stores are whole coalesced lines.
-__global__ void __launch_bounds__(kScanThreads) k_scan_down(ScanIn src, uint32_t* out, const uint32_t* n_ptr,
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* in, uint32_t* out, const uint32_t* n_ptr,
                                                             const uint32_t* sums) {
     __shared__ uint32_t wsum[33];
     __shared__ uint32_t tb[kScanTile + kScanTile / 32];
     const uint32_t n = *n_ptr;
-    const uint32_t* in = src.get();
     const uint32_t tiles = (n + kScanTile - 1) / kScanTile;
     for (uint32_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
         const uint32_t t0 = tile * kScanTile;
@@ -1849,29 +1849,22 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(ScanIn src, uint32_t
     }
 }
 
-// out[0..n) = exclusive prefix sums of the input, out[n] = total, with n read
+// out[0..n) = exclusive prefix sums of in[0..n), out[n] = total, with n read
 // from device memory (*n_ptr); n_host (if known) only sizes the grid.  tmp
 // holds scan_tmp_elems(n) entries; done is a counter that is zero between
-// scans.  The input is in, or with sel given in_alt when *sel is odd.
-static cudaError_t launch_scan_sel(const uint32_t* in, const uint32_t* in_alt, const uint32_t* sel, uint32_t* out,
-                                   const uint32_t* n_ptr, const uint32_t* n_host, uint32_t* tmp, uint32_t* done,
-                                   Prof* pf, cudaStream_t st) {
-    const ScanIn src{{in, in_alt}, sel};
+// scans.
+cudaError_t launch_scan_u32(const uint32_t* in, uint32_t* out, const uint32_t* n_ptr, const uint32_t* n_host,
+                            uint32_t* tmp, uint32_t* done, Prof* pf, cudaStream_t st) {
     uint32_t grid = device_sms() * 8u;
     if (n_host) {
         const uint32_t tiles = (*n_host + kScanTile - 1) / kScanTile;
         grid = max(1u, min(grid, tiles));
     }
     ProfScope ps(pf, kScan, st);
-    k_scan_reduce<<<grid, kScanThreads, 0, st>>>(src, n_ptr, tmp, out, done);
-    k_scan_down<<<grid, kScanThreads, 0, st>>>(src, out, n_ptr, tmp);
+    k_scan_reduce<<<grid, kScanThreads, 0, st>>>(in, n_ptr, tmp, out, done);
+    k_scan_down<<<grid, kScanThreads, 0, st>>>(in, out, n_ptr, tmp);
     if (pf) { pf->launches += 1; pf->cls_launches[kScan] += 1; }
     return cudaGetLastError();
-}
-
-cudaError_t launch_scan_u32(const uint32_t* in, uint32_t* out, const uint32_t* n_ptr, const uint32_t* n_host,
-                            uint32_t* tmp, uint32_t* done, Prof* pf, cudaStream_t st) {
-    return launch_scan_sel(in, in, nullptr, out, n_ptr, n_host, tmp, done, pf, st);
 }
 
 // ------------------------------------------------------------ launches
@@ -2126,24 +2119,17 @@ static cudaError_t launch_tiny(const Work& w, const Params& p, const Hdr* hc, Pr
     return cudaGetLastError();
 }
 
-// The tile-form base case (scan of the bucket sizes, tile map, k_base) and
-// the large runs of equal strings.
+// The tile-form base case (k_base over chunks of the small list) and the
+// large runs of equal strings.  out_tiles: the chunks launched.
 static cudaError_t launch_tiles(const Work& w, const Params& p, const Hdr* hc, uint32_t* out_tiles, Prof* pf,
                                 cudaStream_t st) {
     const uint32_t sms = p.num_sms;
-    uint32_t tiles = hc ? (hc->small_elems_snap + p.base_threshold - 1) / p.base_threshold : 0u;
-    if (!hc || hc->n_small_snap) {
-        cudaError_t e = launch_scan_sel(w.small_size[0], w.small_size[1], &w.hdr->round, w.small_off,
-                                        &w.hdr->n_small_snap, hc ? &hc->n_small_snap : nullptr, w.scan_tmp2,
-                                        w.scan_tmp2 + (w.scan_tmp_max - 1u), pf, st);
-        if (e != cudaSuccess) return e;
-        {
-            ProfScope ps(pf, kBase, st);
-            k_tile_map<<<hc ? grid_for(tiles, 256, 4, sms) : sms, 256, 0, st>>>(w, p);
-        }
+    const uint32_t tiles = hc ? (hc->n_small_snap + kBaseChunk - 1u) / kBaseChunk : 0u;
+    if (!hc || tiles) {
         ProfScope ps(pf, kBase, st);
-        if (p.key_bytes == 16) k_base<Key16><<<grid_of(sms * 8u, hc, tiles), kBaseThreads, 0, st>>>(w, p);
-        else k_base<uint64_t><<<grid_of(sms * 8u, hc, tiles), kBaseThreads, 0, st>>>(w, p);
+        const uint32_t g = grid_of(sms * 8u, hc, tiles);
+        if (p.key_bytes == 16) k_base<Key16><<<g, kBaseThreads, 0, st>>>(w, p);
+        else k_base<uint64_t><<<g, kBaseThreads, 0, st>>>(w, p);
     }
     const uint32_t gr = grid_of(sms * 4u, hc, hc ? hc->n_bigrun_snap : 0u);
     if (gr) {
