@@ -700,6 +700,16 @@ def main():
     opts.profile = 0
     sss.sss_set_options(opts)
 
+    # the host-side oracle run ends before the end-to-end timing: its threads
+    # would compete with the uploads for the host's memory bandwidth
+    oracle_info = None
+    if child is not None:
+        try:
+            oracle_info = q.get(timeout=900)
+        except Exception as e:
+            oracle_info = {"error": repr(e)}
+        child.join(timeout=10)
+
     # end to end through the host-buffer entry point
     e2e = None
     if args.e2e_steps > 0:
@@ -781,13 +791,6 @@ def main():
                              "launches_per_step": int(prof_launches[i]) // args.steps}
                     for i in range(len(cls)) if prof_launches[i]}
 
-    oracle_info = None
-    if child is not None:
-        try:
-            oracle_info = q.get(timeout=900)
-        except Exception as e:
-            oracle_info = {"error": repr(e)}
-        child.join(timeout=10)
     cpu = None
     D = None
     if oracle_info and "error" not in oracle_info:
