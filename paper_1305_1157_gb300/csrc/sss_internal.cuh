@@ -317,7 +317,6 @@ __device__ __forceinline__ bool kgt(uint64_t a, uint64_t b) { return a > b; }
 __device__ __forceinline__ bool kgt(const Key16& a, const Key16& b) { return a.h > b.h || (a.h == b.h && a.l > b.l); }
 __device__ __forceinline__ bool keq(uint64_t a, uint64_t b) { return a == b; }
 __device__ __forceinline__ bool keq(const Key16& a, const Key16& b) { return a.h == b.h && a.l == b.l; }
-template <class KT> __device__ __forceinline__ bool klt(const KT& a, const KT& b) { return kgt(b, a); }
 
 // The key holds the terminator (bytes after it are zero).
 __device__ __forceinline__ bool kends(uint64_t x) { return key_ends(x); }
