@@ -86,7 +86,7 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 struct Layout {
     size_t total = 0;
     size_t o_rec0, o_rec1, o_counts, o_counts_scan, o_tlvl, o_tino, o_plans, o_chunk_seg,
-        o_large, o_med0, o_med1, o_small0, o_small1, o_tiny0, o_tiny1,
+        o_large, o_med0, o_med1, o_medw0, o_medw1, o_small0, o_small1, o_tiny0, o_tiny1,
         o_bigrun0, o_bigrun1, o_bids, o_scan_tmp, o_hdr, o_roots,
         o_cdf_tab, o_cdf_norm;
     uint32_t cmax, tmax, lmax, chmax, smax, ymax, bmax, scan_tmp_max, mmax;
@@ -148,6 +148,8 @@ Layout layout_for(uint32_t n, const sss_options& o, uint32_t num_roots, bool lea
     L.o_large = take(sizeof(Seg) * lmax);
     L.o_med0 = take(sizeof(Seg) * mmax);
     L.o_med1 = take(sizeof(Seg) * mmax);
+    L.o_medw0 = take(sizeof(Seg) * mmax);
+    L.o_medw1 = take(sizeof(Seg) * mmax);
     L.o_small0 = take(sizeof(Seg) * smax);
     L.o_small1 = take(sizeof(Seg) * smax);
     L.o_tiny0 = take(sizeof(Seg) * ymax);
@@ -183,6 +185,8 @@ Work make_work(const Layout& L, char* ws, const uint8_t* chars, const uint64_t* 
     w.large = (Seg*)(ws + L.o_large);
     w.med[0] = (Seg*)(ws + L.o_med0);
     w.med[1] = (Seg*)(ws + L.o_med1);
+    w.medw[0] = (Seg*)(ws + L.o_medw0);
+    w.medw[1] = (Seg*)(ws + L.o_medw1);
     w.small[0] = (Seg*)(ws + L.o_small0);
     w.small[1] = (Seg*)(ws + L.o_small1);
     w.tiny[0] = (Seg*)(ws + L.o_tiny0);
@@ -381,10 +385,10 @@ int run_sort(const Work& w, const sss_options& o, const Seg* roots_dev, uint32_t
     rc = read_hdr(hh, w, st);
     if (rc) return rc;
     CK(launch_fused_root(w, p, hh, pf, st), "root round");
-    for (uint32_t round = 0; hh->L > 0 || hh->n_med_snap > 0; round++) {
+    for (uint32_t round = 0; hh->L > 0 || hh->n_med_snap > 0 || hh->n_medw_snap > 0; round++) {
         if (round >= 1u << 22) return fail(SSS_ERR_INTERNAL, "round limit exceeded");
         if (round < SSS_MAX_ROUNDS_LOGGED) {
-            stats->round_segments[round] = hh->L + hh->n_med_snap;
+            stats->round_segments[round] = hh->L + hh->n_med_snap + hh->n_medw_snap;
             stats->round_active[round] = hh->large_elems_snap + hh->med_elems_snap;
         }
         stats->rounds++;

@@ -23,6 +23,14 @@ constexpr uint32_t kRunPiece = 2048;            // strings per work item of a la
 constexpr uint32_t kMedMax = 8192;              // largest bucket one CTA distributes alone
 constexpr int kMedKMax = 9;                     // its deepest tree: choose_k(8192) = 9
 constexpr int kMedNB = (2 << kMedKMax) - 1;     // 1023 buckets
+// medium buckets this small take one warp each (0: all take a CTA)
+#ifndef SSS_MED_WARP_MAX
+#define SSS_MED_WARP_MAX 1023u
+#endif
+constexpr uint32_t kMedWarpMax = SSS_MED_WARP_MAX;
+constexpr int kMWKMax = 5;                       // their deepest tree: choose_k(1023) = 5
+constexpr int kMWNB = (2 << kMWKMax) - 1;        // 63 buckets
+static_assert(kMedWarpMax < 1024u, "a per-warp medium bucket's tree has at most kMWKMax levels");
 #ifndef SSS_CHUNKS_PER_SM
 #define SSS_CHUNKS_PER_SM 8
 #endif
@@ -102,18 +110,18 @@ struct Hdr {
     uint32_t n_large, n_med, n_small, n_bigrun, err, small_elems, med_elems, n_tiny, tiny_elems;
     uint32_t learned_models;  // segment models fitted by k_cdf_fit
     uint32_t radix_segments;  // segments of device-wide rounds classified by a digit
-    uint32_t pad0;
+    uint32_t n_medw;          // children for the next round's one-warp-per-bucket medium round
     // snapshot for the host, written by k_plan
     uint32_t L, total_chunks, total_counts, total_tree;
     uint32_t n_med_snap, n_small_snap, n_bigrun_snap, small_elems_snap;
     uint32_t large_elems_snap, med_elems_snap, chunk, round;  // round: rounds done (buffer parity)
-    uint32_t n_tiny_snap, tiny_elems_snap, pad1[2];
+    uint32_t n_tiny_snap, tiny_elems_snap, n_medw_snap, pad1;
     unsigned long long refills;   // key words gathered in device-wide rounds
     unsigned long long med_refills;  // key words gathered in medium (per-CTA) rounds
     unsigned long long base_iters;  // base-case refill iterations summed over tiles
     unsigned long long learned_keys, learned_misses;  // proposals made / rejected by the exact check
     // work queues of the persistent kernels (reset by k_plan)
-    uint32_t q_sample, q_fit, q_classify, q_scatter, q_med, q_base, q_bigrun, q_pad;
+    uint32_t q_sample, q_fit, q_classify, q_scatter, q_med, q_base, q_bigrun, q_medw;
     uint32_t small_hist[8];         // base-case segments by floor(log2(size))
 };
 
@@ -176,6 +184,7 @@ struct Work {
     // (r + 1) & 1 while the base case of the children of round r - 1 reads
     // parity r & 1 concurrently
     Seg* med[2];             // [mmax] children for the next per-CTA round
+    Seg* medw[2];            // [mmax] children for the next per-warp round (at most kMedWarpMax strings)
     Seg* small[2];           // [smax] children for the base case (tile form)
     Seg* tiny[2];            // [ymax] children of at most kTinyMax strings (warp form)
     Seg* bigrun[2];          // [bmax] pieces of large runs of equal strings

@@ -78,14 +78,14 @@ __device__ uint32_t block_excl_sum(uint32_t x, uint32_t* wsum, uint32_t* total) 
 
 // Where a bucket of `size` strings goes next (Sec. 3.1 "Parallelization of
 // S^5": size classes).  isrun: all its strings are equal (finished).
-enum : uint32_t { kChildNone = 0, kChildRuns, kChildTiny, kChildSmall, kChildMed, kChildLarge };
+enum : uint32_t { kChildNone = 0, kChildRuns, kChildTiny, kChildSmall, kChildMed, kChildLarge, kChildMedW };
 
 __device__ __forceinline__ uint32_t child_kind(const Params& p, uint32_t size, bool isrun) {
     if (size <= 1) return kChildNone;
     if (isrun && size > p.base_threshold) return kChildRuns;
     if (size <= min(p.base_threshold, kTinyMax)) return kChildTiny;
     if (size <= p.base_threshold) return kChildSmall;
-    if (size <= p.med_threshold) return kChildMed;
+    if (size <= p.med_threshold) return size <= kMedWarpMax ? kChildMedW : kChildMed;
     return kChildLarge;
 }
 
@@ -118,7 +118,7 @@ __device__ __forceinline__ void append_children_n(const Work& w, int out, const 
                                                   const uint32_t (&start)[PER], const uint32_t (&size)[PER],
                                                   const uint32_t (&cdepth)[PER], const uint32_t (&runlcp)[PER]) {
     Hdr* h = w.hdr;
-    uint32_t n_runs = 0, n_tiny = 0, n_small = 0, n_med = 0, n_large = 0;
+    uint32_t n_runs = 0, n_tiny = 0, n_small = 0, n_med = 0, n_large = 0, n_medw = 0;
 #pragma unroll
     for (int q = 0; q < PER; q++) {
         n_runs += kind[q] == kChildRuns ? (size[q] + kRunPiece - 1u) / kRunPiece : 0u;
@@ -126,26 +126,29 @@ __device__ __forceinline__ void append_children_n(const Work& w, int out, const 
         n_small += kind[q] == kChildSmall ? 1u : 0u;
         n_med += kind[q] == kChildMed ? 1u : 0u;
         n_large += kind[q] == kChildLarge ? 1u : 0u;
+        n_medw += kind[q] == kChildMedW ? 1u : 0u;
     }
-    if (!__any_sync(FULL_MASK, n_runs + n_tiny + n_small + n_med + n_large > 0u)) return;
+    if (!__any_sync(FULL_MASK, n_runs + n_tiny + n_small + n_med + n_large + n_medw > 0u)) return;
     const uint32_t lane = threadIdx.x & 31u;
-    uint32_t t_runs, t_tiny, t_small, t_med, t_large;
+    uint32_t t_runs, t_tiny, t_small, t_med, t_large, t_medw;
     const uint32_t x_runs = warp_excl(n_runs, &t_runs), x_tiny = warp_excl(n_tiny, &t_tiny);
     const uint32_t x_small = warp_excl(n_small, &t_small), x_med = warp_excl(n_med, &t_med);
-    const uint32_t x_large = warp_excl(n_large, &t_large);
-    uint32_t b_runs = 0, b_tiny = 0, b_small = 0, b_med = 0, b_large = 0;
+    const uint32_t x_large = warp_excl(n_large, &t_large), x_medw = warp_excl(n_medw, &t_medw);
+    uint32_t b_runs = 0, b_tiny = 0, b_small = 0, b_med = 0, b_large = 0, b_medw = 0;
     if (lane == 31u) {
         if (t_runs) b_runs = atomicAdd(&h->n_bigrun, t_runs);
         if (t_tiny) b_tiny = atomicAdd(&h->n_tiny, t_tiny);
         if (t_small) b_small = atomicAdd(&h->n_small, t_small);
         if (t_med) b_med = atomicAdd(&h->n_med, t_med);
         if (t_large) b_large = atomicAdd(&h->n_large, t_large);
+        if (t_medw) b_medw = atomicAdd(&h->n_medw, t_medw);
     }
     uint32_t s_runs = __shfl_sync(FULL_MASK, b_runs, 31) + x_runs;
     uint32_t s_tiny = __shfl_sync(FULL_MASK, b_tiny, 31) + x_tiny;
     uint32_t s_small = __shfl_sync(FULL_MASK, b_small, 31) + x_small;
     uint32_t s_med = __shfl_sync(FULL_MASK, b_med, 31) + x_med;
     uint32_t s_large = __shfl_sync(FULL_MASK, b_large, 31) + x_large;
+    uint32_t s_medw = __shfl_sync(FULL_MASK, b_medw, 31) + x_medw;
     uint32_t e_tiny = 0, e_small = 0, e_med = 0;
     uint32_t hist[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 #pragma unroll
@@ -192,6 +195,14 @@ __device__ __forceinline__ void append_children_n(const Work& w, int out, const 
             if (s_large < w.lmax) w.large[s_large] = Seg{start[q], size[q], cdepth[q], 0u};
             else atomicOr(&h->err, kErrLargeOverflow);
             s_large++;
+        } else if (kq == kChildMedW) {
+            if (s_medw < w.mmax) {
+                w.medw[out][s_medw] = Seg{start[q], size[q], cdepth[q], 0u};
+                e_med += size[q];
+            } else {
+                atomicOr(&h->err, kErrMedOverflow);
+            }
+            s_medw++;
         }
         // base-case buckets by floor(log2(size))
         const int bin = (kq == kChildTiny || kq == kChildSmall) ? min(31 - __clz(size[q]), 7) : 0;
@@ -303,6 +314,7 @@ __global__ void k_hdr_reset(Work w) {
     h->round = 0;
     h->q_sample = 0; h->q_fit = 0; h->q_classify = 0; h->q_scatter = 0;
     h->q_med = 0; h->q_base = 0; h->q_bigrun = 0;
+    h->n_medw = 0; h->q_medw = 0;
     for (int i = 0; i < 8; i++) h->small_hist[i] = 0;
     // the scan's completion counter (the last entry of its scratch)
     w.scan_tmp[w.scan_tmp_max - 1u] = 0u;
@@ -377,6 +389,9 @@ __global__ void __launch_bounds__(1024) k_plan(Work w, Params p) {
         h->chunk = chunk;
         h->large_elems_snap = ok ? ta : 0u;
         h->n_med_snap = min(h->n_med, w.mmax);
+        h->n_medw_snap = min(h->n_medw, w.mmax);
+        h->n_medw = 0;
+        h->q_medw = 0;
         h->med_elems_snap = h->med_elems;
         h->n_small_snap = h->n_small;
         h->n_tiny_snap = h->n_tiny;
@@ -1340,6 +1355,297 @@ __global__ void __launch_bounds__(kScatterThreads, SSS_MED_MIN_BLOCKS) k_med_rou
     }
 }
 
+// ------------------------------------------------------------ medium round, one warp per bucket
+
+// The medium buckets of at most kMedWarpMax strings: one warp runs the
+// whole distribution round of a bucket (sample of at most 63 keys, tree of
+// at most 31 splitters, classification, bucket starts, child segments,
+// stable move), with warp shuffles and __syncwarp instead of block-wide
+// barriers, so that the many small buckets of a round overlap their phases
+// instead of leaving most of a CTA idle between barriers.
+#ifndef SSS_MW_WARPS
+#define SSS_MW_WARPS 4
+#endif
+constexpr int kMWWarps = SSS_MW_WARPS;  // buckets a CTA holds at once
+
+template <class KT>
+struct MedWarpSmem {
+    KT samp[2 << kMWKMax];                       // the sorted sample (64 keys)
+    KT lvl[1 << kMWKMax];                        // splitter choice, level order 1..v
+    int32_t ra[1 << kMWKMax], rb[1 << kMWKMax];  // its sample ranges
+    uint16_t run_lo[2 << kMWKMax], run_hi[2 << kMWKMax];
+    LevelTree<KT, 1 << kMWKMax> t;               // the tree of the descent, level order 1..v
+    KT ino[1 << kMWKMax];                        // in-order splitters 0..v-1
+    uint32_t hist[kMWNB + 1];                    // bucket sizes (entry kMWNB: no string)
+    uint32_t run_pos[kMWNB + 1];                 // next output position of each bucket
+    uint32_t rdep[kMWNB + 1];                    // refill code of each bucket
+    uint8_t bid[kMedWarpMax + 1];                // bucket of each string of the segment
+};
+
+// bitonic_sort_regs for one warp and 64 keys: element 2 lane + r is x[r];
+// every stride lies within the warp.  Leaves s[0..64) sorted.
+template <class KT>
+__device__ __forceinline__ void warp_bitonic64(KT* s, KT x0, KT x1) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t i0 = 2u * lane, i1 = i0 + 1u;
+#pragma unroll
+    for (uint32_t size = 2; size <= 64u; size <<= 1) {
+#pragma unroll
+        for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+            if (stride >= 2u) {
+                const KT y0 = shfl_xor_key(x0, (int)(stride >> 1)), y1 = shfl_xor_key(x1, (int)(stride >> 1));
+                x0 = bitonic_keep(x0, y0, i0, stride, size);
+                x1 = bitonic_keep(x1, y1, i1, stride, size);
+            } else if (kgt(x0, x1) == ((i0 & size) == 0u)) {
+                const KT y = x0;
+                x0 = x1;
+                x1 = y;
+            }
+        }
+    }
+    s[i0] = x0;
+    s[i1] = x1;
+    __syncwarp();
+}
+
+// equal_runs for one warp and at most 64 keys (indices 2 lane, 2 lane + 1).
+template <class KT>
+__device__ __forceinline__ void warp_equal_runs(const KT* s, uint32_t cnt, uint16_t* lo, uint16_t* hi) {
+    constexpr uint32_t kInf = 0xFFFFu;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t i0 = 2u * lane, i1 = i0 + 1u;
+    uint32_t a0 = 0u, a1 = 0u, b0 = kInf, b1 = kInf;
+    if (i0 < cnt) a0 = (i0 == 0u || !keq(s[i0 - 1u], s[i0])) ? i0 : 0u;
+    a1 = (i1 < cnt && !keq(s[i0], s[i1])) ? i1 : a0;
+    if (i1 < cnt) b1 = (i1 + 1u >= cnt || !keq(s[i1], s[i1 + 1u])) ? i1 + 1u : kInf;
+    if (i0 < cnt) b0 = (i1 >= cnt || !keq(s[i0], s[i1])) ? i0 + 1u : b1;
+    uint32_t pa = a1, sb = b0;
+#pragma unroll
+    for (uint32_t o = 1; o < 32u; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL_MASK, pa, o);
+        const uint32_t z = __shfl_down_sync(FULL_MASK, sb, o);
+        if (lane >= o) pa = max(pa, y);
+        if (lane + o < 32u) sb = min(sb, z);
+    }
+    uint32_t cpre = __shfl_up_sync(FULL_MASK, pa, 1);
+    uint32_t csuf = __shfl_down_sync(FULL_MASK, sb, 1);
+    if (lane == 0u) cpre = 0u;
+    if (lane == 31u) csuf = kInf;
+    if (i0 < cnt) {
+        lo[i0] = (uint16_t)max(cpre, a0);
+        hi[i0] = (uint16_t)min(csuf, b0);
+    }
+    if (i1 < cnt) {
+        lo[i1] = (uint16_t)max(cpre, a1);
+        hi[i1] = (uint16_t)min(csuf, b1);
+    }
+    __syncwarp();
+}
+
+// select_splitters for one warp and a tree of at most kMWKMax levels (a
+// level's nodes, at most 16, one per lane); returns the levels that hold a
+// node with a non-empty sample range.
+template <class KT>
+__device__ __forceinline__ int warp_select_splitters(const KT* s, uint32_t cnt, int k, KT* lvl, int32_t* ra,
+                                                     int32_t* rb, const uint16_t* run_lo, const uint16_t* run_hi) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t v = (1u << k) - 1u;
+    if (lane == 0) {
+        ra[1] = 0;
+        rb[1] = (int32_t)cnt - 1;
+    }
+    __syncwarp();
+    int used = 0;
+    for (int l = 0; l < k; l++) {
+        const uint32_t first = 1u << l;
+        const uint32_t i = first + lane;
+        bool nonempty = false;
+        if (lane < first) {
+            const int32_t a = ra[i], b = rb[i];
+            KT x;
+            int32_t bl, ar;
+            if (a <= b) {
+                nonempty = true;
+                const int32_t m = a + (b - a) / 2;
+                x = s[m];
+                bl = max(a, (int32_t)run_lo[m]) - 1;
+                ar = min(b + 1, (int32_t)run_hi[m]);
+            } else {
+                x = lvl[i >> 1];
+                bl = a - 1;
+                ar = b + 1;
+            }
+            lvl[i] = x;
+            if (2u * i <= v) {
+                ra[2 * i] = a; rb[2 * i] = bl;
+                ra[2 * i + 1] = ar; rb[2 * i + 1] = b;
+            }
+        }
+        if (__any_sync(FULL_MASK, nonempty)) used = l + 1;
+        __syncwarp();
+    }
+    return used;
+}
+
+// emit_tree_smem for one warp (v <= 31 nodes, one per lane).
+template <class KT, int N>
+__device__ __forceinline__ void warp_emit_tree(const KT* lvl, int k, LevelTree<KT, N>& t, KT* ino) {
+    const uint32_t v = (1u << k) - 1u;
+    const uint32_t i = 1u + (threadIdx.x & 31u);
+    if (i <= v) {
+        const uint32_t l = 31u - __clz(i);
+        const uint32_t q = i - (1u << l);
+        const uint32_t pos = (2u * q + 1u) * (1u << (k - 1 - (int)l)) - 1u;
+        t.set(i, lvl[i]);
+        ino[pos] = lvl[i];
+    }
+    __syncwarp();
+}
+
+template <class KT>
+__global__ void __launch_bounds__(32 * kMWWarps, 32 / kMWWarps) k_med_warp(Work w, Params p) {
+    constexpr int kU = 4;  // strings a lane takes at once
+    __shared__ MedWarpSmem<KT> smw[kMWWarps];
+    const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+    MedWarpSmem<KT>& sm = smw[wid];
+    const int cur = w.hdr->round & 1u;
+    const int med_in = cur, med_out = cur ^ 1;
+    const uint32_t n = w.hdr->n_medw_snap;
+    const uint32_t lt = lanemask_lt();
+    const Rec* rec_in = w.rec[cur];
+    Rec* rec_out = w.rec[cur ^ 1];
+    const uint32_t nwarps = gridDim.x * kMWWarps;
+    uint32_t nref = 0;
+    for (uint32_t mi = blockIdx.x * kMWWarps + wid; mi < n;) {
+        Seg g = w.medw[med_in][mi];
+        const uint32_t m = g.size, end = g.begin + g.size;
+        const int kp = choose_k(m, min(p.k_max, kMWKMax));
+        const uint32_t pw = 2u << kp, cnt = pw - 1u;
+        int k = kp;
+        uint32_t nb = pw - 1u;
+        Rec* recs = w.rec[cur];
+        for (uint32_t level = 0;; level++) {
+            // sample, sorted two keys a lane (top past the sample)
+            KT x[2];
+#pragma unroll
+            for (int r = 0; r < 2; r++) {
+                const uint32_t j = 2u * lane + r;
+                x[r] = j < cnt ? KeyTraits<KT>::load(recs + g.begin + sample_pos(p.seed, g.begin, m, j))
+                               : KeyTraits<KT>::top();
+            }
+            sm.hist[lane] = 0u;
+            sm.hist[lane + 32u] = 0u;
+            warp_bitonic64(sm.samp, x[0], x[1]);
+            warp_equal_runs(sm.samp, cnt, sm.run_lo, sm.run_hi);
+            k = max(1, warp_select_splitters(sm.samp, cnt, kp, sm.lvl, sm.ra, sm.rb, sm.run_lo, sm.run_hi));
+            nb = (2u << k) - 1u;
+            warp_emit_tree(sm.lvl, k, sm.t, sm.ino);
+            // classify: bucket of every string, sizes
+            for (uint32_t base = g.begin; base < end; base += 32u * kU) {
+                KT kk[kU];
+#pragma unroll
+                for (int u = 0; u < kU; u++) {
+                    const uint32_t e = base + 32u * u + lane;
+                    kk[u] = e < end ? KeyTraits<KT>::load(recs + e) : KeyTraits<KT>::top();
+                }
+                uint32_t bk[kU];
+                classify_keys_by<kU>(p.equal_test != 0, kk, bk, sm.t.view(), sm.ino, k);
+#pragma unroll
+                for (int u = 0; u < kU; u++) {
+                    const uint32_t e = base + 32u * u + lane;
+                    const uint32_t b = e < end ? bk[u] : (uint32_t)kMWNB;
+                    if (e < end) sm.bid[e - g.begin] = (uint8_t)b;
+                    const uint32_t peers = __match_any_sync(FULL_MASK, b);
+                    if (lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&sm.hist[b], (uint32_t)__popc(peers));
+                }
+            }
+            __syncwarp();
+            // every string in the equality bucket of one splitter without the
+            // terminator: they share the next w characters; gather their keys
+            // w deeper in place and classify again
+            bool full = false;
+            for (uint32_t b = 1u + 2u * lane; b < nb; b += 64u)
+                if (sm.hist[b] == m && !kends(sm.ino[b >> 1])) full = true;
+            if (!__any_sync(FULL_MASK, full) || level >= kBaseMaxIters) break;
+            for (uint32_t e = g.begin + lane; e < end; e += 32u) {
+                Rec r = load_rec(recs + e);
+                refill_rec<KT>(w.chars, r, g.depth + KeyTraits<KT>::kBytes, g.depth);
+                store_rec(recs + e, r);
+                nref++;
+            }
+            g.depth += KeyTraits<KT>::kBytes;
+            __syncwarp();
+        }
+        // bucket starts, two buckets a lane, and the child segments
+        uint32_t cnts[2], ckind[2], cstart[2], cdep[2], crun[2];
+#pragma unroll
+        for (int q = 0; q < 2; q++) cnts[q] = 2u * lane + q < nb ? sm.hist[2u * lane + q] : 0u;
+        uint32_t tot;
+        uint32_t start = g.begin + warp_excl(cnts[0] + cnts[1], &tot);
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+            const uint32_t b = 2u * lane + q;
+            BucketInfo bi{0u, 0u, false};
+            if (b < nb) {
+                bi = bucket_info(b, nb, g.depth, sm.ino, cnts[q], p.base_threshold);
+                sm.run_pos[b] = start;
+                sm.rdep[b] = refill_code(bi, cnts[q], g.depth);
+                if (cnts[q] > 0 && start > g.begin) w.out_lcp[start] = kLcpFlag | g.depth;
+            }
+            ckind[q] = b < nb && cnts[q] > 0 ? child_kind(p, cnts[q], bi.isrun) : kChildNone;
+            cstart[q] = start;
+            cdep[q] = bi.cdepth;
+            crun[q] = bi.runlcp;
+            start += cnts[q];
+        }
+        append_children_n<2>(w, med_out, ckind, cstart, cnts, cdep, crun);
+        __syncwarp();
+        // stable move, strings in index order
+        for (uint32_t base = g.begin; base < end; base += 32u * kU) {
+            Rec rr[kU];
+            uint32_t bb[kU];
+#pragma unroll
+            for (int u = 0; u < kU; u++) {
+                const uint32_t e = base + 32u * u + lane;
+                const bool ok = e < end;
+                rr[u] = ok ? load_rec(rec_in + e) : Rec{0ull, 0ull, 0ull, 0u, 0u};
+                bb[u] = ok ? (uint32_t)sm.bid[e - g.begin] : (uint32_t)kMWNB;
+            }
+            // next key words of strings whose bucket moves deeper, issued
+            // before any store
+#pragma unroll
+            for (int u = 0; u < kU; u++) {
+                const uint32_t rd = bb[u] < nb ? sm.rdep[bb[u]] : kNoRefill;
+                if (rd != kNoRefill && rd != kSingle) {
+                    refill_rec<KT>(w.chars, rr[u], rd, g.depth);
+                    nref++;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kU; u++) {
+                const uint32_t b = bb[u];
+                const uint32_t peers = __match_any_sync(FULL_MASK, b);
+                const uint32_t leader = (uint32_t)__ffs(peers) - 1u;
+                const uint32_t pos = sm.run_pos[b] + (uint32_t)__popc(peers & lt);
+                __syncwarp();
+                if (lane == leader && b < nb) sm.run_pos[b] += (uint32_t)__popc(peers);
+                __syncwarp();
+                if (b < nb) {
+                    if (pos >= end) atomicOr(&w.hdr->err, kErrPosition);
+                    else if (sm.rdep[b] == kSingle) w.out_perm[pos] = rr[u].idx;
+                    else store_rec(rec_out + pos, rr[u]);
+                }
+            }
+        }
+        __syncwarp();
+        // the next bucket
+        uint32_t nx = 0;
+        if (lane == 0) nx = nwarps + atomicAdd(&w.hdr->q_medw, 1u);
+        mi = __shfl_sync(FULL_MASK, nx, 0);
+    }
+    add_refills(&w.hdr->med_refills, nref);
+}
+
 // ------------------------------------------------------------ base case
 
 constexpr int kBaseThreads = kBaseCap;  // one thread per slot of a tile
@@ -1981,6 +2287,14 @@ static cudaError_t launch_medium_t(const Work& w, const Params& p, const Hdr* hc
         ProfScope ps(pf, kMedium, st);
         k_med_round<KT><<<gm, kScatterThreads, sizeof(MedSmem<KT>), st>>>(w, p);
     }
+    if (kMedWarpMax > 0u) {
+        const uint32_t gw = grid_of(p.num_sms * (32u / kMWWarps), hc,
+                                    hc ? (hc->n_medw_snap + kMWWarps - 1u) / kMWWarps : 0u);
+        if (gw) {
+            ProfScope ps(pf, kMedium, st);
+            k_med_warp<KT><<<gw, 32 * kMWWarps, 0, st>>>(w, p);
+        }
+    }
     return cudaGetLastError();
 }
 
@@ -2073,7 +2387,7 @@ cudaError_t launch_body(const Work& w, const Params& p, const Hdr* hc, uint32_t*
 // Loop condition of the graph form: another round is needed while the last
 // plan left large or medium segments.
 __global__ void k_set_cond(Work w, cudaGraphConditionalHandle cond) {
-    cudaGraphSetConditional(cond, (w.hdr->L > 0u || w.hdr->n_med_snap > 0u) ? 1u : 0u);
+    cudaGraphSetConditional(cond, (w.hdr->L > 0u || w.hdr->n_med_snap > 0u || w.hdr->n_medw_snap > 0u) ? 1u : 0u);
 }
 
 cudaError_t launch_set_cond(const Work& w, cudaGraphConditionalHandle cond, cudaStream_t st) {
