@@ -30,6 +30,7 @@ import hashlib
 import json
 import multiprocessing as mp
 import os
+import gc
 import statistics
 import subprocess
 import sys
@@ -724,10 +725,16 @@ def main():
         # the median call, as for the headline, with the mean and the
         # slowest beside it
         calls = []
-        for _ in range(args.e2e_steps):
-            t0 = time.perf_counter()
-            sss.sss_sort_host(h_chars, len(s.chars), h_off, n, h_perm, h_lcp)
-            calls.append(time.perf_counter() - t0)
+        gc_was_on = gc.isenabled()
+        gc.disable()  # no collector pause inside a host-timed call
+        try:
+            for _ in range(args.e2e_steps):
+                t0 = time.perf_counter()
+                sss.sss_sort_host(h_chars, len(s.chars), h_off, n, h_perm, h_lcp)
+                calls.append(time.perf_counter() - t0)
+        finally:
+            if gc_was_on:
+                gc.enable()
         te = reduce_max(statistics.median(calls), dist, dev)
         e2e = {"value": n * world / te, "unit": "strings/s", "h2d_bytes_per_step": int(len(s.chars) + 8 * n),
                "d2h_bytes_per_step": int(8 * n), "ms_per_step": te * 1e3,
