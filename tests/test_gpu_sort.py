@@ -420,14 +420,17 @@ def test_profiled_timeline():
 
 
 @pytest.mark.parametrize("key_bytes", [8, 16])
-def test_medium_rounds_step_over_shared_prefixes(key_bytes):
-    # medium-sized groups whose strings share 100+ characters: the per-CTA
-    # round steps over them in place (gathering keys deeper) before it moves
+@pytest.mark.parametrize("group", [(1500, 97), (300, 53)])
+def test_medium_rounds_step_over_shared_prefixes(key_bytes, group):
+    # medium-sized groups whose strings share 100+ characters: the medium
+    # round steps over them in place (gathering keys deeper) before it moves;
+    # groups of 1500..2567 strings take the per-CTA round, groups of 300..883
+    # the per-warp one
     rng = random.Random(17)
     items = []
     for gi in range(12):
         prefix = b"group%02d/" % gi + bytes(rng.choice(b"abcdef") for _ in range(100 + 7 * gi))
-        for _ in range(1500 + 97 * gi):
+        for _ in range(group[0] + group[1] * gi):
             items.append(prefix + bytes(rng.choice(b"ab") for _ in range(rng.randint(0, 12))))
     rng.shuffle(items)
     s = gen.from_list(items)
