@@ -61,8 +61,9 @@ typedef enum {
 typedef struct sss_options {
     int32_t k_max;             /* largest splitter tree depth k: v = 2^k - 1 splitters, 1..10 */
     uint32_t base_threshold;   /* buckets of at most this many strings go to the base case, 16..128 */
-    uint32_t medium_threshold; /* buckets of at most this many strings get one CTA for their
-                                  next round, base_threshold..8192 */
+    uint32_t medium_threshold; /* buckets of at most this many strings get one CTA (one warp
+                                  up to 1023 strings) for their next round,
+                                  base_threshold..8192 */
     uint32_t chunk;            /* largest work item (strings) of a device-wide round,
                                   multiple of 2048 */
     uint64_t seed;           /* seed of the pseudo-random sample positions */
@@ -126,7 +127,7 @@ enum {
     SSS_K_RUNS = 7,     /* large runs of equal strings */
     SSS_K_FIXUP = 8,    /* LCP at bucket boundaries, batched index rebasing */
     SSS_K_LEARNED = 9,  /* learned CDF fit and proposal */
-    SSS_K_MEDIUM = 10,  /* one CTA per medium bucket: a whole round in shared memory */
+    SSS_K_MEDIUM = 10,  /* one CTA (or warp) per medium bucket: a whole round in shared memory */
     SSS_K_ALPHABET = 11, /* alphabet compression: character scan, packing, LCP conversion */
     SSS_K_CLASSES = 12
 };
@@ -136,7 +137,7 @@ typedef struct sss_stats {
     uint32_t rounds;                 /* distribution rounds run */
     uint32_t base_tiles;             /* base-case work tiles launched */
     uint64_t round_strings;          /* sum over rounds of strings distributed */
-    uint64_t medium_strings;         /* of those, strings in per-CTA (medium) rounds */
+    uint64_t medium_strings;         /* of those, strings in per-CTA or per-warp (medium) rounds */
     uint64_t base_iterations;        /* base-case sort passes summed over tiles and warp packs */
     uint32_t base_segment_hist[8];   /* base-case buckets by floor(log2(size)) (2-3, 4-7, ..., >= 128) */
     uint64_t base_strings;           /* strings finished by the base case */
@@ -144,7 +145,7 @@ typedef struct sss_stats {
     uint64_t learned_keys;           /* keys the learned model proposed a bucket for */
     uint64_t learned_misses;         /* of those, proposals the exact check rejected */
     uint64_t refilled_strings;       /* key words gathered again from chars during rounds */
-    uint64_t medium_refilled_strings; /* of those, gathered in per-CTA (medium) rounds */
+    uint64_t medium_refilled_strings; /* of those, gathered in medium rounds */
     uint32_t launches;               /* kernel launches of the call */
     uint32_t profiled;               /* 1 if the prof_* fields below were measured */
     uint32_t prof_launches[SSS_K_CLASSES]; /* launches per kernel class */
