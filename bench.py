@@ -523,7 +523,7 @@ def leg_batched(sss, torch, stream, dev, args, world, dist):
 def leg_uniform(sss, torch, stream, dev, args, world, dist):
     """The small configured workload (100k strings of 8-20 letters, 1.5 MB:
     it lives in L2 and the sort is bound by launch and round latency, so it
-    is reported, not judged), graph form."""
+    is reported beside the headline, not as one), graph form."""
     s = gen.workload("uniform-100k")
     n = s.n
     chars = torch.from_numpy(s.chars).to(dev)
@@ -544,7 +544,7 @@ def leg_uniform(sss, torch, stream, dev, args, world, dist):
     return {"workload": WORKLOAD_TEXT["uniform-100k"], "n": n, "chars_bytes": int(s.total),
             "value": n * world / (ms * 1e-3), "unit": "strings/s", "ms_per_step": ms, "steps": steps,
             "rounds": int(st.rounds), "gpu_launches_per_step": int(st.launches),
-            "l2": "inputs fit in L2 (no flush): reported, not judged"}
+            "l2": "inputs fit in L2 (no flush): a side figure, not a headline"}
 
 
 def leg_literal(sss, torch, stream, dev, args, world, dist):
