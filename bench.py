@@ -521,7 +521,7 @@ def leg_batched(sss, torch, stream, dev, args, world, dist):
 
 
 def leg_uniform(sss, torch, stream, dev, args, world, dist):
-    """The small configured workload (100k strings of 8-20 letters, 1.5 MB:
+    """The small workload (100k strings of 8-20 letters, 1.5 MB:
     it lives in L2 and the sort is bound by launch and round latency, so it
     is reported beside the headline, not as one), graph form."""
     s = gen.workload("uniform-100k")
@@ -548,7 +548,7 @@ def leg_uniform(sss, torch, stream, dev, args, world, dist):
 
 
 def leg_literal(sss, torch, stream, dev, args, world, dist):
-    """The batch as configured: 10,000 sets, sizes log-uniform in [100, 1M]
+    """The sets-literal batch: 10,000 sets, sizes log-uniform in [100, 1M]
     (1.09 G strings, about 51 GB of characters), one graph launch with the
     default options, against one sss_sort call per set (host-driven rounds),
     all sets once."""

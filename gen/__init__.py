@@ -38,10 +38,10 @@ WORKLOADS = {
 }
 
 # batched workloads, 10,000 sets each, kinds uniform, seed 5:
-#   sets-literal  sizes log-uniform in [100, 1,000,000] as configured
+#   sets-literal  sizes log-uniform in [100, 1,000,000]
 #                 (1,092,616,105 strings, about 51 GB of characters)
-#   sets-10k      sizes log-uniform in [100, 4000], the reading that keeps the
-#                 configured total of about 500M characters
+#   sets-10k      sizes log-uniform in [100, 4000]: about 500M characters in
+#                 all
 BATCH_WORKLOADS = {
     "sets-literal": dict(num_sets=10_000, lo=100, hi=1_000_000, seed=5),
     "sets-10k": dict(num_sets=10_000, lo=100, hi=4000, seed=5),

@@ -54,7 +54,7 @@ def test_batch_recipe():
 
 
 def test_literal_batch_sizes():
-    """The configured batch: 10,000 sets, sizes log-uniform in [100, 1M]
+    """The sets-literal batch: 10,000 sets, sizes log-uniform in [100, 1M]
     (mean (1M - 100) / ln(10^4), about 108.6k strings a set), kinds uniform."""
     w = gen.BATCH_WORKLOADS["sets-literal"]
     sizes, kinds = gen.batch_sizes(w["num_sets"], w["lo"], w["hi"], w["seed"])

@@ -71,7 +71,7 @@ def test_batched_sets_10k_full_workload():
 
 
 def test_batched_sets_literal_full_workload():
-    """The batch as configured: 10,000 sets with sizes log-uniform in
+    """The sets-literal batch: 10,000 sets with sizes log-uniform in
     [100, 1M] (1.09 G strings, about 51 GB of characters), so one graph
     launch mixes device-wide rounds of sets up to 1M strings with thousands
     of small sets.  Every set is checked against the oracle's verify."""
