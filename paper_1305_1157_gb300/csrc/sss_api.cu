@@ -399,8 +399,7 @@ int run_sort(const Work& w, const sss_options& o, const Seg* roots_dev, uint32_t
         const unsigned long long lk0 = hh->learned_keys, lm0 = hh->learned_misses;
         CK(launch_body(w, p, hh, &tiles, pf, st, br), "round");
         stats->base_tiles += tiles;
-        CK(launch_plan(w, p, pf, st), "plan");
-        CK(launch_advance(w, pf, st), "advance");
+        CK(launch_plan(w, p, pf, st, 1u), "plan");  // and hdr->round += 1 (flips the buffers and lists)
         rc = read_hdr(hh, w, st);
         if (rc) return rc;
         if (round < SSS_MAX_ROUNDS_LOGGED) {  // the learned proposals of this round
@@ -533,14 +532,12 @@ int build_graph(const Work& w, const Params& p, const Seg* roots_dev, uint32_t n
         return done(err, "begin body capture");
     counter.reset(false);
     if ((err = launch_body(w, p, nullptr, nullptr, &counter, body_st, &br)) != cudaSuccess ||
-        (err = launch_plan(w, p, &counter, body_st)) != cudaSuccess ||
-        (err = launch_advance(w, &counter, body_st)) != cudaSuccess ||
-        (err = launch_set_cond(w, cond, body_st)) != cudaSuccess) {
+        (err = launch_plan(w, p, &counter, body_st, 2u, cond)) != cudaSuccess) {
         cudaGraph_t b2 = nullptr;
         cudaStreamEndCapture(body_st, &b2);
         return done(err, "graph body");
     }
-    gc.launches_body = counter.launches + 1;
+    gc.launches_body = counter.launches;
     cudaGraph_t body_out = nullptr;
     if ((err = cudaStreamEndCapture(body_st, &body_out)) != cudaSuccess) return done(err, "end body capture");
     // epilogue

@@ -691,7 +691,10 @@ cudaError_t launch_fused_root(const Work& w, const Params& p, const Hdr* hc, Pro
 // roots == nullptr: one root [0, n); else num_roots device segments (batched)
 cudaError_t launch_roots(const Work& w, const Params& p, const Seg* roots, uint32_t num_roots, Prof* pf,
                          cudaStream_t st);
-cudaError_t launch_plan(const Work& w, const Params& p, Prof* pf, cudaStream_t st);
+// The next round's plan; advance 1: and the round counter; 2: and the graph
+// form's round-loop condition (cond)
+cudaError_t launch_plan(const Work& w, const Params& p, Prof* pf, cudaStream_t st, uint32_t advance = 0u,
+                        cudaGraphConditionalHandle cond = 0);
 // One distribution round: device-wide kernels for the planned large segments
 // and one CTA per medium segment, reading counts and the buffer parity
 // (hdr->round) from device memory.  hc: host copy of the header when known
@@ -721,8 +724,6 @@ cudaError_t launch_body(const Work& w, const Params& p, const Hdr* hc, uint32_t*
 cudaError_t launch_set_cond(const Work& w, cudaGraphConditionalHandle cond, cudaStream_t st);
 cudaError_t prepare_kernels(uint32_t cdf_M);
 cudaError_t prepare_cdf_kernels(uint32_t M);
-// hdr->round += 1 (flips the working buffers and medium lists)
-cudaError_t launch_advance(const Work& w, Prof* pf, cudaStream_t st);
 // base case and large runs of the buckets listed by the last k_plan
 cudaError_t launch_small(const Work& w, const Params& p, const Hdr* hc, uint32_t* out_tiles, Prof* pf,
                          cudaStream_t st);

@@ -338,7 +338,10 @@ __global__ void k_roots(Work w, Params p, const Seg* roots, uint32_t num_roots, 
 
 // One CTA: layout of the next device-wide round.  The chunk size is chosen so
 // that the round has about kChunksPerSM work items per SM.
-__global__ void __launch_bounds__(1024) k_plan(Work w, Params p) {
+// advance: 0 plans only; 1 also advances the round counter (the host-driven
+// loop); 2 also sets the graph's round-loop condition (the graph form's loop
+// body), so that the round's last kernel is this one.
+__global__ void __launch_bounds__(1024) k_plan(Work w, Params p, uint32_t advance, cudaGraphConditionalHandle cond) {
     __shared__ uint32_t wsum[33];
     Hdr* h = w.hdr;
     const uint32_t L_all = h->n_large;
@@ -408,6 +411,11 @@ __global__ void __launch_bounds__(1024) k_plan(Work w, Params p) {
         h->med_elems = 0;
         h->q_sample = 0; h->q_fit = 0; h->q_classify = 0; h->q_scatter = 0;
         h->q_med = 0; h->q_base = 0; h->q_bigrun = 0;
+        if (advance) {
+            h->round += 1u;
+            if (advance == 2u)
+                cudaGraphSetConditional(cond, (h->L > 0u || h->n_med_snap > 0u || h->n_medw_snap > 0u) ? 1u : 0u);
+        }
     }
 }
 
@@ -2240,13 +2248,12 @@ cudaError_t launch_roots(const Work& w, const Params& p, const Seg* roots, uint3
     return cudaGetLastError();
 }
 
-cudaError_t launch_plan(const Work& w, const Params& p, Prof* pf, cudaStream_t st) {
+cudaError_t launch_plan(const Work& w, const Params& p, Prof* pf, cudaStream_t st, uint32_t advance,
+                        cudaGraphConditionalHandle cond) {
     ProfScope ps(pf, kPlan, st);
-    k_plan<<<1, 1024, 0, st>>>(w, p);
+    k_plan<<<1, 1024, 0, st>>>(w, p, advance, cond);
     return cudaGetLastError();
 }
-
-__global__ void k_advance(Work w) { w.hdr->round += 1u; }
 
 template <class KT>
 static cudaError_t launch_round_t(const Work& w, const Params& p, const Hdr* hc, Prof* pf, cudaStream_t st) {
@@ -2413,12 +2420,6 @@ cudaError_t prepare_kernels(uint32_t cdf_M) {
     if (e == cudaSuccess) e = prepare_kernels_t<Key16>();
     if (e == cudaSuccess) e = prepare_cdf_kernels(cdf_M);
     return e;
-}
-
-cudaError_t launch_advance(const Work& w, Prof* pf, cudaStream_t st) {
-    ProfScope ps(pf, kPlan, st);
-    k_advance<<<1, 1, 0, st>>>(w);
-    return cudaGetLastError();
 }
 
 // The warp-form base case (buckets of at most kTinyMax strings).
